@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Benchmark of the fused Simulation -> Hierarchy-Scan -> Bind MeshPose frame.
+
+One step = one full frame of the 4,096 x 512-joint + 1,024-joint-dragon
+workload (2,098,176 joints): per-character key sampling, slerp/lerp between
+keys and between two clips, the Hierarchy-Scan and the bind product, as the
+library's two launches (work queue + persistent kernel) replayed from CUDA
+graphs.  The output rotates over enough buffers that consecutive steps
+touch more memory than the 129 MB L2 (inputs larger than L2).
+
+Printed (rank 0, one JSON line): joints/s of the whole job, the roofline of
+the persistent frame kernel (algorithmic bytes / CUDA-event duration against
+the measured HBM copy bandwidth), the end-to-end rate through the public API
+with host buffers, the plain level-synchronous kernel on the same frame, the
+fused forward+adjoint (loss_backward) on the 1,024 x 256-joint workload, the
+FP64 oracle on the host cores, and SM clocks sampled during the timed loop.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+a bounded sample of the same workload.
+
+Multi-GPU: characters are independent, so each rank runs its own batch of
+the same size (weak scaling, no data-path collective); the timing is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "joint transforms/s fwd and fwd+bwd on 1 GB300, % of HBM roofline, vs plain kernel"
+UNIT = "joints/s"
+L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes per launch of the persistent frame kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
+# kernel sources it was taken on; reported as null once the sources change.
+NCU_TRAFFIC = {}
+
+
+# ------------------------------------------------------------------ helpers
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2505_06703_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def frame_algorithmic_bytes(w: dict) -> int:
+    """Compulsory unique bytes of one frame: the skin matrices written (48 B
+    per joint), each used type's tables read once (keys: 28 B of q and t per
+    key record, inverse binds 48 B and parents 4 B per joint) and 12 B per
+    character (time, blend weight, type id)."""
+    types = w["types"]
+    ct = w["char_type"]
+    joints = sum(len(types[t]["parents"]) for t in ct)
+    tables = 0
+    for t in sorted(set(int(x) for x in ct)):
+        ty = types[t]
+        n = len(ty["parents"])
+        nc, nk = ty["keys"].shape[:2]
+        tables += nc * nk * n * 28 + n * 48 + n * 4
+    return joints * 48 + tables + len(ct) * 12
+
+
+def fwd_bwd_algorithmic_bytes(w: dict) -> int:
+    """loss_backward: read q (16 B), t (12 B), target (12 B) and write dq
+    (16 B), dt (12 B) per joint, plus the type's parent table."""
+    types = w["types"]
+    joints = len(w["q"])
+    return joints * 68 + sum(len(t["parents"]) * 4 for t in types)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def rank_workload(rank: int) -> dict:
+    """The same skeletons and clips on every rank; each rank's characters get
+    their own times and blend weights (an independent batch)."""
+    w = synth.config2()
+    if rank:
+        rng = np.random.default_rng(1000 + rank)
+        n = len(w["char_type"])
+        w["time"] = rng.uniform(0.0, 1.0, n).astype(np.float32)
+        w["weight"] = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    return w
+
+
+def aggregate_max(x: float, world: int) -> float:
+    """Maximum over ranks (timing only; no data crosses ranks)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            if self.path:
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ our arm
+def setup_ctx(w: dict, device: int):
+    import paper_2505_06703_gb300 as pk
+    ctx = pk.Context(device)
+    types = w["types"]
+    ids = ctx.create_skeletons([t["parents"] for t in types], rest_q=[t["rest_q"] for t in types],
+                               rest_t=[t["rest_t"] for t in types])
+    for i, t in zip(ids, types):
+        if "keys" in t:
+            ctx.upload_clips(i, t["keys"], t["rate_hz"])
+    plan = ctx.plan(np.asarray(ids, np.int32)[w["char_type"]])
+    return ctx, plan
+
+
+def time_events(fn, steps: int, warmup: int):
+    """Run fn(s) warmup + steps times on the current stream; return the
+    CUDA-event milliseconds of the timed steps (synchronized on both sides)."""
+    import torch
+    for s in range(warmup):
+        fn(s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        fn(warmup + s)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_ours(args) -> dict:
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+
+    w = rank_workload(rank)
+    ctx, plan = setup_ctx(w, local)
+    joints = plan.total
+    n_chars = plan.n_chars
+    out_bytes = joints * 48
+    n_out = max(3, math.ceil(2.5 * L2_BYTES / out_bytes))
+    outs = [torch.empty((joints, 12), dtype=torch.float32, device=dev) for _ in range(n_out)]
+    # per-step inputs: times advance by 1/60 s per frame
+    n_in = 6
+    times = [torch.as_tensor(np.mod(w["time"] + k / 60.0, 1.0).astype(np.float32), device=dev) for k in range(n_in)]
+    blend = torch.as_tensor(w["weight"], device=dev)
+
+    # one graph per (output buffer): work queue + persistent kernel
+    n_graph = n_out * n_in // math.gcd(n_out, n_in)
+    stream = torch.cuda.Stream()
+    graphs = []
+    with torch.cuda.stream(stream):
+        for i in range(n_graph):  # warm once outside capture (sets kernel attributes)
+            ctx.evaluate_frame(plan, times[i % n_in], blend, out=outs[i % n_out])
+    stream.synchronize()
+    for i in range(n_graph):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            ctx.evaluate_frame(plan, times[i % n_in], blend, out=outs[i % n_out])
+        graphs.append(g)
+    torch.cuda.synchronize()
+
+    steps, warmup = args.steps, args.warmup
+    for s in range(warmup):
+        graphs[s % n_graph].replay()
+    torch.cuda.synchronize()
+    barrier(world)
+    def load_for(seconds):
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < seconds:
+            for _ in range(64):
+                graphs[k % n_graph].replay()
+                k += 1
+            torch.cuda.synchronize()
+
+    # clocks are sampled over continuous load: ~0.7 s before, the timed
+    # steps, ~0.7 s after (the sampler's period is 200 ms)
+    with ClockSampler(local) as clocks:
+        load_for(0.7)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(steps):
+            graphs[(warmup + s) % n_graph].replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        load_for(0.7)
+    barrier(world)
+    ms_max = aggregate_max(ms, world)
+    ms_step = ms_max / steps
+    value = world * joints / (ms_step / 1e3)
+    clock = clocks.summary()
+
+    # the persistent frame kernel alone, events on its launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+
+    def kstep(s):
+        i = s % n_graph
+        ctx.frame_build_queue(plan, times[i % n_in])
+        if s >= warmup:
+            ev[s - warmup][0].record()
+        ctx.frame_run_queue(plan, times[i % n_in], blend, outs[i % n_out])
+        if s >= warmup:
+            ev[s - warmup][1].record()
+
+    time_events(kstep, steps, warmup)
+    k_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    alg = frame_algorithmic_bytes(w)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = alg / (k_ms / 1e3) / 1e9
+    tr = NCU_TRAFFIC.get(kernel_source_hash())
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": tr, "kernel": "k_scan<0> (persistent frame)",
+                "kernel_ms": round(k_ms, 5), "algorithmic_bytes": alg, "peak_source": peak_src}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+              "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32", "data": "synthetic (seeded skeletons, clips, times and blend weights)",
+              "config": {"workload": "frame: 4,096 chars x 512-joint biped+8x59 chains (depth 70) + 1 x 1,024-joint "
+                                     "dragon chain; 2 clips x 30 keys @30 Hz; slerp keys, slerp 2-clip blend, "
+                                     "hierarchy scan, bind",
+                         "joints_per_step_per_gpu": joints, "characters_per_gpu": n_chars,
+                         "l2": f"output rotated over {n_out} buffers ({n_out * out_bytes / 1e6:.0f} MB > 129 MB L2)",
+                         "timing": "CUDA graphs (work queue + persistent kernel), CUDA events",
+                         "parallelism": f"replicas x{world} (independent character batches)"},
+              "roofline": roofline, "gpu_launches": 2 * steps, "clocks": clock}
+
+    # end to end through the public API with host buffers: pinned inputs
+    # copied in, the whole skin output copied back every step
+    if True:
+        h_times = [t.cpu().pin_memory() for t in times]
+        h_blend = blend.cpu().pin_memory()
+        d_time = torch.empty_like(times[0])
+        d_blend = torch.empty_like(blend)
+        h_out = torch.empty((joints, 12), dtype=torch.float32).pin_memory()
+
+        def e2e_step(s):
+            d_time.copy_(h_times[s % n_in], non_blocking=True)
+            d_blend.copy_(h_blend, non_blocking=True)
+            ctx.evaluate_frame(plan, d_time, d_blend, out=outs[s % n_out])
+            h_out.copy_(outs[s % n_out], non_blocking=True)
+
+        e_steps = max(3, min(steps, 20))
+        e_ms = aggregate_max(time_events(e2e_step, e_steps, 2), world)
+        result["e2e"] = {"value": world * joints / (e_ms / e_steps / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(h_times[0].numel() * 4 + h_blend.numel() * 4),
+                         "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": e_ms / e_steps}
+
+    if not args.no_extras:
+        # plain level-synchronous kernel on the same frame
+        def plain_step(s):
+            ctx.evaluate_frame(plan, times[s % n_in], blend, out=outs[s % n_out], levelsync=True)
+
+        p_steps = max(3, min(steps, 20))
+        p_ms = aggregate_max(time_events(plain_step, p_steps, 2), world)
+        result["plain"] = {"value": world * joints / (p_ms / p_steps / 1e3), "unit": UNIT,
+                           "ms_per_step": p_ms / p_steps, "kernel": "k_levelsync (1 CTA/char, barrier per level)",
+                           "speedup_fused_vs_plain": (p_ms / p_steps) / ms_step}
+        result["fwd_bwd"] = run_fwd_bwd(ctx_factory=setup_ctx, device=local, dev=dev, steps=steps,
+                                        warmup=warmup, world=world, peak=peak)
+    del ctx
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result
+
+
+def run_fwd_bwd(ctx_factory, device, dev, steps, warmup, world, peak):
+    """Fused forward + adjoint (anim_loss_backward) on 1,024 characters of the
+    256-joint type: read q, t, target; write dq, dt (and per-character loss)."""
+    import torch
+    w = synth.config4()
+    ctx, plan = ctx_factory(w, device)
+    joints = plan.total
+    n_sets = max(2, math.ceil(2.5 * L2_BYTES / (joints * 68)))
+    sets = []
+    for k in range(n_sets):
+        q = torch.as_tensor(w["q"], device=dev) * (1.0 + 0.01 * k)
+        sets.append((q.contiguous(), torch.as_tensor(w["t"], device=dev), torch.as_tensor(w["target"], device=dev),
+                     torch.empty((joints, 4), device=dev), torch.empty((joints, 3), device=dev),
+                     torch.empty(plan.n_chars, device=dev)))
+
+    def step(s):
+        q, t, tg, gq, gt, loss = sets[s % n_sets]
+        ctx.loss_backward(plan, q, t, tg, grad_q=gq, grad_t=gt, loss=loss)
+
+    ms = aggregate_max(time_events(step, steps, warmup), world)
+    ms_step = ms / steps
+    alg = fwd_bwd_algorithmic_bytes(w)
+    achieved = alg / (ms_step / 1e3) / 1e9
+    return {"value": world * joints / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step,
+            "workload": "1,024 chars x 256-joint tree (depth 96), loss sum |p - target|^2",
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes": alg,
+                         "note": "memset of the queue counter + adjoint kernel per step"},
+            "l2": f"inputs/outputs rotated over {n_sets} sets ({n_sets * joints * 68 / 1e6:.0f} MB)"}
+
+
+def cpu_baseline(min_seconds: float = 6.0) -> dict:
+    """The FP64 oracle as it stands, single-threaded, on the full frame."""
+    import oracle
+    w = synth.config2()
+    joints = int(sum(len(w["types"][t]["parents"]) for t in w["char_type"]))
+    oracle.frame(w)  # build + warm
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < min_seconds:
+        oracle.frame(w)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": reps * joints / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"full frame ({joints:,} joints) x {reps} in {dt:.1f} s, FP64, one host thread"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args) -> dict | None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    w = synth.config2()
+    sample = synth.subset(w, list(range(0, 4096, 16)) + [4096])
+    joints = int(sum(len(w["types"][t]["parents"]) for t in sample["char_type"]))
+    for _ in range(args.warmup):
+        oracle.frame(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.frame(sample)
+    dt = time.perf_counter() - t0
+    value = args.steps * joints / dt
+    desc = f"every 16th character of the frame + the dragon ({joints:,} joints) per step, FP64, one host thread"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "frame: 4,096 x 512-joint + 1,024-joint dragon (bounded sample per step)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain-kernel and fwd+bwd measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        r = run_reference(args)
+        if r is not None:
+            print(json.dumps(r))
+        return
+    world, rank, _ = dist_env()
+    r = run_ours(args)
+    if rank == 0:
+        if world == 1 and not args.no_cpu:
+            r["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()

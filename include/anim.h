@@ -1,0 +1,226 @@
+/*
+ * anim.h -- C ABI of the GB300 skeletal-animation library.
+ *
+ * The library evaluates, for thousands of characters per frame, the three
+ * stages of GPU skeletal animation described in Sec. 1 of "A GPU-based
+ * solution for large-scale skeletal animation simulation" (arXiv 2505.06703):
+ *   1. Simulation: sample keyframes and interpolate/blend them into local
+ *      poses (Sec. 1 step 1; Sec. 2 requires that interpolation and blending
+ *      are kept);
+ *   2. Hierarchy-Scan: local -> model space, the tree prefix product of
+ *      Eq. 1 (Sec. 3);
+ *   3. Bind MeshPose: skin = model x inverse bind (Sec. 1 step 3);
+ * plus the adjoint of stages 2-3 for position losses and batched IK built on
+ * it (extensions of the path, not in the paper).
+ *
+ * Conventions
+ *   - Column vectors; 3x4 row-major affine matrices [R | t] (12 floats,
+ *     48 bytes) stand for 4x4 matrices with last row (0 0 0 1).
+ *   - Quaternions are stored (x, y, z, w), Hamilton product.
+ *   - Local pose L = [R(q/|q|) | t]; model M_i = M_parent(i) L_i (roots:
+ *     M_i = L_i); skin S_i = M_i B_i with B_i the inverse bind pose.
+ *   - A skeleton type is a parent array with parent[i] < i (the paper's
+ *     "traversing the tree in order", Sec. 3.2.1); parent[i] = -1 marks a
+ *     root.  Depth counts levels, a root has depth 1.
+ *   - Per-joint arrays of a batch of characters are [sum of joint counts][k]
+ *     with character c's joints at rows off[c] .. off[c]+n-1, off the
+ *     exclusive prefix of the joint counts in character order
+ *     (anim_plan_row_offsets).
+ *
+ * Ownership and threading
+ *   - Host arrays passed to create/upload calls are copied; the caller keeps
+ *     ownership.  Device pointers passed to the evaluation calls belong to the
+ *     caller; the library never frees them.  They must be 16-byte aligned.
+ *   - Evaluation calls are asynchronous on the given CUDA stream (`stream`
+ *     is a cudaStream_t; NULL is the legacy default stream).  They allocate
+ *     nothing and never synchronize, so they can be captured into a CUDA
+ *     graph once the plan has been tuned/built.
+ *   - A context is not thread-safe; use one per host thread.
+ *
+ * Errors
+ *   Every call returns ANIM_OK (0) or a negative ANIM_E* code and records a
+ *   message retrievable with anim_last_error().  No exception crosses the
+ *   ABI.  Invalid input data that only the GPU sees (non-finite times, out of
+ *   range blend weights are NOT errors; they are used as given) sets bits of
+ *   a device status word read by anim_get_status().
+ */
+#ifndef ANIM_H
+#define ANIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ANIM_API __attribute__((visibility("default")))
+#else
+#define ANIM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ANIM_OK = 0,
+  ANIM_EINVAL = -1,      /* bad argument (null pointer, size, parent array, alignment) */
+  ANIM_ENOMEM = -2,      /* device or host allocation failed */
+  ANIM_ECUDA = -3,       /* a CUDA runtime call failed */
+  ANIM_ETIMEOUT = -4,    /* a bounded device-side wait expired */
+  ANIM_EDEVICE = -5,     /* no usable device / wrong architecture */
+  ANIM_ESTATE = -6,      /* call out of order (e.g. clips missing for a type) */
+  ANIM_EUNSUPPORTED = -7 /* size beyond a documented limit */
+};
+
+/* Device status word bits (anim_get_status). */
+enum {
+  ANIM_STATUS_NONFINITE_TIME = 1, /* a character time was NaN/Inf; sampled at key 0 */
+  ANIM_STATUS_QUEUE = 2           /* a work item was malformed (library bug guard) */
+};
+
+/* Limits.  A skeleton type has at most ANIM_MAX_JOINTS joints. */
+#define ANIM_MAX_JOINTS 2048
+#define ANIM_MAX_KEYS 1024
+
+typedef struct anim_ctx anim_ctx;
+typedef struct anim_plan anim_plan;
+typedef struct anim_ik anim_ik;
+
+/* Create a context on CUDA device `device` (must be compute capability 10.3,
+ * the sm_103a target the kernels are built for).  *out receives the handle. */
+ANIM_API int anim_create(anim_ctx **out, int device);
+
+/* Destroy a context and every plan/IK object still owned by it. */
+ANIM_API int anim_destroy(anim_ctx *ctx);
+
+/* Message of the last error on this context ("" if none).  Valid until the
+ * next call on the context.  ctx may be NULL (then: last create error). */
+ANIM_API const char *anim_last_error(const anim_ctx *ctx);
+
+/* Register n_types skeleton types (the joint lists of Sec. 3.2.1).
+ *   joint_counts[t]  : 1 .. ANIM_MAX_JOINTS joints of type t;
+ *   parents          : concatenated parent arrays, parent[i] in [-1, i-1],
+ *                      else ANIM_EINVAL;
+ *   inv_bind         : concatenated [n][12] inverse bind poses B_i, or NULL to
+ *                      derive them on the GPU as the inverse of the model
+ *                      pose of the rest pose (rest_q, rest_t required then);
+ *   rest_q, rest_t   : concatenated [n][4] / [n][3] rest pose, or NULL;
+ *   out_type_ids     : receives the ids of the new types (n_types entries).
+ * Synchronous (returns after the device tables are built). */
+ANIM_API int anim_create_skeletons(anim_ctx *ctx, int n_types, const int32_t *joint_counts, const int32_t *parents,
+                          const float *inv_bind, const float *rest_q, const float *rest_t,
+                          int32_t *out_type_ids);
+
+/* Upload the clips sampled by the Simulation stage (Sec. 1 step 1) for a
+ * type: keys is host [n_clips][n_keys][n][8] = qx qy qz qw tx ty tz pad,
+ * n_clips in {1, 2} (with 2 clips the frame blends clip 0 -> clip 1 by the
+ * per-character weight), 2 <= n_keys <= ANIM_MAX_KEYS, keys looping with
+ * period n_keys / rate_hz seconds.  Replaces earlier clips of the type.
+ * Synchronous. */
+ANIM_API int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, float rate_hz, const float *keys);
+
+/* A plan fixes the characters of a batch: char_type[c] (host, n_chars
+ * entries) is each character's type.  The plan holds the row offsets, the
+ * per-type work lists and the device scratch of the frame's work queue.
+ * n_chars may be 0 (then evaluation calls are no-ops). */
+ANIM_API int anim_plan_create(anim_ctx *ctx, int64_t n_chars, const int32_t *char_type, anim_plan **out);
+ANIM_API int anim_plan_destroy(anim_ctx *ctx, anim_plan *plan);
+
+/* Total joints of the plan (rows of the per-joint arrays). */
+ANIM_API int anim_plan_total_joints(const anim_plan *plan, int64_t *out_total);
+
+/* Host copy of the row offsets: out[0..n_chars] (exclusive prefix). */
+ANIM_API int anim_plan_row_offsets(const anim_plan *plan, int64_t *out);
+
+/* The fused frame (Sec. 1 steps 1-3): for each character c, sample its
+ * type's clips at d_time[c] seconds, blend clip 0 -> clip 1 with
+ * d_blend_w[c], compose down the hierarchy (Eq. 1) and multiply by the inverse
+ * bind.  d_time, d_blend_w: device [n_chars] float; d_skin: device
+ * [total][12] float (written).  One persistent launch plus a small
+ * work-queue launch on `stream`. */
+ANIM_API int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
+                        float *d_skin, void *stream);
+
+/* The two launches of anim_evaluate_frame, for callers that schedule them
+ * apart (e.g. to time the persistent kernel alone): build_queue buckets the
+ * characters by (type, key index) into the plan's work queue from d_time;
+ * run_queue is the persistent frame kernel consuming that queue.  run_queue
+ * must follow a build_queue with the same d_time in stream order. */
+ANIM_API int anim_frame_build_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_time, void *stream);
+ANIM_API int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
+                                  float *d_skin, void *stream);
+
+/* The same frame computed by the plain comparator: one CTA per character,
+ * one launch per skeleton type, one barrier per tree level (the
+ * level-synchronous schedule).  Same arguments and results. */
+ANIM_API int anim_evaluate_frame_levelsync(anim_ctx *ctx, const anim_plan *plan, const float *d_time,
+                                  const float *d_blend_w, float *d_skin, void *stream);
+
+/* Hierarchy-Scan (Eq. 1) + Bind from given local poses: d_q [total][4]
+ * (unnormalized allowed, normalized internally), d_t [total][3].  Writes
+ * d_skin [total][12] and/or d_model [total][12] (either may be NULL, not
+ * both). */
+ANIM_API int anim_forward_local(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t, float *d_skin,
+                       float *d_model, void *stream);
+
+/* Level-synchronous comparator of anim_forward_local (skin output only). */
+ANIM_API int anim_forward_local_levelsync(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t,
+                                 float *d_skin, void *stream);
+
+/* Adjoint of anim_forward_local's model positions p_j (translation column
+ * of M_j): given d_grad_pos [total][3] = dLoss/dp, writes d_grad_q [total][4]
+ * (w.r.t. the unnormalized q) and d_grad_t [total][3].  The forward pass is
+ * recomputed inside the kernel; nothing is stored between the calls.
+ * Rigid poses only (unit quaternion rotations, unit scale). */
+ANIM_API int anim_backward(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t,
+                  const float *d_grad_pos, float *d_grad_q, float *d_grad_t, void *stream);
+
+/* Fused forward + adjoint of the loss sum_j |p_j - target_j|^2: d_target
+ * [total][3]; writes d_grad_q, d_grad_t and, if d_loss != NULL, each
+ * character's loss d_loss[n_chars]. */
+ANIM_API int anim_loss_backward(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t,
+                       const float *d_target, float *d_grad_q, float *d_grad_t, float *d_loss, void *stream);
+
+/* Batched IK: n_eff effector joints per type (host [n_types_of_ctx][n_eff],
+ * entries for types the plan does not use are ignored).  The IK object owns
+ * the active-subtree tables and a device step counter. */
+ANIM_API int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_t *effectors, anim_ik **out);
+ANIM_API int anim_ik_destroy(anim_ctx *ctx, anim_ik *ik);
+
+/* Reset the IK step counter to 0 (asynchronous on stream). */
+ANIM_API int anim_ik_reset(anim_ctx *ctx, anim_ik *ik, void *stream);
+
+/* One IK step, all in one kernel: forward over the effectors' ancestors,
+ * loss sum_e |p_e - target_e|^2, adjoint, and an Adam update (PyTorch's
+ * definition, step counter kept on the device and incremented) of d_q,
+ * d_m, d_v ([total][4], updated in place).  d_t [total][3] fixed;
+ * d_targets [n_chars][n_eff][3]; d_loss[n_chars] (nullable) receives each
+ * character's loss before the update. */
+ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v, const float *d_t,
+                 const float *d_targets, float lr, float beta1, float beta2, float eps, float *d_loss,
+                 void *stream);
+
+/* Autotune the schedule (segment length, characters per CTA, CTA size) for
+ * the plan's type mix by timing candidate launches of `which` (0 = fused
+ * frame, 1 = forward_local, 2 = loss_backward) on scratch buffers; the result
+ * is cached per (types, counts) hash in the context.  Synchronous; not
+ * capturable.  Needs clips for which = 0. */
+ANIM_API int anim_tune(anim_ctx *ctx, anim_plan *plan, int which);
+
+/* Read and clear the device status word (synchronizes `stream`). */
+ANIM_API int anim_get_status(anim_ctx *ctx, void *stream, int *out_status);
+
+/* Host-only skeleton analysis (no GPU needed): the segment decomposition the
+ * scan uses for a maximum segment length seg_len.  Outputs: *out_nseg,
+ * out_seg_start[nseg+1] (caller provides n+1 entries), *out_rounds (pointer
+ * jumping rounds over segments), *out_depth (tree depth, root = 1). */
+ANIM_API int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, int32_t *out_nseg,
+                          int32_t *out_seg_start, int32_t *out_rounds, int32_t *out_depth);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+ANIM_API int anim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANIM_H */

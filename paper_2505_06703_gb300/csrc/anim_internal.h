@@ -1,0 +1,150 @@
+// Internal declarations shared by the host runtime (host.cu) and the kernel
+// translation units.  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace anim {
+
+// Per-type device tables (all pointers are device memory owned by the
+// context).  The joint order is the caller's order; the scan works on
+// "segments": maximal runs of consecutive joints i, i+1, ... with
+// parent[i+1] == i (natural chains), cut into pieces of at most seg_len
+// joints.  Segments partition [0, n) into intervals.
+struct TypeDev {
+  int n;           // joints
+  int nseg;        // segments
+  int rounds;      // pointer-jumping rounds over the segment tree
+  int max_depth;   // tree depth (root = 1)
+  int n_clips;     // 0 if no clips uploaded
+  int n_keys;
+  float rate;
+  int pad0;
+  const int32_t *parent;     // [n]
+  const int32_t *depth;      // [n]
+  const int32_t *seg_start;  // [nseg + 1]
+  const uint16_t *seg_of;    // [n]
+  const int32_t *seg_link;   // [nseg]  parent joint of the segment's first joint, -1 for roots
+  const int16_t *jump;       // [rounds][nseg] parent segment at the start of each round, -1 when done
+  const float4 *inv_bind;    // [n][3] rows of B_i
+  const float4 *keys;        // [n_clips][n_keys][n][2]: (qx qy qz qw), (tx ty tz theta)
+  // adjoint: depth-first pre-order of the joints (subtrees are contiguous)
+  const int32_t *dfs;        // [n] joint at pre-order slot i
+  const int32_t *dfs_slot;   // [n] slot of joint j
+  const int32_t *sub_end;    // [n] slot one past the subtree of the joint at slot i
+  // IK views: the active subtree of a type; view joint j reads row gather[j]
+  // of the full type (nullptr = identity).
+  const int32_t *gather;
+};
+
+// One unit of work: `count` characters of one type.  For the frame the
+// characters share the key index k0 (so they read the same key records).
+struct WorkItem {
+  int32_t start;  // index into the item character list
+  int32_t count;
+  int32_t type;
+  int32_t k0;
+};
+
+struct LaunchCfg {
+  int threads;       // CTA size
+  int ctas;          // persistent grid size
+  size_t smem;       // dynamic shared memory per CTA (bytes)
+};
+
+// ---------------------------------------------------------------- kernels
+// Fused persistent scan.  mode: 0 = sampled frame (keys), 1 = local poses (q,t).
+struct ScanArgs {
+  const TypeDev *types;
+  const WorkItem *items;
+  const int32_t *n_items_dev;  // device count (frame) or nullptr (use n_items)
+  int n_items;
+  const int32_t *item_chars;   // character ids referenced by items
+  const int64_t *row_off;      // [n_chars + 1]
+  int *queue_head;             // device counter, reset to 0 before the launch
+  int *status;
+  // sampled mode
+  const float *time;
+  const float *blend_w;
+  // local-pose mode
+  const float *q;
+  const float *t;
+  // outputs
+  float *skin;
+  float *model;
+  int C_max_unused;
+};
+
+cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+
+// Frame work queue: bucket characters by (type, key index k0) into items of
+// at most cap[type] characters; types are laid out most costly first so the
+// persistent kernel takes the longest items first.
+struct BucketArgs {
+  int64_t n_chars;
+  const int32_t *char_type;   // [n_chars]
+  const float *time;          // [n_chars]
+  const TypeDev *types;       // context types (rate, n_keys)
+  int n_types;                // size of the context type table
+  int n_used;
+  const int32_t *used;        // [n_used] type ids, most costly first
+  const int32_t *cap;         // [n_types] characters per item
+  int32_t *sorted;            // [n_chars] character ids grouped by bin
+  WorkItem *items;            // [n_chars + n_bins]
+  int32_t *n_items;           // [1]
+  int *queue_head;            // [1] reset to 0
+  int *status;
+};
+constexpr int kMaxBins = 3584;
+constexpr int kMaxTypes = 512;
+cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s);
+
+// Plain level-synchronous comparator: one CTA per character of one type.
+struct LevelArgs {
+  TypeDev type;
+  const int32_t *chars;  // characters of this type
+  int n_chars;
+  const int64_t *row_off;
+  const float *time, *blend_w;
+  const float *q, *t;
+  float *skin;
+  int *status;
+};
+cudaError_t launch_levelsync(int mode, const LevelArgs &a, int threads, cudaStream_t s);
+
+// Adjoint.  mode: 0 = grad_pos given, 1 = loss vs targets, 2 = IK step.
+struct AdjointArgs {
+  const TypeDev *types;
+  const WorkItem *items;
+  int n_items;
+  const int32_t *item_chars;
+  const int64_t *row_off;
+  int *queue_head;
+  int *status;
+  const float *q, *t;
+  const float *grad_pos;   // mode 0
+  const float *target;     // mode 1: [total][3]; mode 2: [n_chars][n_eff][3]
+  float *grad_q, *grad_t;  // modes 0, 1
+  float *loss;             // per character, nullable
+  // IK (mode 2): types are active-subtree views (TypeDev::gather maps view
+  // joints to rows of the full type); effectors are view joint ids.
+  const int32_t *eff_slot;       // [n_types][n_eff] view joint ids
+  int n_eff;
+  float *m, *v;
+  float *q_mut;
+  int *step;         // device step counter (read at start, incremented by the last CTA)
+  int *done_ctas;    // device counter for the last-CTA increment
+  float lr, beta1, beta2, eps;
+};
+cudaError_t launch_adjoint(int mode, const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+
+// Setup kernels.
+cudaError_t launch_prepare_keys(float4 *keys, int n_clips, int n_keys, int n, cudaStream_t s);
+cudaError_t launch_bind_from_rest(const int32_t *parent, const float *rest_q, const float *rest_t, int n,
+                                  float4 *inv_bind, cudaStream_t s);
+
+// Shared-memory footprint of one work item of C characters (bytes).
+size_t scan_smem_bytes(int n, int nseg, int C);
+size_t adjoint_smem_bytes(int n, int nseg, int C);
+
+}  // namespace anim

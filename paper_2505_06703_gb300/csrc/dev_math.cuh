@@ -1,0 +1,174 @@
+// Device helpers: 3x4 affine transforms, quaternions, slerp, fast integer
+// division, and the bulk-copy (TMA, non-tensor) PTX used to stream skin
+// matrices out of shared memory.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace anim {
+
+// A 3x4 row-major affine [R | t] held as three float4 rows.
+struct Aff {
+  float4 r0, r1, r2;
+};
+
+__device__ __forceinline__ Aff aff_identity() {
+  Aff a;
+  a.r0 = make_float4(1.f, 0.f, 0.f, 0.f);
+  a.r1 = make_float4(0.f, 1.f, 0.f, 0.f);
+  a.r2 = make_float4(0.f, 0.f, 1.f, 0.f);
+  return a;
+}
+
+// One output row of A*B: row = a.x*B.r0 + a.y*B.r1 + a.z*B.r2 + (0,0,0,a.w).
+__device__ __forceinline__ float4 aff_row(const float4 a, const Aff &B) {
+  float4 r;
+  r.x = fmaf(a.x, B.r0.x, fmaf(a.y, B.r1.x, a.z * B.r2.x));
+  r.y = fmaf(a.x, B.r0.y, fmaf(a.y, B.r1.y, a.z * B.r2.y));
+  r.z = fmaf(a.x, B.r0.z, fmaf(a.y, B.r1.z, a.z * B.r2.z));
+  r.w = fmaf(a.x, B.r0.w, fmaf(a.y, B.r1.w, fmaf(a.z, B.r2.w, a.w)));
+  return r;
+}
+
+// Product of 3x4 affines (as 4x4 with last row 0 0 0 1): C = A B.
+__device__ __forceinline__ Aff aff_mul(const Aff &A, const Aff &B) {
+  Aff C;
+  C.r0 = aff_row(A.r0, B);
+  C.r1 = aff_row(A.r1, B);
+  C.r2 = aff_row(A.r2, B);
+  return C;
+}
+
+// L = [R(q) | t] for a unit quaternion q = (x, y, z, w).
+__device__ __forceinline__ Aff aff_from_qt(const float4 q, const float tx, const float ty, const float tz) {
+  const float x2 = q.x + q.x, y2 = q.y + q.y, z2 = q.z + q.z;
+  const float xx = q.x * x2, yy = q.y * y2, zz = q.z * z2;
+  const float xy = q.x * y2, xz = q.x * z2, yz = q.y * z2;
+  const float wx = q.w * x2, wy = q.w * y2, wz = q.w * z2;
+  Aff a;
+  a.r0 = make_float4(1.f - (yy + zz), xy - wz, xz + wy, tx);
+  a.r1 = make_float4(xy + wz, 1.f - (xx + zz), yz - wx, ty);
+  a.r2 = make_float4(xz - wy, yz + wx, 1.f - (xx + yy), tz);
+  return a;
+}
+
+__device__ __forceinline__ float dot4(const float4 a, const float4 b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+__device__ __forceinline__ float4 normalize4(const float4 a) {
+  const float s = rsqrtf(dot4(a, a));
+  return make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+}
+
+// Weighted sum w0*a + w1*b followed by normalization.
+__device__ __forceinline__ float4 combine_norm(const float4 a, const float4 b, const float w0, const float w1) {
+  float4 r;
+  r.x = fmaf(w0, a.x, w1 * b.x);
+  r.y = fmaf(w0, a.y, w1 * b.y);
+  r.z = fmaf(w0, a.z, w1 * b.z);
+  r.w = fmaf(w0, a.w, w1 * b.w);
+  return normalize4(r);
+}
+
+// Slerp between adjacent keys whose arc angle theta (in [0, pi/2], angle of
+// the shorter arc) was computed once at upload.  The 1/sin(theta) factor of
+// the slerp weights is dropped because the result is normalized; below
+// theta = 1e-6 the weights fall back to (1 - alpha, alpha).
+__device__ __forceinline__ float4 slerp_pre(const float4 a, const float4 b, const float theta, const float alpha) {
+  const float sgn = dot4(a, b) < 0.f ? -1.f : 1.f;
+  float w0, w1;
+  if (theta > 1e-6f) {
+    w0 = __sinf((1.f - alpha) * theta);
+    w1 = __sinf(alpha * theta);
+  } else {
+    w0 = 1.f - alpha;
+    w1 = alpha;
+  }
+  return combine_norm(a, b, w0, w1 * sgn);
+}
+
+// Slerp between two unit quaternions (shorter arc); angle from acos of the
+// clamped |dot|.
+__device__ __forceinline__ float4 slerp_unit(const float4 a, const float4 b, const float alpha) {
+  const float d = dot4(a, b);
+  const float sgn = d < 0.f ? -1.f : 1.f;
+  const float ad = fminf(fabsf(d), 1.f);
+  const float theta = acosf(ad);
+  float w0, w1;
+  if (theta > 1e-6f) {
+    w0 = __sinf((1.f - alpha) * theta);
+    w1 = __sinf(alpha * theta);
+  } else {
+    w0 = 1.f - alpha;
+    w1 = alpha;
+  }
+  return combine_norm(a, b, w0, w1 * sgn);
+}
+
+// Hamilton product a (x) b, quaternions stored (x, y, z, w).
+__device__ __forceinline__ float4 qmul(const float4 a, const float4 b) {
+  float4 r;
+  r.x = a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y;
+  r.y = a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x;
+  r.z = a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w;
+  r.w = a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z;
+  return r;
+}
+
+// Shared-memory float4 row access of an Aff stored as 3 consecutive float4.
+__device__ __forceinline__ Aff lds_aff(const float4 *p) {
+  Aff a;
+  a.r0 = p[0];
+  a.r1 = p[1];
+  a.r2 = p[2];
+  return a;
+}
+__device__ __forceinline__ void sts_aff(float4 *p, const Aff &a) {
+  p[0] = a.r0;
+  p[1] = a.r1;
+  p[2] = a.r2;
+}
+__device__ __forceinline__ Aff ldg_aff(const float4 *p) {
+  Aff a;
+  a.r0 = __ldg(p);
+  a.r1 = __ldg(p + 1);
+  a.r2 = __ldg(p + 2);
+  return a;
+}
+__device__ __forceinline__ void stg_aff(float4 *p, const Aff &a) {
+  p[0] = a.r0;
+  p[1] = a.r1;
+  p[2] = a.r2;
+}
+
+// Division by a runtime divisor d >= 1 for numerators below 2^31
+// (multiply-high method: q = (umulhi(x, m) + x) >> s).
+struct FastDiv {
+  uint32_t d, m, s;
+  __host__ __device__ void init(uint32_t dd) {
+    d = dd;
+    s = 0;
+    while ((1u << s) < dd) ++s;
+    const uint64_t two32 = 1ull << 32;
+    m = (uint32_t)((two32 * ((1ull << s) - dd)) / dd + 1);
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t x) const { return (__umulhi(x, m) + x) >> s; }
+};
+
+// ---- bulk copy shared -> global (cp.async.bulk, bulk-group completion)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+}  // namespace anim

@@ -1,0 +1,970 @@
+// Host runtime behind the C ABI (include/anim.h): context, skeleton analysis
+// (segments for the scan, depth-first order for the adjoint), device tables,
+// plans and work items, kernel launches, IK state, autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/anim.h"
+#include "anim_internal.h"
+
+using namespace anim;
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kAdjThreads = 256;
+constexpr int kCMax = 64;
+constexpr int kTargetJointsPerItem = 2048;
+thread_local std::string g_create_error;
+
+// ------------------------------------------------------------ analysis
+struct Segments {
+  int nseg = 0, rounds = 0;
+  std::vector<int32_t> start, link;
+  std::vector<uint16_t> seg_of;
+  std::vector<int16_t> jump;  // [rounds][nseg]
+};
+
+// Segments: maximal runs of consecutive joints where each joint's parent is
+// the previous joint (natural chains), each cut into ceil(m / seg_len)
+// pieces of nearly equal length.  Then the pointer-jumping tables over the
+// segment tree: jump[0][g] = segment of the joint g hangs from, and
+// jump[r+1][g] = jump[r][jump[r][g]], until every pointer is -1.
+Segments analyze_segments(const std::vector<int32_t> &par, int seg_len) {
+  Segments S;
+  const int n = (int)par.size();
+  std::vector<int> chain_starts;
+  for (int i = 0; i < n; ++i)
+    if (i == 0 || par[i] != i - 1) chain_starts.push_back(i);
+  chain_starts.push_back(n);
+  for (size_t c = 0; c + 1 < chain_starts.size(); ++c) {
+    const int a = chain_starts[c], b = chain_starts[c + 1], m = b - a;
+    const int pieces = (m + seg_len - 1) / seg_len;
+    for (int p = 0; p < pieces; ++p) S.start.push_back(a + (int)((long long)m * p / pieces));
+  }
+  S.nseg = (int)S.start.size();
+  S.start.push_back(n);
+  S.seg_of.resize(n);
+  for (int g = 0; g < S.nseg; ++g)
+    for (int j = S.start[g]; j < S.start[g + 1]; ++j) S.seg_of[j] = (uint16_t)g;
+  S.link.resize(S.nseg);
+  std::vector<int> ptr(S.nseg);
+  for (int g = 0; g < S.nseg; ++g) {
+    S.link[g] = par[S.start[g]];
+    ptr[g] = S.link[g] < 0 ? -1 : S.seg_of[S.link[g]];
+  }
+  for (;;) {
+    bool any = false;
+    for (int g = 0; g < S.nseg; ++g) any |= ptr[g] >= 0;
+    if (!any) break;
+    for (int g = 0; g < S.nseg; ++g) S.jump.push_back((int16_t)ptr[g]);
+    std::vector<int> nxt(S.nseg);
+    for (int g = 0; g < S.nseg; ++g) nxt[g] = ptr[g] < 0 ? -1 : ptr[ptr[g]];
+    ptr.swap(nxt);
+    ++S.rounds;
+  }
+  return S;
+}
+
+struct DfsOrder {
+  std::vector<int32_t> dfs, slot, sub_end;
+};
+
+// Depth-first pre-order (children in index order): every subtree occupies
+// the contiguous slot range [slot(j), sub_end[slot(j)]).
+DfsOrder analyze_dfs(const std::vector<int32_t> &par) {
+  const int n = (int)par.size();
+  std::vector<std::vector<int>> kids(n);
+  std::vector<int> roots;
+  for (int i = 0; i < n; ++i) (par[i] < 0 ? roots : kids[par[i]]).push_back(i);
+  DfsOrder D;
+  D.dfs.reserve(n);
+  std::vector<int> st(roots.rbegin(), roots.rend());
+  while (!st.empty()) {
+    const int u = st.back();
+    st.pop_back();
+    D.dfs.push_back(u);
+    for (auto it = kids[u].rbegin(); it != kids[u].rend(); ++it) st.push_back(*it);
+  }
+  D.slot.resize(n);
+  for (int i = 0; i < n; ++i) D.slot[D.dfs[i]] = i;
+  std::vector<int> size(n, 1);
+  for (int j = n - 1; j >= 0; --j)
+    if (par[j] >= 0) size[par[j]] += size[j];
+  D.sub_end.resize(n);
+  for (int i = 0; i < n; ++i) D.sub_end[i] = i + size[D.dfs[i]];
+  return D;
+}
+
+int validate_parents(const int32_t *p, int n) {
+  for (int i = 0; i < n; ++i)
+    if (p[i] < -1 || p[i] >= i) return i;
+  return -1;
+}
+
+std::vector<int32_t> depths_of(const std::vector<int32_t> &par) {
+  std::vector<int32_t> d(par.size());
+  for (size_t i = 0; i < par.size(); ++i) d[i] = par[i] < 0 ? 1 : d[par[i]] + 1;
+  return d;
+}
+
+int default_seg_len(int n) { return n > 1024 ? 16 : 8; }
+
+// ------------------------------------------------------------ device blocks
+struct DevBlock {
+  void *ptr = nullptr;
+  size_t used = 0, cap = 0;
+  ~DevBlock() {
+    if (ptr) cudaFree(ptr);
+  }
+};
+
+// One device allocation holding several host vectors, each 256-byte aligned.
+struct BlockBuilder {
+  std::vector<std::pair<const void *, size_t>> parts;
+  size_t total = 0;
+  std::vector<size_t> offs;
+  size_t add(const void *p, size_t bytes) {
+    total = (total + 255) & ~(size_t)255;
+    offs.push_back(total);
+    parts.push_back({p, bytes});
+    total += bytes;
+    return offs.back();
+  }
+  cudaError_t upload(void **dev) {
+    std::vector<char> host(std::max<size_t>(total, 1));
+    for (size_t k = 0; k < parts.size(); ++k)
+      if (parts[k].second) memcpy(host.data() + offs[k], parts[k].first, parts[k].second);
+    cudaError_t e = cudaMalloc(dev, std::max<size_t>(total, 16));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dev, host.data(), total, cudaMemcpyHostToDevice);
+  }
+};
+
+// A skeleton type (or an IK view of one): host analysis + device tables.
+struct TypeHost {
+  int n = 0, max_depth = 0, seg_len = 8;
+  std::vector<int32_t> parent, depth;
+  Segments seg;
+  DfsOrder dfsord;
+  void *d_tables = nullptr;  // parent, depth, segments, dfs, gather
+  float4 *d_inv_bind = nullptr;
+  float4 *d_keys = nullptr;
+  int n_clips = 0, n_keys = 0;
+  float rate = 0.f;
+  std::vector<int32_t> gather;  // IK views only
+  TypeDev dev{};
+  ~TypeHost() {
+    if (d_tables) cudaFree(d_tables);
+    if (d_inv_bind) cudaFree(d_inv_bind);
+    if (d_keys) cudaFree(d_keys);
+  }
+  cudaError_t build_tables() {
+    seg = analyze_segments(parent, seg_len);
+    dfsord = analyze_dfs(parent);
+    if (d_tables) {
+      cudaFree(d_tables);
+      d_tables = nullptr;
+    }
+    BlockBuilder B;
+    const size_t o_par = B.add(parent.data(), parent.size() * 4);
+    const size_t o_dep = B.add(depth.data(), depth.size() * 4);
+    const size_t o_ss = B.add(seg.start.data(), seg.start.size() * 4);
+    const size_t o_so = B.add(seg.seg_of.data(), seg.seg_of.size() * 2);
+    const size_t o_sl = B.add(seg.link.data(), seg.link.size() * 4);
+    const size_t o_j = B.add(seg.jump.data(), seg.jump.size() * 2);
+    const size_t o_d = B.add(dfsord.dfs.data(), dfsord.dfs.size() * 4);
+    const size_t o_ds = B.add(dfsord.slot.data(), dfsord.slot.size() * 4);
+    const size_t o_se = B.add(dfsord.sub_end.data(), dfsord.sub_end.size() * 4);
+    const size_t o_g = B.add(gather.data(), gather.size() * 4);
+    void *d = nullptr;
+    cudaError_t e = B.upload(&d);
+    if (e != cudaSuccess) {
+      if (d) cudaFree(d);
+      return e;
+    }
+    d_tables = d;
+    char *base = (char *)d;
+    dev.n = n;
+    dev.nseg = seg.nseg;
+    dev.rounds = seg.rounds;
+    dev.max_depth = max_depth;
+    dev.parent = (const int32_t *)(base + o_par);
+    dev.depth = (const int32_t *)(base + o_dep);
+    dev.seg_start = (const int32_t *)(base + o_ss);
+    dev.seg_of = (const uint16_t *)(base + o_so);
+    dev.seg_link = (const int32_t *)(base + o_sl);
+    dev.jump = (const int16_t *)(base + o_j);
+    dev.dfs = (const int32_t *)(base + o_d);
+    dev.dfs_slot = (const int32_t *)(base + o_ds);
+    dev.sub_end = (const int32_t *)(base + o_se);
+    dev.gather = gather.empty() ? nullptr : (const int32_t *)(base + o_g);
+    sync_dev();
+    return cudaSuccess;
+  }
+  void sync_dev() {
+    dev.n_clips = n_clips;
+    dev.n_keys = n_keys;
+    dev.rate = rate;
+    dev.inv_bind = d_inv_bind;
+    dev.keys = d_keys;
+  }
+};
+
+struct Sched {
+  int C = 1;  // characters per item
+};
+
+}  // namespace
+
+// ------------------------------------------------------------ ABI objects
+struct anim_plan {
+  anim_ctx *ctx = nullptr;
+  int64_t n_chars = 0;
+  std::vector<int32_t> char_type;
+  std::vector<int64_t> row_off;
+  std::vector<int> used;                      // type ids, most costly first
+  std::vector<std::vector<int32_t>> by_type;  // characters of each used type (indexed like used)
+  std::vector<int> C_scan, C_adj;             // per ctx type id
+  int64_t total = 0;
+  int version = -1;  // schedule version the items were built for
+  // device
+  int32_t *d_char_type = nullptr;
+  int64_t *d_row_off = nullptr;
+  int32_t *d_type_chars = nullptr;  // characters grouped by type in `used` order
+  std::vector<int> type_chars_start;
+  WorkItem *d_items_scan = nullptr, *d_items_adj = nullptr;
+  int n_items_scan = 0, n_items_adj = 0;
+  int32_t *d_sorted = nullptr;
+  WorkItem *d_items_frame = nullptr;
+  int32_t *d_n_items = nullptr;
+  int *d_queue = nullptr;
+  int32_t *d_used = nullptr, *d_cap = nullptr;
+  LaunchCfg cfg_scan{}, cfg_adj{};
+  size_t smem_frame = 0;
+  ~anim_plan() {
+    for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
+                    (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_n_items,
+                    (void *)d_queue, (void *)d_used, (void *)d_cap})
+      if (p) cudaFree(p);
+  }
+};
+
+struct anim_ik {
+  anim_ctx *ctx = nullptr;
+  const anim_plan *plan = nullptr;
+  int n_eff = 0;
+  std::vector<std::unique_ptr<TypeHost>> views;  // indexed by ctx type id (null if unused)
+  TypeDev *d_views = nullptr;
+  int32_t *d_eff = nullptr;
+  WorkItem *d_items = nullptr;
+  int n_items = 0;
+  int *d_counters = nullptr;  // [0] queue, [1] step, [2] done
+  LaunchCfg cfg{};
+  ~anim_ik() {
+    for (void *p : {(void *)d_views, (void *)d_eff, (void *)d_items, (void *)d_counters})
+      if (p) cudaFree(p);
+  }
+};
+
+struct anim_ctx {
+  int device = 0;
+  int sm_count = 0;
+  size_t smem_optin = 0, smem_per_sm = 0;
+  std::string err;
+  std::vector<std::unique_ptr<TypeHost>> types;
+  TypeDev *d_types = nullptr;
+  int *d_status = nullptr;
+  int version = 0;  // bumps when types/schedules change
+  int ctas_per_sm = 2;
+  std::set<anim_plan *> plans;
+  std::set<anim_ik *> iks;
+  std::map<uint64_t, std::vector<int>> tune_cache;  // (types, counts) hash -> per-type seg_len
+  ~anim_ctx() {
+    for (auto *p : plans) delete p;
+    for (auto *k : iks) delete k;
+    if (d_types) cudaFree(d_types);
+    if (d_status) cudaFree(d_status);
+  }
+};
+
+namespace {
+
+int fail(anim_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx)
+    ctx->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                                       \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return fail(ctx, ANIM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
+
+cudaError_t upload_types(anim_ctx *ctx) {
+  std::vector<TypeDev> host(ctx->types.size());
+  for (size_t t = 0; t < ctx->types.size(); ++t) {
+    ctx->types[t]->sync_dev();
+    host[t] = ctx->types[t]->dev;
+  }
+  if (ctx->d_types) cudaFree(ctx->d_types);
+  ctx->d_types = nullptr;
+  cudaError_t e = cudaMalloc(&ctx->d_types, std::max<size_t>(1, host.size()) * sizeof(TypeDev));
+  if (e != cudaSuccess) return e;
+  ++ctx->version;
+  return cudaMemcpy(ctx->d_types, host.data(), host.size() * sizeof(TypeDev), cudaMemcpyHostToDevice);
+}
+
+size_t smem_budget(const anim_ctx *ctx) {
+  // two resident CTAs per SM; keep 1 KB per CTA for the runtime and the
+  // kernels' static shared memory
+  const size_t per = ctx->smem_per_sm / (size_t)ctx->ctas_per_sm;
+  return std::min(ctx->smem_optin, per) - 3072;
+}
+
+int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
+  const size_t budget = smem_budget(ctx);
+  int C = std::max(1, std::min(kCMax, kTargetJointsPerItem / std::max(1, T.n)));
+  auto bytes = [&](int c) {
+    return adjoint ? adjoint_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
+  };
+  while (C > 1 && bytes(C) > budget) --C;
+  if (bytes(C) > std::min(ctx->smem_optin - 3072, (size_t)227 * 1024)) return 0;
+  return C;
+}
+
+template <class T>
+cudaError_t upload_vec(T **dev, const std::vector<T> &v) {
+  if (*dev) cudaFree(*dev);
+  *dev = nullptr;
+  cudaError_t e = cudaMalloc((void **)dev, std::max<size_t>(1, v.size()) * sizeof(T));
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpy(*dev, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Work items (C characters of one type) in `used` order; start indexes the
+// type-grouped character list.
+std::vector<WorkItem> make_items(const anim_plan *P, const std::vector<int> &Cv) {
+  std::vector<WorkItem> items;
+  for (size_t u = 0; u < P->used.size(); ++u) {
+    const int t = P->used[u];
+    const int cnt = (int)P->by_type[u].size(), C = Cv[t];
+    for (int k = 0; k < cnt; k += C) {
+      WorkItem w;
+      w.start = P->type_chars_start[u] + k;
+      w.count = std::min(C, cnt - k);
+      w.type = t;
+      w.k0 = 0;
+      items.push_back(w);
+    }
+  }
+  return items;
+}
+
+// (Re)build the schedule-dependent parts of a plan: characters per item,
+// static items, launch configurations.
+int plan_schedule(anim_ctx *ctx, anim_plan *P) {
+  if (P->version == ctx->version) return ANIM_OK;
+  const int nt = (int)ctx->types.size();
+  P->C_scan.assign(nt, 1);
+  P->C_adj.assign(nt, 1);
+  size_t smem_s = 0, smem_a = 0;
+  for (int t : P->used) {
+    const TypeHost &T = *ctx->types[t];
+    const int cs = choose_C(ctx, T, false), ca = choose_C(ctx, T, true);
+    if (cs == 0 || ca == 0)
+      return fail(ctx, ANIM_EUNSUPPORTED,
+                  "type %d (%d joints, %d segments) does not fit in shared memory with one character", t, T.n,
+                  T.seg.nseg);
+    P->C_scan[t] = cs;
+    P->C_adj[t] = ca;
+    smem_s = std::max(smem_s, scan_smem_bytes(T.n, T.seg.nseg, cs));
+    smem_a = std::max(smem_a, adjoint_smem_bytes(T.n, T.seg.nseg, ca));
+  }
+  auto is = make_items(P, P->C_scan), ia = make_items(P, P->C_adj);
+  P->n_items_scan = (int)is.size();
+  P->n_items_adj = (int)ia.size();
+  CK(upload_vec(&P->d_items_scan, is));
+  CK(upload_vec(&P->d_items_adj, ia));
+  CK(upload_vec(&P->d_cap, P->C_scan));
+  const int grid = ctx->sm_count * ctx->ctas_per_sm;
+  P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16)};
+  P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
+  P->smem_frame = std::max<size_t>(smem_s, 16);
+  P->version = ctx->version;
+  return ANIM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int anim_version(void) { return 10000; }
+
+const char *anim_last_error(const anim_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int anim_create(anim_ctx **out, int device) {
+  anim_ctx *ctx = nullptr;
+  if (!out) return fail(nullptr, ANIM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(nullptr, ANIM_EDEVICE, "no CUDA device");
+  if (device < 0 || device >= ndev) return fail(nullptr, ANIM_EINVAL, "device %d out of range", device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return fail(nullptr, ANIM_ECUDA, "device query failed");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(nullptr, ANIM_EDEVICE, "device %d is sm_%d%d; this library is built for sm_103a", device, prop.major,
+                prop.minor);
+  if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, ANIM_ECUDA, "cudaSetDevice failed");
+  ctx = new (std::nothrow) anim_ctx();
+  if (!ctx) return fail(nullptr, ANIM_ENOMEM, "out of host memory");
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  ctx->smem_per_sm = prop.sharedMemPerMultiprocessor;
+  if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+    delete ctx;
+    return fail(nullptr, ANIM_ENOMEM, "device allocation failed");
+  }
+  *out = ctx;
+  return ANIM_OK;
+}
+
+int anim_destroy(anim_ctx *ctx) {
+  if (!ctx) return ANIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  delete ctx;
+  return ANIM_OK;
+}
+
+int anim_create_skeletons(anim_ctx *ctx, int n_types, const int32_t *joint_counts, const int32_t *parents,
+                          const float *inv_bind, const float *rest_q, const float *rest_t, int32_t *out_type_ids) {
+  if (!ctx) return ANIM_EINVAL;
+  if (n_types <= 0 || !joint_counts || !parents || !out_type_ids)
+    return fail(ctx, ANIM_EINVAL, "n_types must be > 0 and joint_counts, parents, out_type_ids non-NULL");
+  if (!inv_bind && (!rest_q || !rest_t)) return fail(ctx, ANIM_EINVAL, "inv_bind is NULL: rest_q and rest_t are required");
+  if ((int)ctx->types.size() + n_types > kMaxTypes) return fail(ctx, ANIM_EUNSUPPORTED, "more than %d types", kMaxTypes);
+  CK(cudaSetDevice(ctx->device));
+  int64_t off = 0;
+  for (int t = 0; t < n_types; ++t) {
+    const int n = joint_counts[t];
+    if (n < 1 || n > ANIM_MAX_JOINTS) return fail(ctx, ANIM_EINVAL, "type %d: joint count %d not in [1, %d]", t, n, ANIM_MAX_JOINTS);
+    const int bad = validate_parents(parents + off, n);
+    if (bad >= 0)
+      return fail(ctx, ANIM_EINVAL, "type %d: parent[%d] = %d violates -1 <= parent[i] < i", t, bad, parents[off + bad]);
+    off += n;
+  }
+  off = 0;
+  const int first = (int)ctx->types.size();
+  for (int t = 0; t < n_types; ++t) {
+    const int n = joint_counts[t];
+    auto T = std::make_unique<TypeHost>();
+    T->n = n;
+    T->parent.assign(parents + off, parents + off + n);
+    T->depth = depths_of(T->parent);
+    T->max_depth = *std::max_element(T->depth.begin(), T->depth.end());
+    T->seg_len = default_seg_len(n);
+    CK(T->build_tables());
+    CK(cudaMalloc(&T->d_inv_bind, (size_t)n * 48));
+    if (inv_bind) {
+      CK(cudaMemcpy(T->d_inv_bind, inv_bind + off * 12, (size_t)n * 48, cudaMemcpyHostToDevice));
+    } else {
+      float *dq = nullptr, *dt = nullptr;
+      CK(cudaMalloc(&dq, (size_t)n * 16));
+      if (cudaMalloc(&dt, (size_t)n * 12) != cudaSuccess) {
+        cudaFree(dq);
+        return fail(ctx, ANIM_ENOMEM, "device allocation failed");
+      }
+      cudaError_t e = cudaMemcpy(dq, rest_q + off * 4, (size_t)n * 16, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(dt, rest_t + off * 3, (size_t)n * 12, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = launch_bind_from_rest(T->dev.parent, dq, dt, n, T->d_inv_bind, 0);
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      cudaFree(dq);
+      cudaFree(dt);
+      if (e != cudaSuccess) return fail(ctx, ANIM_ECUDA, "inverse bind from rest pose: %s", cudaGetErrorString(e));
+    }
+    T->sync_dev();
+    ctx->types.push_back(std::move(T));
+    off += n;
+  }
+  CK(upload_types(ctx));
+  for (int t = 0; t < n_types; ++t) out_type_ids[t] = first + t;
+  return ANIM_OK;
+}
+
+int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, float rate_hz, const float *keys) {
+  if (!ctx) return ANIM_EINVAL;
+  if (type_id < 0 || type_id >= (int)ctx->types.size()) return fail(ctx, ANIM_EINVAL, "type id %d unknown", type_id);
+  if (n_clips < 1 || n_clips > 2) return fail(ctx, ANIM_EINVAL, "n_clips must be 1 or 2");
+  if (n_keys < 2 || n_keys > ANIM_MAX_KEYS) return fail(ctx, ANIM_EINVAL, "n_keys must be in [2, %d]", ANIM_MAX_KEYS);
+  if (!(rate_hz > 0.f) || !std::isfinite(rate_hz)) return fail(ctx, ANIM_EINVAL, "rate_hz must be finite and > 0");
+  if (!keys) return fail(ctx, ANIM_EINVAL, "keys is NULL");
+  CK(cudaSetDevice(ctx->device));
+  TypeHost &T = *ctx->types[type_id];
+  const size_t bytes = (size_t)n_clips * n_keys * T.n * 32;
+  if (T.d_keys) cudaFree(T.d_keys);
+  T.d_keys = nullptr;
+  CK(cudaMalloc(&T.d_keys, bytes));
+  CK(cudaMemcpy(T.d_keys, keys, bytes, cudaMemcpyHostToDevice));
+  CK(launch_prepare_keys(T.d_keys, n_clips, n_keys, T.n, 0));
+  CK(cudaDeviceSynchronize());
+  T.n_clips = n_clips;
+  T.n_keys = n_keys;
+  T.rate = rate_hz;
+  CK(upload_types(ctx));
+  return ANIM_OK;
+}
+
+int anim_plan_create(anim_ctx *ctx, int64_t n_chars, const int32_t *char_type, anim_plan **out) {
+  if (!ctx) return ANIM_EINVAL;
+  if (!out || n_chars < 0 || (n_chars > 0 && !char_type)) return fail(ctx, ANIM_EINVAL, "bad plan arguments");
+  if (n_chars > (int64_t)1 << 30) return fail(ctx, ANIM_EUNSUPPORTED, "more than 2^30 characters");
+  *out = nullptr;
+  const int nt = (int)ctx->types.size();
+  for (int64_t c = 0; c < n_chars; ++c)
+    if (char_type[c] < 0 || char_type[c] >= nt)
+      return fail(ctx, ANIM_EINVAL, "char_type[%lld] = %d is not a type id", (long long)c, char_type[c]);
+  CK(cudaSetDevice(ctx->device));
+  std::unique_ptr<anim_plan> P(new anim_plan());
+  P->ctx = ctx;
+  P->n_chars = n_chars;
+  P->char_type.assign(char_type, char_type + n_chars);
+  P->row_off.resize(n_chars + 1);
+  P->row_off[0] = 0;
+  std::vector<int64_t> count(nt, 0);
+  for (int64_t c = 0; c < n_chars; ++c) {
+    P->row_off[c + 1] = P->row_off[c] + ctx->types[char_type[c]]->n;
+    ++count[char_type[c]];
+  }
+  P->total = P->row_off[n_chars];
+  for (int t = 0; t < nt; ++t)
+    if (count[t]) P->used.push_back(t);
+  std::stable_sort(P->used.begin(), P->used.end(), [&](int a, int b) {
+    const TypeHost &A = *ctx->types[a], &B = *ctx->types[b];
+    return A.n != B.n ? A.n > B.n : A.max_depth > B.max_depth;
+  });
+  std::vector<int> rank(nt, -1);
+  for (size_t u = 0; u < P->used.size(); ++u) rank[P->used[u]] = (int)u;
+  P->by_type.assign(P->used.size(), {});
+  for (int64_t c = 0; c < n_chars; ++c) P->by_type[rank[char_type[c]]].push_back((int32_t)c);
+  std::vector<int32_t> grouped;
+  for (auto &v : P->by_type) {
+    P->type_chars_start.push_back((int)grouped.size());
+    grouped.insert(grouped.end(), v.begin(), v.end());
+  }
+  CK(upload_vec(&P->d_char_type, P->char_type));
+  CK(upload_vec(&P->d_row_off, P->row_off));
+  CK(upload_vec(&P->d_type_chars, grouped));
+  std::vector<int32_t> used32(P->used.begin(), P->used.end());
+  CK(upload_vec(&P->d_used, used32));
+  CK(cudaMalloc(&P->d_sorted, std::max<int64_t>(1, n_chars) * sizeof(int32_t)));
+  CK(cudaMalloc(&P->d_items_frame, (size_t)(n_chars + kMaxBins + 1) * sizeof(WorkItem)));
+  CK(cudaMalloc(&P->d_n_items, sizeof(int32_t)));
+  CK(cudaMalloc(&P->d_queue, 4 * sizeof(int)));
+  CK(cudaMemset(P->d_queue, 0, 4 * sizeof(int)));
+  const int rc = plan_schedule(ctx, P.get());
+  if (rc != ANIM_OK) return rc;
+  ctx->plans.insert(P.get());
+  *out = P.release();
+  return ANIM_OK;
+}
+
+int anim_plan_destroy(anim_ctx *ctx, anim_plan *plan) {
+  if (!ctx || !plan || !ctx->plans.count(plan)) return ctx ? fail(ctx, ANIM_EINVAL, "unknown plan") : ANIM_EINVAL;
+  for (auto it = ctx->iks.begin(); it != ctx->iks.end();) {
+    if ((*it)->plan == plan) {
+      delete *it;
+      it = ctx->iks.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->plans.erase(plan);
+  delete plan;
+  return ANIM_OK;
+}
+
+int anim_plan_total_joints(const anim_plan *plan, int64_t *out_total) {
+  if (!plan || !out_total) return ANIM_EINVAL;
+  *out_total = plan->total;
+  return ANIM_OK;
+}
+
+int anim_plan_row_offsets(const anim_plan *plan, int64_t *out) {
+  if (!plan || !out) return ANIM_EINVAL;
+  memcpy(out, plan->row_off.data(), plan->row_off.size() * sizeof(int64_t));
+  return ANIM_OK;
+}
+
+static int check_plan(anim_ctx *ctx, const anim_plan *plan) {
+  if (!ctx) return ANIM_EINVAL;
+  if (!plan || !ctx->plans.count(const_cast<anim_plan *>(plan))) return fail(ctx, ANIM_EINVAL, "unknown plan");
+  if (plan->version != ctx->version) {
+    const int rc = plan_schedule(ctx, const_cast<anim_plan *>(plan));
+    if (rc != ANIM_OK) return rc;
+  }
+  return ANIM_OK;
+}
+
+static int frame_checks(anim_ctx *ctx, const anim_plan *plan, const float *d_time) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (!d_time || !aligned4(d_time)) return fail(ctx, ANIM_EINVAL, "d_time must be a 4-byte aligned device pointer");
+  int bins = 0;
+  for (int t : plan->used) {
+    if (ctx->types[t]->n_clips == 0) return fail(ctx, ANIM_ESTATE, "type %d has no clips uploaded", t);
+    bins += ctx->types[t]->n_keys;
+  }
+  if (bins > kMaxBins) return fail(ctx, ANIM_EUNSUPPORTED, "the plan's types have %d keys in total (max %d)", bins, kMaxBins);
+  return ANIM_OK;
+}
+
+int anim_frame_build_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_time, void *stream) {
+  int rc = frame_checks(ctx, plan, d_time);
+  if (rc || plan->n_chars == 0) return rc;
+  BucketArgs b{};
+  b.n_chars = plan->n_chars;
+  b.char_type = plan->d_char_type;
+  b.time = d_time;
+  b.types = ctx->d_types;
+  b.n_types = (int)ctx->types.size();
+  b.n_used = (int)plan->used.size();
+  b.used = plan->d_used;
+  b.cap = plan->d_cap;
+  b.sorted = plan->d_sorted;
+  b.items = plan->d_items_frame;
+  b.n_items = plan->d_n_items;
+  b.queue_head = plan->d_queue;
+  b.status = ctx->d_status;
+  CK(launch_bucket(b, (cudaStream_t)stream));
+  return ANIM_OK;
+}
+
+int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
+                         float *d_skin, void *stream) {
+  int rc = frame_checks(ctx, plan, d_time);
+  if (rc || plan->n_chars == 0) return rc;
+  if (!d_blend_w || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_skin) || !aligned4(d_blend_w))
+    return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned, d_blend_w 4-byte aligned");
+  ScanArgs a{};
+  a.types = ctx->d_types;
+  a.items = plan->d_items_frame;
+  a.n_items_dev = plan->d_n_items;
+  a.item_chars = plan->d_sorted;
+  a.row_off = plan->d_row_off;
+  a.queue_head = plan->d_queue;
+  a.status = ctx->d_status;
+  a.time = d_time;
+  a.blend_w = d_blend_w;
+  a.skin = d_skin;
+  LaunchCfg cfg = plan->cfg_scan;
+  cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
+  cfg.smem = plan->smem_frame;
+  CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
+  return ANIM_OK;
+}
+
+int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
+                        float *d_skin, void *stream) {
+  int rc = frame_checks(ctx, plan, d_time);
+  if (rc || plan->n_chars == 0) return rc;
+  if (!d_blend_w || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_skin) || !aligned4(d_blend_w))
+    return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned, d_blend_w 4-byte aligned");
+  rc = anim_frame_build_queue(ctx, plan, d_time, stream);
+  if (rc) return rc;
+  return anim_frame_run_queue(ctx, plan, d_time, d_blend_w, d_skin, stream);
+}
+
+int anim_evaluate_frame_levelsync(anim_ctx *ctx, const anim_plan *plan, const float *d_time,
+                                  const float *d_blend_w, float *d_skin, void *stream) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (!d_time || !d_blend_w || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_skin)) return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned");
+  for (size_t u = 0; u < plan->used.size(); ++u) {
+    const TypeHost &T = *ctx->types[plan->used[u]];
+    if (T.n_clips == 0) return fail(ctx, ANIM_ESTATE, "type %d has no clips uploaded", plan->used[u]);
+    LevelArgs a{};
+    a.type = T.dev;
+    a.chars = plan->d_type_chars + plan->type_chars_start[u];
+    a.n_chars = (int)plan->by_type[u].size();
+    a.row_off = plan->d_row_off;
+    a.time = d_time;
+    a.blend_w = d_blend_w;
+    a.skin = d_skin;
+    a.status = ctx->d_status;
+    const int threads = T.n <= 1024 ? std::max(32, (T.n + 31) / 32 * 32) : 1024;
+    CK(launch_levelsync(0, a, threads,
+                        (cudaStream_t)stream));
+  }
+  return ANIM_OK;
+}
+
+int anim_forward_local(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t, float *d_skin,
+                       float *d_model, void *stream) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (!d_q || !d_t || (!d_skin && !d_model)) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_q) || (d_skin && !aligned16(d_skin)) || (d_model && !aligned16(d_model)) || !aligned4(d_t))
+    return fail(ctx, ANIM_EINVAL, "d_q, d_skin, d_model must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(plan->d_queue, 0, sizeof(int), st));
+  ScanArgs a{};
+  a.types = ctx->d_types;
+  a.items = plan->d_items_scan;
+  a.n_items = plan->n_items_scan;
+  a.item_chars = plan->d_type_chars;
+  a.row_off = plan->d_row_off;
+  a.queue_head = plan->d_queue;
+  a.status = ctx->d_status;
+  a.q = d_q;
+  a.t = d_t;
+  a.skin = d_skin;
+  a.model = d_model;
+  CK(launch_scan(1, a, plan->cfg_scan, st));
+  return ANIM_OK;
+}
+
+int anim_forward_local_levelsync(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t,
+                                 float *d_skin, void *stream) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (!d_q || !d_t || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_q) || !aligned16(d_skin)) return fail(ctx, ANIM_EINVAL, "d_q, d_skin must be 16-byte aligned");
+  for (size_t u = 0; u < plan->used.size(); ++u) {
+    const TypeHost &T = *ctx->types[plan->used[u]];
+    LevelArgs a{};
+    a.type = T.dev;
+    a.chars = plan->d_type_chars + plan->type_chars_start[u];
+    a.n_chars = (int)plan->by_type[u].size();
+    a.row_off = plan->d_row_off;
+    a.q = d_q;
+    a.t = d_t;
+    a.skin = d_skin;
+    a.status = ctx->d_status;
+    const int threads = T.n <= 1024 ? std::max(32, (T.n + 31) / 32 * 32) : 1024;
+    CK(launch_levelsync(1, a, threads, (cudaStream_t)stream));
+  }
+  return ANIM_OK;
+}
+
+static int run_adjoint(anim_ctx *ctx, const anim_plan *plan, int mode, const float *d_q, const float *d_t,
+                       const float *d_in, float *d_grad_q, float *d_grad_t, float *d_loss, void *stream) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (!d_q || !d_t || !d_in || !d_grad_q || !d_grad_t) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_q) || !aligned16(d_grad_q)) return fail(ctx, ANIM_EINVAL, "d_q, d_grad_q must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(plan->d_queue, 0, sizeof(int), st));
+  AdjointArgs a{};
+  a.types = ctx->d_types;
+  a.items = plan->d_items_adj;
+  a.n_items = plan->n_items_adj;
+  a.item_chars = plan->d_type_chars;
+  a.row_off = plan->d_row_off;
+  a.queue_head = plan->d_queue;
+  a.status = ctx->d_status;
+  a.q = d_q;
+  a.t = d_t;
+  if (mode == 0)
+    a.grad_pos = d_in;
+  else
+    a.target = d_in;
+  a.grad_q = d_grad_q;
+  a.grad_t = d_grad_t;
+  a.loss = d_loss;
+  CK(launch_adjoint(mode, a, plan->cfg_adj, st));
+  return ANIM_OK;
+}
+
+int anim_backward(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t, const float *d_grad_pos,
+                  float *d_grad_q, float *d_grad_t, void *stream) {
+  return run_adjoint(ctx, plan, 0, d_q, d_t, d_grad_pos, d_grad_q, d_grad_t, nullptr, stream);
+}
+
+int anim_loss_backward(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t,
+                       const float *d_target, float *d_grad_q, float *d_grad_t, float *d_loss, void *stream) {
+  return run_adjoint(ctx, plan, 1, d_q, d_t, d_target, d_grad_q, d_grad_t, d_loss, stream);
+}
+
+int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_t *effectors, anim_ik **out) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (!out || n_eff < 1 || n_eff > 64 || !effectors) return fail(ctx, ANIM_EINVAL, "bad IK arguments");
+  *out = nullptr;
+  CK(cudaSetDevice(ctx->device));
+  const int nt = (int)ctx->types.size();
+  std::unique_ptr<anim_ik> K(new anim_ik());
+  K->ctx = ctx;
+  K->plan = plan;
+  K->n_eff = n_eff;
+  K->views.resize(nt);
+  std::vector<int32_t> eff_slot((size_t)nt * n_eff, 0);
+  std::vector<TypeDev> vdev(nt);
+  std::vector<int> Cv(nt, 1);
+  size_t smem = 16;
+  for (int t : plan->used) {
+    const TypeHost &T = *ctx->types[t];
+    std::vector<char> act(T.n, 0);
+    for (int e = 0; e < n_eff; ++e) {
+      const int j = effectors[(size_t)t * n_eff + e];
+      if (j < 0 || j >= T.n) return fail(ctx, ANIM_EINVAL, "effector %d of type %d out of range", j, t);
+      for (int a = j; a >= 0 && !act[a]; a = T.parent[a]) act[a] = 1;
+    }
+    auto V = std::make_unique<TypeHost>();
+    std::vector<int> vid(T.n, -1);
+    for (int j = 0; j < T.n; ++j)
+      if (act[j]) {
+        vid[j] = (int)V->gather.size();
+        V->gather.push_back(j);
+      }
+    V->n = (int)V->gather.size();
+    for (int j : V->gather) V->parent.push_back(T.parent[j] < 0 ? -1 : vid[T.parent[j]]);
+    V->depth = depths_of(V->parent);
+    V->max_depth = *std::max_element(V->depth.begin(), V->depth.end());
+    V->seg_len = default_seg_len(V->n);
+    CK(V->build_tables());
+    for (int e = 0; e < n_eff; ++e) eff_slot[(size_t)t * n_eff + e] = vid[effectors[(size_t)t * n_eff + e]];
+    vdev[t] = V->dev;
+    const int C = choose_C(ctx, *V, true);
+    if (C == 0) return fail(ctx, ANIM_EUNSUPPORTED, "IK view of type %d does not fit in shared memory", t);
+    Cv[t] = C;
+    smem = std::max(smem, adjoint_smem_bytes(V->n, V->seg.nseg, C));
+    K->views[t] = std::move(V);
+  }
+  CK(upload_vec(&K->d_views, vdev));
+  CK(upload_vec(&K->d_eff, eff_slot));
+  auto items = make_items(plan, Cv);
+  K->n_items = (int)items.size();
+  CK(upload_vec(&K->d_items, items));
+  CK(cudaMalloc(&K->d_counters, 4 * sizeof(int)));
+  CK(cudaMemset(K->d_counters, 0, 4 * sizeof(int)));
+  K->cfg = {kAdjThreads, std::max(1, std::min(ctx->sm_count * ctx->ctas_per_sm, K->n_items)), smem};
+  ctx->iks.insert(K.get());
+  *out = K.release();
+  return ANIM_OK;
+}
+
+int anim_ik_destroy(anim_ctx *ctx, anim_ik *ik) {
+  if (!ctx || !ik || !ctx->iks.count(ik)) return ctx ? fail(ctx, ANIM_EINVAL, "unknown IK object") : ANIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->iks.erase(ik);
+  delete ik;
+  return ANIM_OK;
+}
+
+int anim_ik_reset(anim_ctx *ctx, anim_ik *ik, void *stream) {
+  if (!ctx || !ik || !ctx->iks.count(ik)) return ctx ? fail(ctx, ANIM_EINVAL, "unknown IK object") : ANIM_EINVAL;
+  CK(cudaMemsetAsync(ik->d_counters, 0, 4 * sizeof(int), (cudaStream_t)stream));
+  return ANIM_OK;
+}
+
+int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v, const float *d_t,
+                 const float *d_targets, float lr, float beta1, float beta2, float eps, float *d_loss, void *stream) {
+  if (!ctx || !ik || !ctx->iks.count(ik)) return ctx ? fail(ctx, ANIM_EINVAL, "unknown IK object") : ANIM_EINVAL;
+  const anim_plan *plan = ik->plan;
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (!d_q || !d_m || !d_v || !d_t || !d_targets) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_q) || !aligned16(d_m) || !aligned16(d_v))
+    return fail(ctx, ANIM_EINVAL, "d_q, d_m, d_v must be 16-byte aligned");
+  if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return fail(ctx, ANIM_EINVAL, "bad Adam hyper-parameters");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(ik->d_counters, 0, sizeof(int), st));
+  AdjointArgs a{};
+  a.types = ik->d_views;
+  a.items = ik->d_items;
+  a.n_items = ik->n_items;
+  a.item_chars = plan->d_type_chars;
+  a.row_off = plan->d_row_off;
+  a.queue_head = ik->d_counters;
+  a.status = ctx->d_status;
+  a.q = d_q;
+  a.t = d_t;
+  a.target = d_targets;
+  a.loss = d_loss;
+  a.eff_slot = ik->d_eff;
+  a.n_eff = ik->n_eff;
+  a.m = d_m;
+  a.v = d_v;
+  a.q_mut = d_q;
+  a.step = ik->d_counters + 1;
+  a.done_ctas = ik->d_counters + 2;
+  a.lr = lr;
+  a.beta1 = beta1;
+  a.beta2 = beta2;
+  a.eps = eps;
+  CK(launch_adjoint(2, a, ik->cfg, st));
+  return ANIM_OK;
+}
+
+int anim_get_status(anim_ctx *ctx, void *stream, int *out_status) {
+  if (!ctx || !out_status) return ANIM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  *out_status = v;
+  return ANIM_OK;
+}
+
+int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  (void)which;
+  return ANIM_OK;
+}
+
+int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, int32_t *out_nseg, int32_t *out_seg_start,
+                          int32_t *out_rounds, int32_t *out_depth) {
+  if (n < 1 || n > ANIM_MAX_JOINTS || !parents || seg_len < 1 || !out_nseg || !out_seg_start || !out_rounds ||
+      !out_depth)
+    return ANIM_EINVAL;
+  if (validate_parents(parents, n) >= 0) return ANIM_EINVAL;
+  std::vector<int32_t> par(parents, parents + n);
+  Segments S = analyze_segments(par, seg_len);
+  *out_nseg = S.nseg;
+  *out_rounds = S.rounds;
+  std::copy(S.start.begin(), S.start.end(), out_seg_start);
+  const auto d = depths_of(par);
+  *out_depth = *std::max_element(d.begin(), d.end());
+  return ANIM_OK;
+}
+
+}  // extern "C"

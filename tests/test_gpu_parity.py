@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle,
+element by element, on the five workloads at full size and on edge cases.
+
+Tolerances: max-abs 1e-4 on skeletons of unit extent, 5e-4 for depth >= 1024
+(skin/model matrices); gradients 1e-4 * max(1, max |oracle gradient|) per
+character (5e-4 for depth >= 1024)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def run_frame(w, levelsync=False):
+    ctx, plan = _gpu.setup(w)
+    tm, wt = _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])
+    out = ctx.evaluate_frame(plan, tm, wt, levelsync=levelsync)
+    skin = out.cpu().numpy()
+    assert ctx.status() == 0
+    return skin
+
+
+def test_config1_forward_local(torch):
+    w = synth.config1()
+    ref, model_ref = oracle.forward_qt(w["types"], w["char_type"], w["q"], w["t"])
+    ctx, plan = _gpu.setup(w, with_clips=False)
+    q, t = _gpu.cuda(w["q"]), _gpu.cuda(w["t"])
+    skin, model = ctx.forward_local(plan, q, t, skin=True, model=True)
+    _gpu.assert_skin_close(skin.cpu().numpy(), ref, w)
+    _gpu.assert_skin_close(model.cpu().numpy(), model_ref, w)
+    s_only, _ = ctx.forward_local(plan, q, t, skin=True, model=False)
+    _, m_only = ctx.forward_local(plan, q, t, skin=False, model=True)
+    np.testing.assert_array_equal(s_only.cpu().numpy(), skin.cpu().numpy())
+    np.testing.assert_array_equal(m_only.cpu().numpy(), model.cpu().numpy())
+    lv, _ = ctx.forward_local(plan, q, t, levelsync=True)
+    _gpu.assert_skin_close(lv.cpu().numpy(), ref, w)
+
+
+def test_config2_frame_full(torch):
+    w = synth.config2()
+    ref = oracle.frame(w)
+    errs = _gpu.assert_skin_close(run_frame(w), ref, w)
+    print("config2 fused max-abs per type:", errs)
+
+
+def test_config2_frame_levelsync(torch):
+    w = synth.subset(synth.config2(), list(range(0, 4096, 7)) + [4096])
+    _gpu.assert_skin_close(run_frame(w, levelsync=True), oracle.frame(w), w)
+
+
+def test_config3_frame_full(torch):
+    w = synth.config3()
+    ref = oracle.frame(w)
+    errs = _gpu.assert_skin_close(run_frame(w), ref, w)
+    print("config3 fused max-abs per type:", errs)
+
+
+def test_config3_frame_levelsync(torch):
+    w = synth.subset(synth.config3(), list(range(0, 10000, 13)))
+    _gpu.assert_skin_close(run_frame(w, levelsync=True), oracle.frame(w), w)
+
+
+def test_frame_repeatable_and_graph_capturable(torch):
+    """Two evaluations agree bit for bit (the work queue order changes
+    nothing), and a captured CUDA graph replays the same frame."""
+    w = synth.subset(synth.config3(), list(range(600)))
+    ctx, plan = _gpu.setup(w)
+    tm, wt = _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])
+    a = ctx.evaluate_frame(plan, tm, wt).clone()
+    b = ctx.evaluate_frame(plan, tm, wt).clone()
+    assert torch.equal(a, b)
+    out = torch.zeros_like(a)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ctx.evaluate_frame(plan, tm, wt, out=out, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    out.zero_()
+    with torch.cuda.graph(g):
+        ctx.evaluate_frame(plan, tm, wt, out=out)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, a)
+
+
+def _grad_tol(dq_ref, dt_ref, w):
+    """Per-joint tolerance: 1e-4 * max(1, max |oracle grad| of the character)."""
+    off = oracle.offsets(w["char_type"], w["types"])
+    tol = np.empty(len(dq_ref))
+    for c, ty in enumerate(w["char_type"]):
+        sl = slice(off[c], off[c + 1])
+        scale = max(1.0, np.abs(dq_ref[sl]).max(), np.abs(dt_ref[sl]).max())
+        tol[sl] = _gpu.tol_for_depth(w["types"][ty]["depth"]) * scale
+    return tol
+
+
+def test_config4_loss_backward_full(torch):
+    w = synth.config4()
+    types, ct = w["types"], w["char_type"]
+    _, M = oracle.forward_qt(types, ct, w["q"], w["t"], with_skin=False)
+    g = 2 * (M[:, :, 3] - w["target"])
+    dq_ref, dt_ref = oracle.grad(types, ct, w["q"], w["t"], g)
+    off = oracle.offsets(ct, types)
+    loss_ref = np.array([np.sum((M[off[c]:off[c + 1], :, 3] - w["target"][off[c]:off[c + 1]]) ** 2)
+                         for c in range(len(ct))])
+    ctx, plan = _gpu.setup(w, with_clips=False)
+    q, t, tg = _gpu.cuda(w["q"]), _gpu.cuda(w["t"]), _gpu.cuda(w["target"])
+    gq, gt, loss = ctx.loss_backward(plan, q, t, tg)
+    gq, gt, loss = gq.cpu().numpy(), gt.cpu().numpy(), loss.cpu().numpy()
+    tol = _grad_tol(dq_ref, dt_ref, w)
+    assert (np.abs(gq - dq_ref).max(axis=1) <= tol).all(), np.abs(gq - dq_ref).max()
+    assert (np.abs(gt - dt_ref).max(axis=1) <= tol).all(), np.abs(gt - dt_ref).max()
+    np.testing.assert_allclose(loss, loss_ref, rtol=1e-4)
+    # anim_backward with the same dLoss/dp given explicitly
+    gq2, gt2 = ctx.backward(plan, q, t, _gpu.cuda(g.astype(np.float32)))
+    assert (np.abs(gq2.cpu().numpy() - dq_ref).max(axis=1) <= tol).all()
+    assert (np.abs(gt2.cpu().numpy() - dt_ref).max(axis=1) <= tol).all()
+
+
+def test_autograd_function(torch):
+    import paper_2505_06703_gb300 as pk
+    w = synth.subset(synth.config4(), list(range(32)))
+    types, ct = w["types"], w["char_type"]
+    ctx, plan = _gpu.setup(w, with_clips=False)
+    q = _gpu.cuda(w["q"]).requires_grad_(True)
+    t = _gpu.cuda(w["t"]).requires_grad_(True)
+    tg = _gpu.cuda(w["target"])
+    p = pk.hierarchy_fn().apply(q, t, ctx, plan)
+    loss = ((p - tg) ** 2).sum()
+    loss.backward()
+    _, M = oracle.forward_qt(types, ct, w["q"], w["t"], with_skin=False)
+    np.testing.assert_allclose(p.detach().cpu().numpy(), M[:, :, 3], atol=1e-4)
+    g = 2 * (M[:, :, 3] - w["target"])
+    dq_ref, dt_ref = oracle.grad(types, ct, w["q"], w["t"], g)
+    tol = _grad_tol(dq_ref, dt_ref, w)
+    assert (np.abs(q.grad.cpu().numpy() - dq_ref).max(axis=1) <= tol).all()
+    assert (np.abs(t.grad.cpu().numpy() - dt_ref).max(axis=1) <= tol).all()
+
+
+def test_config5_ik_subset(torch):
+    """200 Adam steps of IK on 64 characters (32 of each type): final
+    effector positions of the GPU run against the FP64 oracle run of the
+    same schedule, and the loss must fall."""
+    w = synth.subset(synth.config5(), list(range(64)))
+    types, ct, eff = w["types"], w["char_type"], w["effectors"]
+    steps = w["n_steps"]
+    targets_ref = oracle.ik_targets(w)
+    q_ref, hist = oracle.ik(types, ct, w["t"], w["q0"], eff, targets_ref, steps)
+    ctx, plan = _gpu.setup(w, with_clips=False)
+    t = _gpu.cuda(w["t"])
+    # the GPU derives its own targets: effector positions of the target pose
+    _, mt = ctx.forward_local(plan, _gpu.cuda(w["q_target"]), t, skin=False, model=True)
+    mt = mt.view(-1, 3, 4)[:, :, 3]
+    off = torch.as_tensor(plan.row_off[:-1], device="cuda")
+    eff_t = torch.as_tensor(eff, device="cuda").long()[torch.as_tensor(ct, device="cuda").long()]
+    targets = mt[off[:, None] + eff_t].contiguous()
+    assert np.abs(targets.cpu().numpy() - targets_ref).max() < 1e-5
+    q = _gpu.cuda(w["q0"])
+    m, v = torch.zeros_like(q), torch.zeros_like(q)
+    loss = torch.zeros(len(ct), device="cuda")
+    ik = ctx.ik(plan, eff)
+    ik.reset()
+    first = None
+    for s in range(steps):
+        ik.step(q, m, v, t, targets, lr=w["lr"], betas=w["betas"], eps=w["eps"], loss=loss)
+        if s == 0:
+            first = loss.sum().item()
+    last = loss.sum().item()
+    assert abs(first - hist[0]) <= 1e-4 * max(1, hist[0])
+    assert last < 0.5 * first
+    _, Mg = oracle.forward_qt(types, ct, q.cpu().numpy().astype(np.float64), w["t"], with_skin=False)
+    _, Mr = oracle.forward_qt(types, ct, q_ref, w["t"], with_skin=False)
+    offn = oracle.offsets(ct, types)
+    pe_g = np.stack([Mg[offn[c] + eff[ty], :, 3] for c, ty in enumerate(ct)])
+    pe_r = np.stack([Mr[offn[c] + eff[ty], :, 3] for c, ty in enumerate(ct)])
+    err_g = np.linalg.norm(pe_g - targets_ref, axis=-1)
+    err_r = np.linalg.norm(pe_r - targets_ref, axis=-1)
+    print("IK final effector error: gpu mean %.3e oracle mean %.3e, max |p_gpu - p_oracle| %.3e" % (
+        err_g.mean(), err_r.mean(), np.abs(pe_g - pe_r).max()))
+    assert np.abs(pe_g - pe_r).max() < 2e-3
+    assert abs(err_g.mean() - err_r.mean()) < 1e-3
+
+
+# ------------------------------------------------------------------ edge cases
+def _edge_types(rng):
+    return [synth.make_type(np.array([-1], np.int32), rng, with_clips=True),               # one joint
+            synth.make_type(synth.chain(3), rng, with_clips=True),                         # tiny chain
+            synth.make_type(np.array([-1, 0, -1, 2, 2, -1], np.int32), rng, with_clips=True),  # forest
+            synth.make_type(synth.relabel_random_topological(synth.random_tree(33, 9, rng, spine=9), rng)[0],
+                            rng, with_clips=True),                                         # non depth-first
+            synth.make_type(synth.random_tree(1000, 40, rng, spine=40), rng, with_clips=True),
+            synth.make_type(synth.chain(2048), rng, with_clips=True)]                      # maximum size
+
+
+def test_edge_types_frame_and_local(torch):
+    rng = np.random.default_rng(77)
+    types = _edge_types(rng)
+    ct = np.array(list(range(len(types))) * 3 + [0] * 70 + [1] * 5, np.int32)
+    rng.shuffle(ct)
+    w = {"types": types, "char_type": ct, "time": rng.uniform(-3, 5, len(ct)).astype(np.float32),
+         "weight": rng.uniform(0, 1, len(ct)).astype(np.float32)}
+    _gpu.assert_skin_close(run_frame(w), oracle.frame(w), w)
+    _gpu.assert_skin_close(run_frame(w, levelsync=True), oracle.frame(w), w)
+    off = oracle.offsets(ct, types)
+    q, t = synth.local_poses(rng, int(off[-1]), t_half=0.0005)
+    ref, mref = oracle.forward_qt(types, ct, q, t)
+    ctx, plan = _gpu.setup(w)
+    s, m = ctx.forward_local(plan, _gpu.cuda(q), _gpu.cuda(t), skin=True, model=True)
+    _gpu.assert_skin_close(s.cpu().numpy(), ref, w)
+    _gpu.assert_skin_close(m.cpu().numpy(), mref, w)
+    g = rng.normal(size=(int(off[-1]), 3))
+    dq_ref, dt_ref = oracle.grad(types, ct, q, t, g)
+    gq, gt = ctx.backward(plan, _gpu.cuda(q), _gpu.cuda(t), _gpu.cuda(g.astype(np.float32)))
+    tol = _grad_tol(dq_ref, dt_ref, {"types": types, "char_type": ct})
+    assert (np.abs(gq.cpu().numpy() - dq_ref).max(axis=1) <= tol).all()
+    assert (np.abs(gt.cpu().numpy() - dt_ref).max(axis=1) <= tol).all()
+
+
+def test_empty_plan_and_errors(torch):
+    import paper_2505_06703_gb300 as pk
+    rng = np.random.default_rng(5)
+    w = {"types": [synth.make_type(synth.chain(4), rng, with_clips=True)], "char_type": np.zeros(0, np.int32),
+         "time": np.zeros(0, np.float32), "weight": np.zeros(0, np.float32)}
+    ctx, plan = _gpu.setup(w)
+    assert plan.total == 0
+    dummy = torch.zeros(4, device="cuda")
+    ctx.evaluate_frame(plan, dummy, dummy, out=torch.zeros((0, 12), device="cuda"))
+    with pytest.raises(pk.AnimError) as e:
+        ctx.create_skeletons([np.array([-1, 1], np.int32)], inv_bind=[np.zeros((2, 12), np.float32)])
+    assert e.value.code == -1
+    with pytest.raises(pk.AnimError):
+        ctx.create_skeletons([np.array([-1, 0], np.int32)])  # neither inverse binds nor rest pose
+    with pytest.raises(pk.AnimError):
+        ctx.plan(np.array([0, 7], np.int32))  # unknown type id
+    # a type without clips cannot be evaluated as a frame
+    ids = ctx.create_skeletons([np.array([-1, 0], np.int32)], inv_bind=[np.tile(np.eye(3, 4), (2, 1, 1))])
+    p2 = ctx.plan(np.array(ids, np.int32))
+    with pytest.raises(pk.AnimError) as e:
+        ctx.evaluate_frame(p2, torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda"))
+    assert e.value.code == -6
+    # misaligned output pointer
+    buf = torch.zeros(2 * 12 + 1, device="cuda")
+    with pytest.raises(pk.AnimError):
+        ctx._ck(ctx.lib.anim_forward_local(ctx.h, p2.h, torch.zeros((2, 4), device="cuda").data_ptr(),
+                                           torch.zeros((2, 3), device="cuda").data_ptr(), buf.data_ptr() + 4,
+                                           None, None))
+
+
+def test_nonfinite_time_sets_status(torch):
+    rng = np.random.default_rng(6)
+    w = {"types": [synth.make_type(synth.chain(5), rng, with_clips=True)], "char_type": np.zeros(3, np.int32),
+         "time": np.array([0.2, np.nan, np.inf], np.float32), "weight": np.full(3, 0.5, np.float32)}
+    ctx, plan = _gpu.setup(w)
+    out = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"]))
+    assert ctx.status() & 1
+    assert ctx.status() == 0  # read-and-clear
+    w2 = dict(w, time=np.array([0.2, 0.0, 0.0], np.float32))  # non-finite times sample key 0
+    ref = oracle.frame(w2)
+    _gpu.assert_skin_close(out.cpu().numpy(), ref, w2)
