@@ -26,6 +26,10 @@ struct TypeDev {
   const uint16_t *seg_of;    // [n]
   const int32_t *seg_link;   // [nseg]  parent joint of the segment's first joint, -1 for roots
   const int16_t *jump;       // [rounds][nseg] parent segment at the start of each round, -1 when done
+  int njobs;                 // pass-1 lane jobs: runs of whole consecutive segments, about seg_len joints each
+  int pad1;
+  const int32_t *job_start;  // [njobs + 1] first joint of each job
+  const uint32_t *jinfo;     // [n] segment of the joint (bits 0-15) | kJStart | kJLink
   const float4 *inv_bind;    // [n][3] rows of B_i
   const float4 *keys;        // [n_clips][n_keys][n][2]: (qx qy qz qw), (tx ty tz theta)
   // adjoint: depth-first pre-order of the joints (subtrees are contiguous)
@@ -37,6 +41,9 @@ struct TypeDev {
   const int32_t *gather;
 };
 
+constexpr uint32_t kJStart = 1u << 16;  // joint opens its segment
+constexpr uint32_t kJLink = 1u << 17;   // the joint's segment hangs from a parent joint
+
 // One unit of work: `count` characters of one type.  For the frame the
 // characters share the key index k0 (so they read the same key records).
 struct WorkItem {
@@ -45,6 +52,9 @@ struct WorkItem {
   int32_t type;
   int32_t k0;
 };
+
+// Persistent kernels: 8 compute warps + 1 producer warp per CTA.
+constexpr int kPersistentThreads = 288;
 
 struct LaunchCfg {
   int threads;       // CTA size
@@ -77,25 +87,36 @@ struct ScanArgs {
 
 cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
-// Frame work queue: bucket characters by (type, key index k0) into items of
-// at most cap[type] characters; types are laid out most costly first so the
-// persistent kernel takes the longest items first.
+// Frame work queue.  The plan cuts the characters of each type (types in
+// cost order) into ranges of at most kRangeChars.  One CTA per range sorts its
+// characters by key index k0 (counting sort in shared memory) and emits work
+// items of at most cap[type] characters sharing (type, k0) into the range's
+// slot region; the last CTA to finish compacts the regions, in range order,
+// into the item list and resets the queue counter.
+constexpr int kRangeChars = 256;
+constexpr int kMaxRanges = 4096;  // so at most 1,048,576 characters per plan
+struct RangeDev {
+  int32_t type;
+  int32_t start;   // first index into the type-grouped character list
+  int32_t count;   // characters (<= kRangeChars)
+  int32_t region;  // first item slot of the range
+};
 struct BucketArgs {
-  int64_t n_chars;
-  const int32_t *char_type;   // [n_chars]
+  const RangeDev *ranges;
+  int n_ranges;
+  const int32_t *type_chars;  // characters grouped by type, plan order
   const float *time;          // [n_chars]
-  const TypeDev *types;       // context types (rate, n_keys)
-  int n_types;                // size of the context type table
-  int n_used;
-  const int32_t *used;        // [n_used] type ids, most costly first
+  const TypeDev *types;
   const int32_t *cap;         // [n_types] characters per item
-  int32_t *sorted;            // [n_chars] character ids grouped by bin
-  WorkItem *items;            // [n_chars + n_bins]
+  int32_t *sorted;            // same indexing as type_chars, sorted by k0 within each range
+  WorkItem *regions;          // item slots of every range
+  int32_t *range_items;       // [n_ranges]
+  WorkItem *items;            // compacted items
   int32_t *n_items;           // [1]
   int *queue_head;            // [1] reset to 0
+  int *done;                  // [1] last-CTA counter, left at 0
   int *status;
 };
-constexpr int kMaxBins = 3584;
 constexpr int kMaxTypes = 512;
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s);
 

@@ -22,8 +22,8 @@ using namespace anim;
 
 namespace {
 
-constexpr int kScanThreads = 256;
-constexpr int kAdjThreads = 256;
+constexpr int kScanThreads = kPersistentThreads;
+constexpr int kAdjThreads = kPersistentThreads;
 constexpr int kCMax = 64;
 constexpr int kTargetJointsPerItem = 2048;
 thread_local std::string g_create_error;
@@ -34,6 +34,8 @@ struct Segments {
   std::vector<int32_t> start, link;
   std::vector<uint16_t> seg_of;
   std::vector<int16_t> jump;  // [rounds][nseg]
+  std::vector<int32_t> job_start;  // pass-1 lane jobs (runs of whole segments)
+  std::vector<uint32_t> jinfo;     // per joint: segment | kJStart | kJLink
 };
 
 // Segments: maximal runs of consecutive joints where each joint's parent is
@@ -73,6 +75,24 @@ Segments analyze_segments(const std::vector<int32_t> &par, int seg_len) {
     for (int g = 0; g < S.nseg; ++g) nxt[g] = ptr[g] < 0 ? -1 : ptr[ptr[g]];
     ptr.swap(nxt);
     ++S.rounds;
+  }
+  // lane jobs: consecutive whole segments, greedily grouped to about seg_len
+  // joints, so the pass-1 lanes get balanced walks
+  int acc = 0;
+  S.job_start.push_back(0);
+  for (int g = 0; g < S.nseg; ++g) {
+    const int len = S.start[g + 1] - S.start[g];
+    if (acc > 0 && acc + len > seg_len) {
+      S.job_start.push_back(S.start[g]);
+      acc = 0;
+    }
+    acc += len;
+  }
+  S.job_start.push_back(n);
+  S.jinfo.resize(n);
+  for (int j = 0; j < n; ++j) {
+    const int g = S.seg_of[j];
+    S.jinfo[j] = (uint32_t)g | (j == S.start[g] ? kJStart : 0u) | (S.link[g] >= 0 ? kJLink : 0u);
   }
   return S;
 }
@@ -119,7 +139,7 @@ std::vector<int32_t> depths_of(const std::vector<int32_t> &par) {
   return d;
 }
 
-int default_seg_len(int n) { return n > 1024 ? 16 : 8; }
+int default_seg_len(int) { return 16; }
 
 // ------------------------------------------------------------ device blocks
 struct DevBlock {
@@ -188,6 +208,8 @@ struct TypeHost {
     const size_t o_ds = B.add(dfsord.slot.data(), dfsord.slot.size() * 4);
     const size_t o_se = B.add(dfsord.sub_end.data(), dfsord.sub_end.size() * 4);
     const size_t o_g = B.add(gather.data(), gather.size() * 4);
+    const size_t o_js = B.add(seg.job_start.data(), seg.job_start.size() * 4);
+    const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
     void *d = nullptr;
     cudaError_t e = B.upload(&d);
     if (e != cudaSuccess) {
@@ -210,6 +232,9 @@ struct TypeHost {
     dev.dfs_slot = (const int32_t *)(base + o_ds);
     dev.sub_end = (const int32_t *)(base + o_se);
     dev.gather = gather.empty() ? nullptr : (const int32_t *)(base + o_g);
+    dev.njobs = (int)seg.job_start.size() - 1;
+    dev.job_start = (const int32_t *)(base + o_js);
+    dev.jinfo = (const uint32_t *)(base + o_ji);
     sync_dev();
     return cudaSuccess;
   }
@@ -247,16 +272,20 @@ struct anim_plan {
   WorkItem *d_items_scan = nullptr, *d_items_adj = nullptr;
   int n_items_scan = 0, n_items_adj = 0;
   int32_t *d_sorted = nullptr;
-  WorkItem *d_items_frame = nullptr;
+  WorkItem *d_items_frame = nullptr, *d_regions = nullptr;
+  RangeDev *d_ranges = nullptr;
+  int32_t *d_range_items = nullptr;
+  int n_ranges = 0;
   int32_t *d_n_items = nullptr;
-  int *d_queue = nullptr;
+  int *d_queue = nullptr;  // [0] queue head, [1] bucket last-CTA counter
   int32_t *d_used = nullptr, *d_cap = nullptr;
   LaunchCfg cfg_scan{}, cfg_adj{};
   size_t smem_frame = 0;
   ~anim_plan() {
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
-                    (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_n_items,
-                    (void *)d_queue, (void *)d_used, (void *)d_cap})
+                    (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_regions,
+                    (void *)d_ranges, (void *)d_range_items, (void *)d_n_items, (void *)d_queue, (void *)d_used,
+                    (void *)d_cap})
       if (p) cudaFree(p);
   }
 };
@@ -338,10 +367,10 @@ cudaError_t upload_types(anim_ctx *ctx) {
 }
 
 size_t smem_budget(const anim_ctx *ctx) {
-  // two resident CTAs per SM; keep 1 KB per CTA for the runtime and the
-  // kernels' static shared memory
+  // ctas_per_sm resident CTAs per SM: each also takes 1 KB of system shared
+  // memory and up to 5 KB of the kernels' static shared memory (item buffers)
   const size_t per = ctx->smem_per_sm / (size_t)ctx->ctas_per_sm;
-  return std::min(ctx->smem_optin, per) - 3072;
+  return std::min(ctx->smem_optin - 5120, per - 1024 - 5120);
 }
 
 int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
@@ -351,7 +380,7 @@ int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
     return adjoint ? adjoint_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
   };
   while (C > 1 && bytes(C) > budget) --C;
-  if (bytes(C) > std::min(ctx->smem_optin - 3072, (size_t)227 * 1024)) return 0;
+  if (bytes(C) > ctx->smem_optin - 5120) return 0;
   return C;
 }
 
@@ -409,6 +438,33 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   CK(upload_vec(&P->d_items_scan, is));
   CK(upload_vec(&P->d_items_adj, ia));
   CK(upload_vec(&P->d_cap, P->C_scan));
+  // frame work queue: ranges of <= kRangeChars characters of one type, each
+  // with an item slot region large enough for any key distribution
+  std::vector<RangeDev> ranges;
+  int slots = 0;
+  for (size_t u = 0; u < P->used.size(); ++u) {
+    const int t = P->used[u];
+    const int cnt = (int)P->by_type[u].size(), C = P->C_scan[t], nk = ctx->types[t]->n_keys;
+    for (int k = 0; k < cnt; k += kRangeChars) {
+      RangeDev r;
+      r.type = t;
+      r.start = P->type_chars_start[u] + k;
+      r.count = std::min(kRangeChars, cnt - k);
+      r.region = slots;
+      slots += (r.count + C - 1) / C + std::min(r.count, std::max(nk, 1));
+      ranges.push_back(r);
+    }
+  }
+  P->n_ranges = (int)ranges.size();
+  CK(upload_vec(&P->d_ranges, ranges));
+  if (P->d_regions) cudaFree(P->d_regions);
+  if (P->d_items_frame) cudaFree(P->d_items_frame);
+  if (P->d_range_items) cudaFree(P->d_range_items);
+  P->d_regions = P->d_items_frame = nullptr;
+  P->d_range_items = nullptr;
+  CK(cudaMalloc(&P->d_regions, std::max(1, slots) * sizeof(WorkItem)));
+  CK(cudaMalloc(&P->d_items_frame, std::max(1, slots) * sizeof(WorkItem)));
+  CK(cudaMalloc(&P->d_range_items, std::max(1, P->n_ranges) * sizeof(int32_t)));
   const int grid = ctx->sm_count * ctx->ctas_per_sm;
   P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16)};
   P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
@@ -542,7 +598,9 @@ int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, f
 int anim_plan_create(anim_ctx *ctx, int64_t n_chars, const int32_t *char_type, anim_plan **out) {
   if (!ctx) return ANIM_EINVAL;
   if (!out || n_chars < 0 || (n_chars > 0 && !char_type)) return fail(ctx, ANIM_EINVAL, "bad plan arguments");
-  if (n_chars > (int64_t)1 << 30) return fail(ctx, ANIM_EUNSUPPORTED, "more than 2^30 characters");
+  if (n_chars > (int64_t)kRangeChars * (kMaxRanges - kMaxTypes))
+    return fail(ctx, ANIM_EUNSUPPORTED, "more than %lld characters in one plan",
+                (long long)kRangeChars * (kMaxRanges - kMaxTypes));
   *out = nullptr;
   const int nt = (int)ctx->types.size();
   for (int64_t c = 0; c < n_chars; ++c)
@@ -582,7 +640,6 @@ int anim_plan_create(anim_ctx *ctx, int64_t n_chars, const int32_t *char_type, a
   std::vector<int32_t> used32(P->used.begin(), P->used.end());
   CK(upload_vec(&P->d_used, used32));
   CK(cudaMalloc(&P->d_sorted, std::max<int64_t>(1, n_chars) * sizeof(int32_t)));
-  CK(cudaMalloc(&P->d_items_frame, (size_t)(n_chars + kMaxBins + 1) * sizeof(WorkItem)));
   CK(cudaMalloc(&P->d_n_items, sizeof(int32_t)));
   CK(cudaMalloc(&P->d_queue, 4 * sizeof(int)));
   CK(cudaMemset(P->d_queue, 0, 4 * sizeof(int)));
@@ -637,12 +694,8 @@ static int frame_checks(anim_ctx *ctx, const anim_plan *plan, const float *d_tim
   if (rc) return rc;
   if (plan->n_chars == 0) return ANIM_OK;
   if (!d_time || !aligned4(d_time)) return fail(ctx, ANIM_EINVAL, "d_time must be a 4-byte aligned device pointer");
-  int bins = 0;
-  for (int t : plan->used) {
+  for (int t : plan->used)
     if (ctx->types[t]->n_clips == 0) return fail(ctx, ANIM_ESTATE, "type %d has no clips uploaded", t);
-    bins += ctx->types[t]->n_keys;
-  }
-  if (bins > kMaxBins) return fail(ctx, ANIM_EUNSUPPORTED, "the plan's types have %d keys in total (max %d)", bins, kMaxBins);
   return ANIM_OK;
 }
 
@@ -650,18 +703,19 @@ int anim_frame_build_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_
   int rc = frame_checks(ctx, plan, d_time);
   if (rc || plan->n_chars == 0) return rc;
   BucketArgs b{};
-  b.n_chars = plan->n_chars;
-  b.char_type = plan->d_char_type;
+  b.ranges = plan->d_ranges;
+  b.n_ranges = plan->n_ranges;
+  b.type_chars = plan->d_type_chars;
   b.time = d_time;
   b.types = ctx->d_types;
-  b.n_types = (int)ctx->types.size();
-  b.n_used = (int)plan->used.size();
-  b.used = plan->d_used;
   b.cap = plan->d_cap;
   b.sorted = plan->d_sorted;
+  b.regions = plan->d_regions;
+  b.range_items = plan->d_range_items;
   b.items = plan->d_items_frame;
   b.n_items = plan->d_n_items;
   b.queue_head = plan->d_queue;
+  b.done = plan->d_queue + 1;
   b.status = ctx->d_status;
   CK(launch_bucket(b, (cudaStream_t)stream));
   return ANIM_OK;

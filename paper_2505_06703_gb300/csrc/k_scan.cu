@@ -6,163 +6,142 @@
 #include "dev_math.cuh"
 #include "scan_core.cuh"
 
+#define ANIM_MAX_KEYS_DEV 1024  // keys per clip (ANIM_MAX_KEYS in the ABI)
+
 namespace anim {
 
-constexpr int kCMax = 64;          // characters per work item
-constexpr int kScanThreads = 256;  // CTA size of the persistent scan
+size_t scan_smem_bytes(int n, int nseg, int C) { return scan_item_bytes(n, nseg, C); }
 
-size_t scan_smem_bytes(int n, int nseg, int C) {
-  return 16ull * ((size_t)C * (3 * (size_t)n + 1) + 6ull * C * nseg);
+// The four key records (keys k0 and k1 of clip 0 and clip 1) of one joint.
+struct KeyRecs {
+  float4 qa0, ta0, qa1, ta1, qb0, tb0, qb1, tb1;
+};
+
+// Simulation stage for one joint: slerp/lerp between the keys of each clip at
+// fraction al, then slerp/lerp from clip 0 to clip 1 by w; the local matrix.
+__device__ __forceinline__ Aff sample_local(const KeyRecs &r, float al, float w, bool two) {
+  float4 q = slerp_pre(r.qa0, r.qa1, r.ta0.w, al);
+  float tx = fmaf(al, r.ta1.x - r.ta0.x, r.ta0.x);
+  float ty = fmaf(al, r.ta1.y - r.ta0.y, r.ta0.y);
+  float tz = fmaf(al, r.ta1.z - r.ta0.z, r.ta0.z);
+  if (two) {
+    const float4 qb = slerp_pre(r.qb0, r.qb1, r.tb0.w, al);
+    const float bx = fmaf(al, r.tb1.x - r.tb0.x, r.tb0.x);
+    const float by = fmaf(al, r.tb1.y - r.tb0.y, r.tb0.y);
+    const float bz = fmaf(al, r.tb1.z - r.tb0.z, r.tb0.z);
+    q = slerp_unit(q, qb, w);
+    tx = fmaf(w, bx - tx, tx);
+    ty = fmaf(w, by - ty, ty);
+    tz = fmaf(w, bz - tz, tz);
+  }
+  return aff_from_qt(q, tx, ty, tz);
 }
 
-// Persistent kernel: each CTA pulls work items (C characters of one type)
-// from a global counter, runs the three scan passes in shared memory and
-// streams the finished character blocks to global memory with bulk copies.
-//   MODE 0: local poses sampled from the type's clips at each character's
-//           time (slerp/lerp between keys, then slerp/lerp between clip 0
-//           and clip 1 with the character's blend weight);
+// Persistent kernel.  Work item = C characters of one type (for the frame:
+// characters sharing the key index k0, so they read the same key records).
+// Compute warps run passes 1a/1b/2/3 in shared memory and thread 0 streams
+// the finished character blocks out with bulk copies; the producer warp
+// stages the next item meanwhile.
+//   MODE 0: local poses sampled from the type's clips at each character's time;
 //   MODE 1: local poses read from q [total][4] (normalized here), t [total][3].
 template <int MODE, bool SKIN, bool MODEL>
-__global__ void __launch_bounds__(kScanThreads, 2) k_scan(const ScanArgs a) {
+__global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
-  __shared__ ItemSmem s;
-  __shared__ long long sOff[kCMax];
-  __shared__ float sAlpha[kCMax];
-  __shared__ float sBlend[kCMax];
-  const int tid = threadIdx.x, nth = blockDim.x;
+  __shared__ ItemBuf bufs[2];
+  const int tid = threadIdx.x;
   const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
+
+  if (tid >= kComputeThreads) {
+    producer_loop<MODE>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time,
+                        a.blend_w, a.status);
+    return;
+  }
+
   bool pending = false;  // thread 0: bulk stores in flight
-
+  int cur = 0;
+  handoff_sync();
   for (;;) {
-    if (tid == 0) {
-      if (pending) {
-        bulk_wait_read_all();  // the staging buffer may be overwritten again
-        pending = false;
-      }
-      s.item = atomicAdd(a.queue_head, 1);
-    }
-    __syncthreads();
-    const int item = s.item;
-    if (item >= n_items) break;
-    const WorkItem wi = a.items[item];
-    const int C = wi.count;
-    load_type_smem(s, a.types, wi.type, tid, nth);
-    if (tid < C) {
-      const int cid = __ldg(a.item_chars + wi.start + tid);
-      sOff[tid] = a.row_off[cid];
-      if (MODE == 0) {
-        const float tm = __ldg(a.time + cid);
-        const float rate = a.types[wi.type].rate;
-        float alpha = 0.f;
-        if (isfinite(tm)) {
-          const float u = __fmul_rn(tm, rate);
-          alpha = u - floorf(u);
-        } else {
-          atomicOr(a.status, 1);
-        }
-        sAlpha[tid] = alpha;
-        sBlend[tid] = __ldg(a.blend_w + cid);
-      }
-    }
-    if (tid == 0) {
-      const TypeDev &T = a.types[wi.type];
-      s.wi = wi;
-      s.divC.init(C);
-      s.divS.init(T.nseg);
-      s.divN.init(T.n);
-    }
-    __syncthreads();
-
-    const int n = s.T.n, nseg = s.T.nseg;
+    const ItemBuf &b = bufs[cur];
+    if (b.item < 0) break;
+    const int C = b.C, n = b.T.n, nseg = b.T.nseg;
     const int cs4 = 3 * n + 1;  // float4 stride between characters (16 B skew against bank conflicts)
     float4 *P = sm;
     float4 *Y0 = P + C * cs4;
     float4 *Y1 = Y0 + 3 * C * nseg;
-
-    // ---- pass 1: per (segment, character) running products
-    {
-      const int NS = nseg * C;
-      if (MODE == 0) {
-        const int nk = s.T.n_keys, k0 = wi.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
-        const float4 *KA0 = s.T.keys + (size_t)k0 * n * 2;
-        const float4 *KA1 = s.T.keys + (size_t)k1 * n * 2;
-        const float4 *KB0 = s.T.keys + (size_t)(nk + k0) * n * 2;
-        const float4 *KB1 = s.T.keys + (size_t)(nk + k1) * n * 2;
-        const bool two = s.T.n_clips >= 2;
-        for (int idx = tid; idx < NS; idx += nth) {
-          const int g = (int)s.divC.div(idx), c = idx - g * C;
-          const int j0 = __ldg(s.T.seg_start + g), j1 = __ldg(s.T.seg_start + g + 1);
-          const float al = sAlpha[c], w = sBlend[c];
-          float4 *Pc = P + c * cs4;
-          Aff acc;
-          for (int j = j0; j < j1; ++j) {
-            const float4 qa0 = __ldg(KA0 + 2 * j), ta0 = __ldg(KA0 + 2 * j + 1);
-            const float4 qa1 = __ldg(KA1 + 2 * j), ta1 = __ldg(KA1 + 2 * j + 1);
-            float4 q = slerp_pre(qa0, qa1, ta0.w, al);
-            float tx = fmaf(al, ta1.x - ta0.x, ta0.x);
-            float ty = fmaf(al, ta1.y - ta0.y, ta0.y);
-            float tz = fmaf(al, ta1.z - ta0.z, ta0.z);
-            if (two) {
-              const float4 qb0 = __ldg(KB0 + 2 * j), tb0 = __ldg(KB0 + 2 * j + 1);
-              const float4 qb1 = __ldg(KB1 + 2 * j), tb1 = __ldg(KB1 + 2 * j + 1);
-              const float4 qb = slerp_pre(qb0, qb1, tb0.w, al);
-              const float bx = fmaf(al, tb1.x - tb0.x, tb0.x);
-              const float by = fmaf(al, tb1.y - tb0.y, tb0.y);
-              const float bz = fmaf(al, tb1.z - tb0.z, tb0.z);
-              q = slerp_unit(q, qb, w);
-              tx = fmaf(w, bx - tx, tx);
-              ty = fmaf(w, by - ty, ty);
-              tz = fmaf(w, bz - tz, tz);
-            }
-            const Aff L = aff_from_qt(q, tx, ty, tz);
-            acc = (j == j0) ? L : aff_mul(acc, L);
-            sts_aff(Pc + 3 * j, acc);
-          }
-        }
-      } else {
-        const bool gath = s.T.gather != nullptr;
-        for (int idx = tid; idx < NS; idx += nth) {
-          const int g = (int)s.divC.div(idx), c = idx - g * C;
-          const int j0 = __ldg(s.T.seg_start + g), j1 = __ldg(s.T.seg_start + g + 1);
-          const long long off = sOff[c];
-          float4 *Pc = P + c * cs4;
-          Aff acc;
-          for (int j = j0; j < j1; ++j) {
-            const long long row = off + (gath ? __ldg(s.T.gather + j) : j);
-            const float4 q = normalize4(__ldg(reinterpret_cast<const float4 *>(a.q) + row));
-            const float *tp = a.t + 3 * row;
-            const Aff L = aff_from_qt(q, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
-            acc = (j == j0) ? L : aff_mul(acc, L);
-            sts_aff(Pc + 3 * j, acc);
-          }
-        }
-      }
+    if (tid == 0 && pending) {
+      bulk_wait_read_all();  // the staging buffer of the previous item has been read out
+      pending = false;
     }
-    __syncthreads();
+    compute_sync();
+
+    // ---- pass 1a: local matrices of every (joint, character)
+    if (MODE == 0) {
+      const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
+      const float4 *KA0 = b.T.keys + (size_t)k0 * n * 2;
+      const float4 *KA1 = b.T.keys + (size_t)k1 * n * 2;
+      const float4 *KB0 = b.T.keys + (size_t)(nk + k0) * n * 2;
+      const float4 *KB1 = b.T.keys + (size_t)(nk + k1) * n * 2;
+      const bool two = b.T.n_clips >= 2;
+      const int CN = C * n;
+#pragma unroll 2
+      for (int idx = tid; idx < CN; idx += kComputeThreads) {
+        const int j = (int)b.divC.div(idx), c = idx - j * C;  // character-minor: lanes share key records
+        KeyRecs r;
+        r.qa0 = __ldg(KA0 + 2 * j);
+        r.ta0 = __ldg(KA0 + 2 * j + 1);
+        r.qa1 = __ldg(KA1 + 2 * j);
+        r.ta1 = __ldg(KA1 + 2 * j + 1);
+        if (two) {
+          r.qb0 = __ldg(KB0 + 2 * j);
+          r.tb0 = __ldg(KB0 + 2 * j + 1);
+          r.qb1 = __ldg(KB1 + 2 * j);
+          r.tb1 = __ldg(KB1 + 2 * j + 1);
+        }
+        sts_aff(P + c * cs4 + 3 * j, sample_local(r, b.alpha[c], b.blend[c], two));
+      }
+    } else {
+      pass1a_qt(b, P, cs4, a.q, a.t, tid);
+    }
+    compute_sync();
+
+    // ---- pass 1b: running products along segments
+    pass1b(b, P, cs4, tid);
+    compute_sync();
 
     // ---- pass 2: pointer jumping over segments
-    const float4 *Y = scan_pass2(s, P, cs4, Y0, Y1, C, tid, nth);
+    const float4 *Y = pass2(b, P, cs4, Y0, Y1, tid);
 
     // ---- pass 3: model pose, bind, stage in place
     {
-      const int CN = C * n;
-      for (int idx = tid; idx < CN; idx += nth) {
-        const int c = (int)s.divN.div(idx), j = idx - c * n;
-        Aff m = scan_model(s, P, cs4, Y, c, j);
-        if (MODEL && SKIN) stg_aff(reinterpret_cast<float4 *>(a.model) + (sOff[c] + j) * 3, m);
-        if (SKIN) m = aff_mul(m, ldg_aff(s.T.inv_bind + 3 * j));
-        sts_aff(P + c * cs4 + 3 * j, m);
+      const int W = n * b.cgroups, cpt = b.cpt;
+      for (int idx = tid; idx < W; idx += kComputeThreads) {
+        const int grp = (int)b.divN.div(idx), j = idx - grp * n;
+        const uint32_t info = __ldg(b.T.jinfo + j);
+        const int g = (int)(info & 0xFFFFu);
+        Aff B;
+        if (SKIN) B = ldg_aff(b.T.inv_bind + 3 * j);
+        const int c1 = min(C, (grp + 1) * cpt);
+        for (int c = grp * cpt; c < c1; ++c) {
+          float4 *slot = P + c * cs4 + 3 * j;
+          Aff m = lds_aff(slot);
+          if (info & kJLink) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
+          if (MODEL && SKIN) stg_aff(reinterpret_cast<float4 *>(a.model) + (b.off[c] + j) * 3, m);
+          if (SKIN) m = aff_mul(m, B);
+          sts_aff(slot, m);
+        }
       }
     }
     fence_proxy_async_smem();
-    __syncthreads();
+    compute_sync();
     if (tid == 0) {
       float *dst = SKIN ? a.skin : a.model;
       const uint32_t bytes = (uint32_t)n * 48u;
-      for (int c = 0; c < C; ++c) bulk_store(dst + sOff[c] * 12, P + c * cs4, bytes);
+      for (int c = 0; c < C; ++c) bulk_store(dst + b.off[c] * 12, P + c * cs4, bytes);
       bulk_commit();
       pending = true;
     }
+    cur ^= 1;
+    handoff_sync();
   }
   if (tid == 0 && pending) bulk_wait_all();
 }
@@ -189,10 +168,7 @@ cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaS
 }
 
 // ------------------------------------------------------------ work queue
-// One CTA: counting sort of the characters by (type rank, key index k0),
-// then the items (at most cap[type] characters sharing type and k0) in
-// that order, so the most costly types come first.
-constexpr int kBucketThreads = 1024;
+constexpr int kBucketThreads = 256;
 
 __device__ __forceinline__ int key_index(float tm, float rate, int nk, int *status) {
   if (!isfinite(tm)) {
@@ -231,91 +207,102 @@ __device__ int block_excl_scan(int v, int *warp_sums, int *total) {
   return before;
 }
 
+// One CTA per range of <= kRangeChars characters of one type: counting sort
+// by key index k0 in shared memory, items of <= cap characters per (k0) bin
+// written to the range's slot region.  The last CTA compacts all regions in
+// range order (types most costly first) and resets the queue counter.
 __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
-  __shared__ int s_hist[kMaxBins];
-  __shared__ int s_start[kMaxBins];
-  __shared__ int s_cursor[kMaxBins];
-  __shared__ int s_tbase[kMaxTypes];
+  __shared__ int s_hist[ANIM_MAX_KEYS_DEV];
+  __shared__ int s_start[ANIM_MAX_KEYS_DEV];
+  __shared__ int s_istart[ANIM_MAX_KEYS_DEV];
   __shared__ int s_warp[32];
-  __shared__ int s_nbins, s_total;
+  __shared__ int s_rpre[kMaxRanges + 1];
+  __shared__ int s_total, s_itotal, s_last;
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int t = tid; t < a.n_types; t += nth) s_tbase[t] = -1;
+  const RangeDev R = a.ranges[blockIdx.x];
+  const int nk = a.types[R.type].n_keys;
+  const float rate = a.types[R.type].rate;
+  const int cap = a.cap[R.type];
+  for (int b = tid; b < nk; b += nth) s_hist[b] = 0;
   __syncthreads();
-  if (tid == 0) {
-    int base = 0;
-    for (int r = 0; r < a.n_used; ++r) {
-      const int t = a.used[r];
-      s_tbase[t] = base;
-      base += a.types[t].n_keys;
-    }
-    s_nbins = base;
+  int cid = -1, k = 0, pos = 0;
+  if (tid < R.count) {
+    cid = __ldg(a.type_chars + R.start + tid);
+    k = key_index(__ldg(a.time + cid), rate, nk, a.status);
+    pos = atomicAdd(&s_hist[k], 1);  // rank inside the bin
   }
   __syncthreads();
-  const int nb = s_nbins;
-  for (int b = tid; b < nb; b += nth) {
-    s_hist[b] = 0;
-    s_cursor[b] = 0;
+  // exclusive scans over the bins: character starts and item starts
+  const int per = (nk + nth - 1) / nth;
+  const int b0 = min(nk, tid * per), b1 = min(nk, b0 + per);
+  int run = 0, irun = 0;
+  for (int b = b0; b < b1; ++b) {
+    run += s_hist[b];
+    irun += (s_hist[b] + cap - 1) / cap;
   }
-  __syncthreads();
-  for (int64_t c = tid; c < a.n_chars; c += nth) {
-    const int t = a.char_type[c];
-    const int b = s_tbase[t] + key_index(a.time[c], a.types[t].rate, a.types[t].n_keys, a.status);
-    atomicAdd(&s_hist[b], 1);
-  }
-  __syncthreads();
-  // exclusive scan of the histogram: each thread owns a run of bins
-  const int per = (nb + nth - 1) / nth;
-  const int b0 = min(nb, tid * per), b1 = min(nb, b0 + per);
-  int run = 0;
-  for (int b = b0; b < b1; ++b) run += s_hist[b];
   int pre = block_excl_scan(run, s_warp, &s_total);
+  int ipre = block_excl_scan(irun, s_warp, &s_itotal);
   for (int b = b0; b < b1; ++b) {
     s_start[b] = pre;
+    s_istart[b] = ipre;
     pre += s_hist[b];
+    ipre += (s_hist[b] + cap - 1) / cap;
   }
   __syncthreads();
-  // scatter character ids into their bins
-  for (int64_t c = tid; c < a.n_chars; c += nth) {
-    const int t = a.char_type[c];
-    const int b = s_tbase[t] + key_index(a.time[c], a.types[t].rate, a.types[t].n_keys, a.status);
-    const int pos = atomicAdd(&s_cursor[b], 1);
-    a.sorted[s_start[b] + pos] = (int32_t)c;
-  }
-  __syncthreads();  // every scatter is done before s_cursor is reused below
-  // items: bin b holds ceil(hist/cap) of them; type of a bin found by rank
-  int nit = 0;
+  if (cid >= 0) a.sorted[R.start + s_start[k] + pos] = cid;
   for (int b = b0; b < b1; ++b) {
-    int r = 0;
-    while (r + 1 < a.n_used && s_tbase[a.used[r + 1]] <= b) ++r;
-    const int cap = a.cap[a.used[r]];
-    s_cursor[b] = (s_hist[b] + cap - 1) / cap;  // reuse: items of the bin
-    nit += s_cursor[b];
-  }
-  int ipre = block_excl_scan(nit, s_warp, &s_total);
-  for (int b = b0; b < b1; ++b) {
-    int r = 0;
-    while (r + 1 < a.n_used && s_tbase[a.used[r + 1]] <= b) ++r;
-    const int t = a.used[r];
-    const int cap = a.cap[t];
     const int cnt = s_hist[b];
-    for (int k = 0; k < s_cursor[b]; ++k) {
+    for (int m = 0; m * cap < cnt; ++m) {
       WorkItem w;
-      w.start = s_start[b] + k * cap;
-      w.count = min(cap, cnt - k * cap);
-      w.type = t;
-      w.k0 = b - s_tbase[t];
-      a.items[ipre + k] = w;
+      w.start = R.start + s_start[b] + m * cap;
+      w.count = min(cap, cnt - m * cap);
+      w.type = R.type;
+      w.k0 = b;
+      a.regions[R.region + s_istart[b] + m] = w;
     }
-    ipre += s_cursor[b];
+  }
+  if (tid == 0) a.range_items[blockIdx.x] = s_itotal;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(a.done, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  // last CTA: compact the regions in range order (ranges are in type cost
+  // order, so the persistent kernel meets the most costly items first)
+  __threadfence();
+  const int nr = a.n_ranges;  // <= kMaxRanges (checked on the host)
+  const int rper = (nr + nth - 1) / nth;
+  const int r0 = min(nr, tid * rper), r1 = min(nr, r0 + rper);
+  int cnt = 0;
+  for (int r = r0; r < r1; ++r) cnt += __ldcg(a.range_items + r);
+  int dst = block_excl_scan(cnt, s_warp, &s_total);
+  for (int r = r0; r < r1; ++r) {
+    s_rpre[r] = dst;
+    dst += __ldcg(a.range_items + r);
+  }
+  if (tid == 0) s_rpre[nr] = s_total;
+  __syncthreads();
+  const int total = s_total;
+#pragma unroll 4
+  for (int i = tid; i < total; i += nth) {
+    int lo = 0, hi = nr - 1;  // last range with s_rpre[r] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_rpre[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int4 v = __ldcg(reinterpret_cast<const int4 *>(a.regions + a.ranges[lo].region + (i - s_rpre[lo])));
+    reinterpret_cast<int4 *>(a.items)[i] = v;
   }
   if (tid == 0) {
-    *a.n_items = s_total;
+    *a.n_items = total;
     *a.queue_head = 0;
+    *a.done = 0;
   }
 }
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st) {
-  k_bucket<<<1, kBucketThreads, 0, st>>>(a);
+  if (a.n_ranges == 0) return cudaSuccess;
+  k_bucket<<<a.n_ranges, kBucketThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -4,60 +4,186 @@
 // matrices on the root-to-i path.  The paper evaluates it with one thread per
 // joint, pointer jumping and block barriers (Sec. 3, Algs. 2-4).  Here the
 // tree is cut into segments (runs of consecutive joints where each joint is
-// the parent of the next, at most seg_len long) and the product is formed in
-// three passes over a work item of C characters staged in shared memory:
-//   pass 1  one lane per (segment, character) walks its segment and writes
-//           the running product P_j = L_first ... L_j (work-efficient: one
-//           3x4 product per joint);
-//   pass 2  pointer jumping over the segment tree (the paper's doubling idea
-//           applied to segments instead of joints): Y_g starts as the
-//           partial product at the joint the segment hangs from and, after
-//           ceil(log2(segment depth)) rounds, is the model pose of that joint;
-//   pass 3  one thread per (character, joint): M_j = Y_seg(j) P_j, then the
-//           Bind MeshPose product S_j = M_j B_j, written back in place.
+// the parent of the next, at most seg_len long) and a work item of C
+// characters is processed in shared memory:
+//   pass 1a  every (joint, character) builds its local matrix L_j: the
+//            Simulation math, fully parallel;
+//   pass 1b  one lane per (segment, character) walks its segment and
+//            replaces L_j by the running product P_j = L_first ... L_j
+//            (work-efficient: one 3x4 product per joint, light serial work);
+//   pass 2   pointer jumping over the segment tree (the paper's doubling idea
+//            applied to segments instead of joints): Y_g starts as the
+//            partial product at the joint the segment hangs from and, after
+//            ceil(log2(segment depth)) rounds, is the model pose of that joint;
+//   pass 3   M_j = Y_seg(j) P_j, then the Bind MeshPose product S_j = M_j B_j,
+//            written back in place; one thread per joint walks a group of the
+//            item's characters so B_j is loaded once per group.
+//
+// CTA layout: kComputeWarps warps run the passes and synchronize among
+// themselves on named barrier 1; one producer warp fetches the next work
+// item (queue counter, descriptor, type table, per-character data) into the
+// other half of a double buffer and hands it over on named barrier 2.
 #pragma once
 #include "anim_internal.h"
 #include "dev_math.cuh"
 
 namespace anim {
 
-// Per-item constants staged in shared memory by the kernels.
-struct ItemSmem {
+constexpr int kComputeWarps = 8;
+constexpr int kComputeThreads = kComputeWarps * 32;
+constexpr int kCtaThreads = kComputeThreads + 32;
+static_assert(kCtaThreads == kPersistentThreads, "CTA shape");
+constexpr int kCMax = 64;  // characters per work item
+
+__device__ __forceinline__ void compute_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kComputeThreads) : "memory");
+}
+__device__ __forceinline__ void handoff_sync() { asm volatile("bar.sync 2, %0;" ::"n"(kCtaThreads) : "memory"); }
+
+// Everything one work item needs besides the big buffers (double-buffered).
+struct ItemBuf {
   TypeDev T;
-  WorkItem wi;
   FastDiv divC, divS, divN;  // by C, by nseg, by n
-  int item;
+  int item;                  // -1: no more work
+  int C, k0, type;
+  int cgroups, cpt;          // pass 3: character groups and characters per group
+  long long off[kCMax];      // first row of each character
+  int cid[kCMax];
+  float alpha[kCMax];        // frame: fraction between keys k0 and k0+1
+  float blend[kCMax];        // frame: clip blend weight
 };
 
-__device__ __forceinline__ void load_type_smem(ItemSmem &s, const TypeDev *types, int type, int tid, int nth) {
-  const int *src = reinterpret_cast<const int *>(types + type);
-  int *dst = reinterpret_cast<int *>(&s.T);
-  for (int k = tid; k < (int)(sizeof(TypeDev) / 4); k += nth) dst[k] = src[k];
+// Producer warp: grab the next item from the queue and stage its data.
+// MODE 0 (frame) also computes each character's key fraction.
+template <int MODE>
+__device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_items, const WorkItem *items,
+                                           const TypeDev *types, const int32_t *item_chars, const int64_t *row_off,
+                                           const float *time, const float *blend_w, int *status) {
+  const int lane = threadIdx.x & 31;
+  int it = 0;
+  if (lane == 0) it = atomicAdd(queue_head, 1);
+  it = __shfl_sync(0xffffffffu, it, 0);
+  if (it >= n_items) {
+    if (lane == 0) b.item = -1;
+    __syncwarp();
+    return;
+  }
+  const WorkItem wi = items[it];
+  const int *src = reinterpret_cast<const int *>(types + wi.type);
+  int *dst = reinterpret_cast<int *>(&b.T);
+  for (int k = lane; k < (int)(sizeof(TypeDev) / 4); k += 32) dst[k] = src[k];
+  const float rate = types[wi.type].rate;
+  for (int c = lane; c < wi.count; c += 32) {
+    const int cid = __ldg(item_chars + wi.start + c);
+    b.cid[c] = cid;
+    b.off[c] = row_off[cid];
+    if (MODE == 0) {
+      const float tm = __ldg(time + cid);
+      float al = 0.f;
+      if (isfinite(tm)) {
+        const float u = __fmul_rn(tm, rate);
+        al = u - floorf(u);
+      } else {
+        atomicOr(status, 1);
+      }
+      b.alpha[c] = al;
+      b.blend[c] = __ldg(blend_w + cid);
+    }
+  }
+  if (lane == 0) {
+    const int n = types[wi.type].n, nseg = types[wi.type].nseg;
+    b.item = it;
+    b.C = wi.count;
+    b.k0 = wi.k0;
+    b.type = wi.type;
+    b.divC.init(wi.count);
+    b.divS.init(nseg);
+    b.divN.init(n);
+    int g = (kComputeThreads + n - 1) / n;
+    g = g < 1 ? 1 : (g > wi.count ? wi.count : g);
+    b.cpt = (wi.count + g - 1) / g;
+    b.cgroups = (wi.count + b.cpt - 1) / b.cpt;
+  }
+  __syncwarp();
+}
+
+// Producer warp main loop: keep one item ahead of the compute warps.
+template <int MODE>
+__device__ __forceinline__ void producer_loop(ItemBuf *bufs, int *queue_head, int n_items, const WorkItem *items,
+                                              const TypeDev *types, const int32_t *item_chars,
+                                              const int64_t *row_off, const float *time, const float *blend_w,
+                                              int *status) {
+  int cur = 0;
+  fetch_item<MODE>(bufs[0], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status);
+  __threadfence_block();
+  handoff_sync();
+  while (bufs[cur].item >= 0) {
+    cur ^= 1;
+    fetch_item<MODE>(bufs[cur], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status);
+    __threadfence_block();
+    handoff_sync();
+  }
+}
+
+// Pass 1a from given local poses (q normalized here, t), optionally through a
+// gather map (IK views).  Character-major so consecutive lanes read
+// consecutive rows.
+__device__ __forceinline__ void pass1a_qt(const ItemBuf &b, float4 *P, int cs4, const float *q_all,
+                                          const float *t_all, int tid) {
+  const int n = b.T.n, CN = b.C * n;
+  const int32_t *gat = b.T.gather;
+  const float4 *q4 = reinterpret_cast<const float4 *>(q_all);
+#pragma unroll 2
+  for (int idx = tid; idx < CN; idx += kComputeThreads) {
+    const int c = (int)b.divN.div(idx), j = idx - c * n;
+    const long long row = b.off[c] + (gat ? __ldg(gat + j) : j);
+    const float4 q = normalize4(__ldg(q4 + row));
+    const float *tp = t_all + 3 * row;
+    sts_aff(P + c * cs4 + 3 * j, aff_from_qt(q, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2)));
+  }
+}
+
+// Pass 1b: running products along each segment, in place.
+__device__ __forceinline__ void pass1b(const ItemBuf &b, float4 *P, int cs4, int tid) {
+  const int C = b.C, NS = b.T.nseg * C;
+  for (int idx = tid; idx < NS; idx += kComputeThreads) {
+    const int g = (int)b.divC.div(idx), c = idx - g * C;
+    const int a0 = __ldg(b.T.seg_start + g), a1 = __ldg(b.T.seg_start + g + 1);
+    float4 *Pc = P + c * cs4;
+    Aff acc = lds_aff(Pc + 3 * a0);
+    if (a0 + 1 >= a1) continue;
+    Aff nxt = lds_aff(Pc + 3 * (a0 + 1));
+    for (int j = a0 + 1; j < a1; ++j) {
+      const Aff L = nxt;
+      if (j + 1 < a1) nxt = lds_aff(Pc + 3 * (j + 1));
+      acc = aff_mul(acc, L);
+      sts_aff(Pc + 3 * j, acc);
+    }
+  }
 }
 
 // Pass 2 + its barriers.  Returns the buffer holding the final Y.
-__device__ __forceinline__ float4 *scan_pass2(const ItemSmem &s, float4 *P, int cs4, float4 *Y0, float4 *Y1,
-                                              int C, int tid, int nth) {
-  const int nseg = s.T.nseg;
-  const int CS = C * nseg;
-  for (int idx = tid; idx < CS; idx += nth) {
-    const int c = (int)s.divS.div(idx), g = idx - c * nseg;
-    const int lk = __ldg(s.T.seg_link + g);
+__device__ __forceinline__ float4 *pass2(const ItemBuf &b, float4 *P, int cs4, float4 *Y0, float4 *Y1, int tid) {
+  const int nseg = b.T.nseg;
+  const int CS = b.C * nseg;
+  for (int idx = tid; idx < CS; idx += kComputeThreads) {
+    const int c = (int)b.divS.div(idx), g = idx - c * nseg;
+    const int lk = __ldg(b.T.seg_link + g);
     const Aff y = lk < 0 ? aff_identity() : lds_aff(P + c * cs4 + 3 * lk);
     sts_aff(Y0 + 3 * idx, y);
   }
-  __syncthreads();
+  compute_sync();
   float4 *cur = Y0, *nxt = Y1;
-  for (int r = 0; r < s.T.rounds; ++r) {
-    const int16_t *jr = s.T.jump + (size_t)r * nseg;
-    for (int idx = tid; idx < CS; idx += nth) {
-      const int c = (int)s.divS.div(idx), g = idx - c * nseg;
+  for (int r = 0; r < b.T.rounds; ++r) {
+    const int16_t *jr = b.T.jump + (size_t)r * nseg;
+    for (int idx = tid; idx < CS; idx += kComputeThreads) {
+      const int c = (int)b.divS.div(idx), g = idx - c * nseg;
       const int p = __ldg(jr + g);
       Aff y = lds_aff(cur + 3 * idx);
       if (p >= 0) y = aff_mul(lds_aff(cur + 3 * (c * nseg + p)), y);
       sts_aff(nxt + 3 * idx, y);
     }
-    __syncthreads();
+    compute_sync();
     float4 *tmp = cur;
     cur = nxt;
     nxt = tmp;
@@ -65,13 +191,9 @@ __device__ __forceinline__ float4 *scan_pass2(const ItemSmem &s, float4 *P, int 
   return cur;
 }
 
-// Model pose of joint j of character c after pass 2 (P holds P_j).
-__device__ __forceinline__ Aff scan_model(const ItemSmem &s, const float4 *P, int cs4, const float4 *Y, int c,
-                                          int j) {
-  Aff m = lds_aff(P + c * cs4 + 3 * j);
-  const int g = __ldg(s.T.seg_of + j);
-  if (__ldg(s.T.seg_link + g) >= 0) m = aff_mul(lds_aff(Y + 3 * (c * s.T.nseg + g)), m);
-  return m;
+// Bytes of shared memory a work item of C characters needs.
+__host__ __device__ inline size_t scan_item_bytes(int n, int nseg, int C) {
+  return 16ull * ((size_t)C * (3 * (size_t)n + 1) + 6ull * C * nseg);
 }
 
 }  // namespace anim
