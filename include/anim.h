@@ -216,6 +216,38 @@ ANIM_API int anim_get_status(anim_ctx *ctx, void *stream, int *out_status);
 ANIM_API int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, int32_t *out_nseg,
                           int32_t *out_seg_start, int32_t *out_rounds, int32_t *out_depth);
 
+/* Forward scan + bind for callers that cannot allocate device memory.
+ * (No counterpart in the paper: this is a deployment variant of
+ * anim_forward_local.)  Some callers may not call cudaMalloc at all: code
+ * running under a fixed device-memory budget or a custom allocator that owns
+ * every byte, plug-ins handed only pre-allocated buffers by their host, or
+ * processes that must not grow their footprint after start-up.  This entry
+ * point creates no context or plan and allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call): its scratch -- the skeleton's segment
+ * tables, the record the kernel reads and the work-queue counter -- lives in
+ * a 96 KB static device array that every GPU loading the library holds
+ * until the process exits.
+ *   n_joints            : 1 .. ANIM_MAX_JOINTS joints of the one skeleton type;
+ *   parents             : host [n_joints], parent[i] in [-1, i-1];
+ *   n_chars             : 0 .. 16,777,216 characters of that type, character c
+ *                         at rows c*n_joints .. c*n_joints + n_joints - 1;
+ *   d_q, d_t            : device [n_chars*n_joints][4] (unnormalized allowed) and
+ *                         [n_chars*n_joints][3] local poses;
+ *   d_inv_bind          : device [n_joints][12] inverse bind poses;
+ *   d_skin              : device [n_chars*n_joints][12], written.
+ * d_q, d_inv_bind and d_skin must be 16-byte aligned.  Returns ANIM_EINVAL
+ * (NULL pointer, bad parent, misalignment), ANIM_EUNSUPPORTED (a size beyond
+ * the limits above) or ANIM_ECUDA; there is no message string.  The first call
+ * on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Each call writes the tables into the array
+ * with an asynchronous copy on `stream` and launches the kernel after it:
+ * every call shares the one array, so calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialized by the
+ * caller. */
+ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *parents, int64_t n_chars, const float *d_q,
+                                        const float *d_t, const float *d_inv_bind, float *d_skin, void *stream);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 ANIM_API int anim_version(void);
 

@@ -46,6 +46,7 @@ SIGNATURES = {
     "anim_tune": (c_int, [_P, _P, c_int]),
     "anim_get_status": (c_int, [_P, _P, POINTER(c_int)]),
     "anim_analyze_skeleton": (c_int, [c_int, _P, c_int, POINTER(c_int32), _P, POINTER(c_int32), POINTER(c_int32)]),
+    "anim_forward_local_noalloc": (c_int, [c_int, _P, c_int64, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
