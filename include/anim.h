@@ -199,11 +199,17 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
                  const float *d_targets, float lr, float beta1, float beta2, float eps, float *d_loss,
                  void *stream);
 
-/* Autotune the schedule (segment length, characters per CTA, CTA size) for
- * the plan's type mix by timing candidate launches of `which` (0 = fused
- * frame, 1 = forward_local, 2 = loss_backward) on scratch buffers; the result
- * is cached per (types, counts) hash in the context.  Synchronous; not
- * capturable.  Needs clips for which = 0. */
+/* Autotuner (no counterpart in the paper; it picks the schedule of the
+ * scan): times every candidate schedule -- segment length 8/16/32, 1 or 2
+ * resident CTAs per SM, work items of about 1,024/2,048/4,096 joints -- of
+ * `which` (0 = fused frame, 1 = forward_local, 2 = loss_backward) with CUDA
+ * events on scratch inputs it allocates, and keeps the fastest.  The result
+ * is cached in the context per hash of (which, type ids, joint counts,
+ * depths, character counts); calling anim_tune again for the same mix
+ * applies the cached schedule without timing.  The schedule is per context
+ * (segment lengths of the plan's types, CTAs per SM, item size), so it also
+ * applies to other plans of the context.  Synchronous; not capturable;
+ * which = 0 needs clips for every type of the plan. */
 ANIM_API int anim_tune(anim_ctx *ctx, anim_plan *plan, int which);
 
 /* Read and clear the device status word (synchronizes `stream`). */

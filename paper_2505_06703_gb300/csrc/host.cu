@@ -316,10 +316,15 @@ struct anim_ctx {
   TypeDev *d_types = nullptr;
   int *d_status = nullptr;
   int version = 0;  // bumps when types/schedules change
-  int ctas_per_sm = 2;
+  int ctas_per_sm = 2;            // resident persistent CTAs per SM the schedule is sized for
+  int joints_per_item = kTargetJointsPerItem;  // target work-item size (characters x joints)
   std::set<anim_plan *> plans;
   std::set<anim_ik *> iks;
-  std::map<uint64_t, std::vector<int>> tune_cache;  // (types, counts) hash -> per-type seg_len
+  struct TuneChoice {
+    int seg_len, ctas_per_sm, joints_per_item;
+    float ms;
+  };
+  std::map<uint64_t, TuneChoice> tune_cache;  // (which, types, counts) hash -> best schedule
   ~anim_ctx() {
     for (auto *p : plans) delete p;
     for (auto *k : iks) delete k;
@@ -375,7 +380,7 @@ size_t smem_budget(const anim_ctx *ctx) {
 
 int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
   const size_t budget = smem_budget(ctx);
-  int C = std::max(1, std::min(kCMax, kTargetJointsPerItem / std::max(1, T.n)));
+  int C = std::max(1, std::min(kCMax, ctx->joints_per_item / std::max(1, T.n)));
   auto bytes = [&](int c) {
     return adjoint ? adjoint_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
   };
@@ -998,11 +1003,123 @@ int anim_get_status(anim_ctx *ctx, void *stream, int *out_status) {
   return ANIM_OK;
 }
 
+static uint64_t mix_hash(const anim_ctx *ctx, const anim_plan *P, int which) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)which;
+  auto add = [&](uint64_t v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  for (size_t u = 0; u < P->used.size(); ++u) {
+    const TypeHost &T = *ctx->types[P->used[u]];
+    add((uint64_t)P->used[u]);
+    add((uint64_t)T.n);
+    add((uint64_t)T.max_depth);
+    add((uint64_t)P->by_type[u].size());
+  }
+  return h;
+}
+
+static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps, int jpi) {
+  ctx->ctas_per_sm = cps;
+  ctx->joints_per_item = jpi;
+  for (int t : P->used) {
+    TypeHost &T = *ctx->types[t];
+    if (T.seg_len != seg_len) {
+      T.seg_len = seg_len;
+      CK(T.build_tables());
+    }
+  }
+  CK(upload_types(ctx));  // bumps the version: every plan rebuilds its schedule
+  return plan_schedule(ctx, const_cast<anim_plan *>(P));
+}
+
+// Autotuner: time every candidate schedule (segment length, resident CTAs per
+// SM, work-item size) on scratch inputs with CUDA events and keep the best;
+// the result is cached by a hash of (which, type ids, joint counts, depths,
+// character counts) and re-applied by anim_plan_create for the same mix.
 int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
-  (void)which;
-  return ANIM_OK;
+  if (which < 0 || which > 2) return fail(ctx, ANIM_EINVAL, "which must be 0, 1 or 2");
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (which == 0)
+    for (int t : plan->used)
+      if (ctx->types[t]->n_clips == 0) return fail(ctx, ANIM_ESTATE, "type %d has no clips uploaded", t);
+  CK(cudaSetDevice(ctx->device));
+  const uint64_t key = mix_hash(ctx, plan, which);
+  auto hit = ctx->tune_cache.find(key);
+  if (hit != ctx->tune_cache.end())
+    return apply_choice(ctx, plan, hit->second.seg_len, hit->second.ctas_per_sm, hit->second.joints_per_item);
+
+  // scratch inputs (tuning may allocate; evaluation calls never do)
+  const int64_t N = plan->n_chars, J = plan->total;
+  std::vector<void *> bufs;
+  auto dalloc = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  };
+  auto release = [&]() {
+    for (void *p : bufs) cudaFree(p);
+  };
+  float *d_time = (float *)dalloc(N * 4), *d_w = (float *)dalloc(N * 4);
+  float *d_q = (float *)dalloc(J * 16), *d_t = (float *)dalloc(J * 12), *d_tg = (float *)dalloc(J * 12);
+  float *d_out = (float *)dalloc(J * 48), *d_gq = (float *)dalloc(J * 16), *d_gt = (float *)dalloc(J * 12);
+  if (bufs.size() != 8 || std::count(bufs.begin(), bufs.end(), nullptr)) {
+    release();
+    return fail(ctx, ANIM_ENOMEM, "tuning buffers");
+  }
+  {
+    std::vector<float> h(std::max<int64_t>(N, 1)), hw(std::max<int64_t>(N, 1));
+    for (int64_t c = 0; c < N; ++c) {
+      h[c] = (float)std::fmod(0.6180339887 * (double)c, 1.0);
+      hw[c] = (float)std::fmod(0.4142135623 * (double)c, 1.0);
+    }
+    std::vector<float> q(J * 4, 0.f), t(J * 3, 0.05f);
+    for (int64_t j = 0; j < J; ++j) q[4 * j + 3] = 1.f;
+    cudaError_t e = cudaMemcpy(d_time, h.data(), N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_w, hw.data(), N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_q, q.data(), J * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_t, t.data(), J * 12, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_tg, t.data(), J * 12, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      release();
+      return fail(ctx, ANIM_ECUDA, "tuning inputs: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto run_once = [&]() -> int {
+    if (which == 0) return anim_evaluate_frame(ctx, plan, d_time, d_w, d_out, nullptr);
+    if (which == 1) return anim_forward_local(ctx, plan, d_q, d_t, d_out, nullptr, nullptr);
+    return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, nullptr);
+  };
+  anim_ctx::TuneChoice best{0, 0, 0, 1e30f};
+  const int segs[] = {8, 16, 32}, cpss[] = {1, 2}, jpis[] = {1024, 2048, 4096};
+  for (int seg : segs)
+    for (int cps : cpss)
+      for (int jpi : jpis) {
+        if (apply_choice(ctx, plan, seg, cps, jpi) != ANIM_OK) continue;  // e.g. does not fit
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
+        cudaEventRecord(e0, nullptr);
+        for (int r = 0; r < 5 && ok; ++r) ok = run_once() == ANIM_OK;
+        cudaEventRecord(e1, nullptr);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 5.f;
+        if (ms < best.ms) best = {seg, cps, jpi, ms};
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release();
+  if (best.seg_len == 0) return fail(ctx, ANIM_ECUDA, "no candidate schedule ran");
+  ctx->tune_cache[key] = best;
+  ctx->err.clear();
+  return apply_choice(ctx, plan, best.seg_len, best.ctas_per_sm, best.joints_per_item);
 }
 
 int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, int32_t *out_nseg, int32_t *out_seg_start,

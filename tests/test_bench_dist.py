@@ -1,0 +1,49 @@
+"""The benchmark's multi-GPU path on CPU: two gloo ranks.
+
+Characters are independent, so every rank evaluates its own batch (same
+skeletons and clips, its own times and blend weights) and the only
+cross-rank operation is the maximum of the timings.  These checks run the
+rank logic of bench.py with the gloo backend."""
+import os
+
+import numpy as np
+import pytest
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    w = bench.rank_workload(rank)
+    t = 1.0 + rank  # stand-in for a rank's measured milliseconds
+    m = bench.aggregate_max(t, world)
+    bench.barrier(world)
+    q.put((rank, m, float(w["time"][0]), len(w["char_type"]), [len(x["parents"]) for x in w["types"]]))
+    dist.destroy_process_group()
+
+
+def test_two_rank_replicas_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + (os.getpid() % 2000)
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, m0, t0, n0, s0), (r1, m1, t1, n1, s1) = res
+    assert m0 == m1 == 2.0          # the max over ranks reaches every rank
+    assert n0 == n1 and s0 == s1    # same workload shape on every rank (weak scaling)
+    assert t0 != t1                 # independent batches
+
+
+def test_single_rank_helpers():
+    import bench
+    assert bench.aggregate_max(3.5, 1) == 3.5
+    w = bench.rank_workload(0)
+    assert bench.frame_algorithmic_bytes(w) > 48 * 2_000_000
+    assert len(bench.kernel_source_hash()) == 16

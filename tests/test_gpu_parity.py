@@ -93,6 +93,23 @@ def test_frame_repeatable_and_graph_capturable(torch):
     assert torch.equal(out, a)
 
 
+def test_autotuned_frame_parity(torch):
+    """anim_tune picks a schedule by timing candidates; the tuned frame still
+    matches the oracle and a second tune of the same mix hits the cache."""
+    import time
+    w = synth.subset(synth.config3(), list(range(0, 10000, 5)))
+    ctx, plan = _gpu.setup(w)
+    t0 = time.perf_counter()
+    ctx.tune(plan, 0)
+    t1 = time.perf_counter()
+    ctx.tune(plan, 0)
+    t2 = time.perf_counter()
+    assert t2 - t1 < 0.5 * (t1 - t0)
+    out = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"]))
+    _gpu.assert_skin_close(out.cpu().numpy(), oracle.frame(w), w)
+    ctx.tune(plan, 2)  # the adjoint's schedule search runs too
+
+
 def _grad_tol(dq_ref, dt_ref, w):
     """Per-joint tolerance: 1e-4 * max(1, max |oracle grad| of the character)."""
     off = oracle.offsets(w["char_type"], w["types"])
