@@ -229,6 +229,7 @@ def run_ours(args) -> dict:
 
     w = rank_workload(rank)
     ctx, plan = setup_ctx(w, local)
+    ctx.tune(plan, 0)  # the library's autotuner picks the schedule for this mix
     joints = plan.total
     n_chars = plan.n_chars
     out_bytes = joints * 48
@@ -321,6 +322,7 @@ def run_ours(args) -> dict:
                          "joints_per_step_per_gpu": joints, "characters_per_gpu": n_chars,
                          "l2": f"output rotated over {n_out} buffers ({n_out * out_bytes / 1e6:.0f} MB > 129 MB L2)",
                          "timing": "CUDA graphs (work queue + persistent kernel), CUDA events",
+                         "schedule": "anim_tune (segment length, CTAs/SM, item size)",
                          "parallelism": f"replicas x{world} (independent character batches)"},
               "roofline": roofline, "gpu_launches": 2 * steps, "clocks": clock}
 
@@ -370,6 +372,7 @@ def run_fwd_bwd(ctx_factory, device, dev, steps, warmup, world, peak):
     import torch
     w = synth.config4()
     ctx, plan = ctx_factory(w, device)
+    ctx.tune(plan, 2)
     joints = plan.total
     n_sets = max(2, math.ceil(2.5 * L2_BYTES / (joints * 68)))
     sets = []

@@ -88,13 +88,13 @@ struct ScanArgs {
 cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 // Frame work queue.  The plan cuts the characters of each type (types in
-// cost order) into ranges of at most kRangeChars.  One CTA per range sorts its
-// characters by key index k0 (counting sort in shared memory) and emits work
-// items of at most cap[type] characters sharing (type, k0) into the range's
-// slot region; the last CTA to finish compacts the regions, in range order,
-// into the item list and resets the queue counter.
+// cost order) into ranges of at most kRangeChars, each owning a region of
+// item slots large enough for any key distribution.  One CTA per range sorts
+// its characters by key index k0 (counting sort in shared memory) and writes
+// work items of at most cap[type] characters sharing (type, k0) into its
+// region, then empty items (count 0) into the rest of the region.
 constexpr int kRangeChars = 256;
-constexpr int kMaxRanges = 4096;  // so at most 1,048,576 characters per plan
+constexpr int kMaxRanges = 4096;  // so at most ~900,000 characters per plan
 struct RangeDev {
   int32_t type;
   int32_t start;   // first index into the type-grouped character list
@@ -104,17 +104,14 @@ struct RangeDev {
 struct BucketArgs {
   const RangeDev *ranges;
   int n_ranges;
+  int n_slots;                // total item slots (end of the last region)
   const int32_t *type_chars;  // characters grouped by type, plan order
   const float *time;          // [n_chars]
   const TypeDev *types;
   const int32_t *cap;         // [n_types] characters per item
   int32_t *sorted;            // same indexing as type_chars, sorted by k0 within each range
-  WorkItem *regions;          // item slots of every range
-  int32_t *range_items;       // [n_ranges]
-  WorkItem *items;            // compacted items
-  int32_t *n_items;           // [1]
+  WorkItem *items;            // [n_slots]
   int *queue_head;            // [1] reset to 0
-  int *done;                  // [1] last-CTA counter, left at 0
   int *status;
 };
 constexpr int kMaxTypes = 512;

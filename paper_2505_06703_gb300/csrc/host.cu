@@ -272,10 +272,9 @@ struct anim_plan {
   WorkItem *d_items_scan = nullptr, *d_items_adj = nullptr;
   int n_items_scan = 0, n_items_adj = 0;
   int32_t *d_sorted = nullptr;
-  WorkItem *d_items_frame = nullptr, *d_regions = nullptr;
+  WorkItem *d_items_frame = nullptr;
   RangeDev *d_ranges = nullptr;
-  int32_t *d_range_items = nullptr;
-  int n_ranges = 0;
+  int n_ranges = 0, n_slots = 0;
   int32_t *d_n_items = nullptr;
   int *d_queue = nullptr;  // [0] queue head, [1] bucket last-CTA counter
   int32_t *d_used = nullptr, *d_cap = nullptr;
@@ -283,8 +282,8 @@ struct anim_plan {
   size_t smem_frame = 0;
   ~anim_plan() {
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
-                    (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_regions,
-                    (void *)d_ranges, (void *)d_range_items, (void *)d_n_items, (void *)d_queue, (void *)d_used,
+                    (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
+                    (void *)d_n_items, (void *)d_queue, (void *)d_used,
                     (void *)d_cap})
       if (p) cudaFree(p);
   }
@@ -461,15 +460,11 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
     }
   }
   P->n_ranges = (int)ranges.size();
+  P->n_slots = slots;
   CK(upload_vec(&P->d_ranges, ranges));
-  if (P->d_regions) cudaFree(P->d_regions);
   if (P->d_items_frame) cudaFree(P->d_items_frame);
-  if (P->d_range_items) cudaFree(P->d_range_items);
-  P->d_regions = P->d_items_frame = nullptr;
-  P->d_range_items = nullptr;
-  CK(cudaMalloc(&P->d_regions, std::max(1, slots) * sizeof(WorkItem)));
+  P->d_items_frame = nullptr;
   CK(cudaMalloc(&P->d_items_frame, std::max(1, slots) * sizeof(WorkItem)));
-  CK(cudaMalloc(&P->d_range_items, std::max(1, P->n_ranges) * sizeof(int32_t)));
   const int grid = ctx->sm_count * ctx->ctas_per_sm;
   P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16)};
   P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
@@ -710,17 +705,14 @@ int anim_frame_build_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_
   BucketArgs b{};
   b.ranges = plan->d_ranges;
   b.n_ranges = plan->n_ranges;
+  b.n_slots = plan->n_slots;
   b.type_chars = plan->d_type_chars;
   b.time = d_time;
   b.types = ctx->d_types;
   b.cap = plan->d_cap;
   b.sorted = plan->d_sorted;
-  b.regions = plan->d_regions;
-  b.range_items = plan->d_range_items;
   b.items = plan->d_items_frame;
-  b.n_items = plan->d_n_items;
   b.queue_head = plan->d_queue;
-  b.done = plan->d_queue + 1;
   b.status = ctx->d_status;
   CK(launch_bucket(b, (cudaStream_t)stream));
   return ANIM_OK;
@@ -736,7 +728,7 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
   ScanArgs a{};
   a.types = ctx->d_types;
   a.items = plan->d_items_frame;
-  a.n_items_dev = plan->d_n_items;
+  a.n_items = plan->n_slots;
   a.item_chars = plan->d_sorted;
   a.row_off = plan->d_row_off;
   a.queue_head = plan->d_queue;

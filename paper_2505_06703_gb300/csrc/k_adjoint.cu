@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
     float4 *P = sm;
     float4 *Y0 = P + C * cs4;
     float4 *Y1 = Y0 + 3 * C * nseg;
-    float4 *PF = Y1 + 3 * C * nseg;  // [C][n+1]
+    float4 *PF = Y1 + 3 * C * nseg + (4 * nseg + 15) / 16;  // [C][n+1], after pass 2's pointers
     float4 *PT = PF + C * (n + 1);   // [C][n+1]
     const int32_t *gat = b.T.gather;
     const bool gath = gat != nullptr;

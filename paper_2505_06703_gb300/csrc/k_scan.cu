@@ -209,20 +209,22 @@ __device__ int block_excl_scan(int v, int *warp_sums, int *total) {
 
 // One CTA per range of <= kRangeChars characters of one type: counting sort
 // by key index k0 in shared memory, items of <= cap characters per (k0) bin
-// written to the range's slot region.  The last CTA compacts all regions in
-// range order (types most costly first) and resets the queue counter.
+// written to the range's slot region, and empty items (count 0) in the
+// region's remaining slots.  Regions are laid out in range order (types most
+// costly first); the persistent kernel's producer warp skips empty slots.
 __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
   __shared__ int s_hist[ANIM_MAX_KEYS_DEV];
   __shared__ int s_start[ANIM_MAX_KEYS_DEV];
   __shared__ int s_istart[ANIM_MAX_KEYS_DEV];
   __shared__ int s_warp[32];
-  __shared__ int s_rpre[kMaxRanges + 1];
-  __shared__ int s_total, s_itotal, s_last;
+  __shared__ int s_total, s_itotal;
   const int tid = threadIdx.x, nth = blockDim.x;
+  if (blockIdx.x == 0 && tid == 0) *a.queue_head = 0;  // consumed by the next launch in stream order
   const RangeDev R = a.ranges[blockIdx.x];
   const int nk = a.types[R.type].n_keys;
   const float rate = a.types[R.type].rate;
   const int cap = a.cap[R.type];
+  const int region_end = (blockIdx.x + 1 < a.n_ranges) ? a.ranges[blockIdx.x + 1].region : a.n_slots;
   for (int b = tid; b < nk; b += nth) s_hist[b] = 0;
   __syncthreads();
   int cid = -1, k = 0, pos = 0;
@@ -258,46 +260,11 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
       w.count = min(cap, cnt - m * cap);
       w.type = R.type;
       w.k0 = b;
-      a.regions[R.region + s_istart[b] + m] = w;
+      a.items[R.region + s_istart[b] + m] = w;
     }
   }
-  if (tid == 0) a.range_items[blockIdx.x] = s_itotal;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = atomicAdd(a.done, 1) == (int)gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  // last CTA: compact the regions in range order (ranges are in type cost
-  // order, so the persistent kernel meets the most costly items first)
-  __threadfence();
-  const int nr = a.n_ranges;  // <= kMaxRanges (checked on the host)
-  const int rper = (nr + nth - 1) / nth;
-  const int r0 = min(nr, tid * rper), r1 = min(nr, r0 + rper);
-  int cnt = 0;
-  for (int r = r0; r < r1; ++r) cnt += __ldcg(a.range_items + r);
-  int dst = block_excl_scan(cnt, s_warp, &s_total);
-  for (int r = r0; r < r1; ++r) {
-    s_rpre[r] = dst;
-    dst += __ldcg(a.range_items + r);
-  }
-  if (tid == 0) s_rpre[nr] = s_total;
-  __syncthreads();
-  const int total = s_total;
-#pragma unroll 4
-  for (int i = tid; i < total; i += nth) {
-    int lo = 0, hi = nr - 1;  // last range with s_rpre[r] <= i
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_rpre[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    const int4 v = __ldcg(reinterpret_cast<const int4 *>(a.regions + a.ranges[lo].region + (i - s_rpre[lo])));
-    reinterpret_cast<int4 *>(a.items)[i] = v;
-  }
-  if (tid == 0) {
-    *a.n_items = total;
-    *a.queue_head = 0;
-    *a.done = 0;
-  }
+  const WorkItem empty = {0, 0, R.type, 0};
+  for (int sl = R.region + s_itotal + tid; sl < region_end; sl += nth) a.items[sl] = empty;
 }
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st) {

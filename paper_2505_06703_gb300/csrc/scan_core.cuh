@@ -61,14 +61,18 @@ __device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_it
                                            const float *time, const float *blend_w, int *status) {
   const int lane = threadIdx.x & 31;
   int it = 0;
-  if (lane == 0) it = atomicAdd(queue_head, 1);
-  it = __shfl_sync(0xffffffffu, it, 0);
-  if (it >= n_items) {
-    if (lane == 0) b.item = -1;
-    __syncwarp();
-    return;
+  WorkItem wi;
+  for (;;) {  // skip empty slots of the frame's work queue
+    if (lane == 0) it = atomicAdd(queue_head, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) {
+      if (lane == 0) b.item = -1;
+      __syncwarp();
+      return;
+    }
+    wi = items[it];
+    if (wi.count > 0) break;
   }
-  const WorkItem wi = items[it];
   const int *src = reinterpret_cast<const int *>(types + wi.type);
   int *dst = reinterpret_cast<int *>(&b.T);
   for (int k = lane; k < (int)(sizeof(TypeDev) / 4); k += 32) dst[k] = src[k];
@@ -162,38 +166,47 @@ __device__ __forceinline__ void pass1b(const ItemBuf &b, float4 *P, int cs4, int
   }
 }
 
-// Pass 2 + its barriers.  Returns the buffer holding the final Y.
+// Pass 2 + its barriers.  Returns the buffer holding the final Y.  The
+// jumping pointers depend only on the skeleton, so one copy per item lives
+// in shared memory (ptr0/ptr1, double-buffered) next to the Y buffers.
 __device__ __forceinline__ float4 *pass2(const ItemBuf &b, float4 *P, int cs4, float4 *Y0, float4 *Y1, int tid) {
   const int nseg = b.T.nseg;
   const int CS = b.C * nseg;
+  int16_t *ptr0 = reinterpret_cast<int16_t *>(Y1 + 3 * CS);
+  int16_t *ptr1 = ptr0 + nseg;
   for (int idx = tid; idx < CS; idx += kComputeThreads) {
     const int c = (int)b.divS.div(idx), g = idx - c * nseg;
     const int lk = __ldg(b.T.seg_link + g);
     const Aff y = lk < 0 ? aff_identity() : lds_aff(P + c * cs4 + 3 * lk);
     sts_aff(Y0 + 3 * idx, y);
+    if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(__ldg(b.T.jinfo + lk) & 0xFFFFu));
   }
   compute_sync();
   float4 *cur = Y0, *nxt = Y1;
+  int16_t *pc = ptr0, *pn = ptr1;
   for (int r = 0; r < b.T.rounds; ++r) {
-    const int16_t *jr = b.T.jump + (size_t)r * nseg;
     for (int idx = tid; idx < CS; idx += kComputeThreads) {
       const int c = (int)b.divS.div(idx), g = idx - c * nseg;
-      const int p = __ldg(jr + g);
+      const int p = pc[g];
       Aff y = lds_aff(cur + 3 * idx);
       if (p >= 0) y = aff_mul(lds_aff(cur + 3 * (c * nseg + p)), y);
       sts_aff(nxt + 3 * idx, y);
+      if (c == 0) pn[g] = (int16_t)(p >= 0 ? pc[p] : -1);
     }
     compute_sync();
     float4 *tmp = cur;
     cur = nxt;
     nxt = tmp;
+    int16_t *tp = pc;
+    pc = pn;
+    pn = tp;
   }
   return cur;
 }
 
 // Bytes of shared memory a work item of C characters needs.
 __host__ __device__ inline size_t scan_item_bytes(int n, int nseg, int C) {
-  return 16ull * ((size_t)C * (3 * (size_t)n + 1) + 6ull * C * nseg);
+  return 16ull * ((size_t)C * (3 * (size_t)n + 1) + 6ull * C * nseg) + 16ull * ((4ull * nseg + 15) / 16);
 }
 
 }  // namespace anim
