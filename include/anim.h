@@ -200,8 +200,10 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
                  void *stream);
 
 /* Autotuner (no counterpart in the paper; it picks the schedule of the
- * scan): times every candidate schedule -- segment length 8/16/32, 1 or 2
- * resident CTAs per SM, work items of about 1,024/2,048/4,096 joints -- of
+ * scan): times every candidate schedule -- segment length 8/16/32 for the
+ * pointer-jumping scan or level-ordered chain walks for skeletons of depth
+ * <= 160, 1 or 2 resident CTAs per SM, work items of about 1,024/2,048/4,096
+ * joints -- of
  * `which` (0 = fused frame, 1 = forward_local, 2 = loss_backward) with CUDA
  * events on scratch inputs it allocates, and keeps the fastest.  The result
  * is cached in the context per hash of (which, type ids, joint counts,

@@ -39,7 +39,22 @@ struct TypeDev {
   // IK views: the active subtree of a type; view joint j reads row gather[j]
   // of the full type (nullptr = identity).
   const int32_t *gather;
+  // Walk mode (shallow skeletons): natural chains (uncut) in level order;
+  // record k = (first joint, end joint, parent of the first joint, 0).
+  int walk;                  // 1: scan by level-ordered chain walks, 0: pointer jumping over segments
+  int nlev;                  // chain levels
+  int nwrec;                 // chains
+  int pad2;
+  const int4 *wrec;          // [nwrec]
+  const int32_t *wlev;       // [nlev + 1] first record of each level
 };
+constexpr int kWalkMaxChains = 256;
+constexpr int kWalkMaxLevels = 64;
+constexpr int kWalkMaxDepth = 160;
+// Static shared memory the persistent kernels may use besides the dynamic
+// item buffers (two staged work items, scan scratch); the host subtracts it
+// from the per-CTA budget.
+constexpr int kStaticSmemAllowance = 14 * 1024;
 
 constexpr uint32_t kJStart = 1u << 16;  // joint opens its segment
 constexpr uint32_t kJLink = 1u << 17;   // the joint's segment hangs from a parent joint
@@ -71,7 +86,8 @@ struct ScanArgs {
   int n_items;
   const int32_t *item_chars;   // character ids referenced by items
   const int64_t *row_off;      // [n_chars + 1]
-  int *queue_head;             // device counter, reset to 0 before the launch
+  int *queue_head;             // device work-queue counter (0 at launch)
+  int *done;                   // finish counter for the last-CTA reset (nullptr: no reset)
   int *status;
   // sampled mode
   const float *time;
@@ -137,7 +153,8 @@ struct AdjointArgs {
   int n_items;
   const int32_t *item_chars;
   const int64_t *row_off;
-  int *queue_head;
+  int *queue_head;         // 0 at launch; reset by the last CTA
+  int *done;               // finish counter for that reset
   int *status;
   const float *q, *t;
   const float *grad_pos;   // mode 0
@@ -151,7 +168,6 @@ struct AdjointArgs {
   float *m, *v;
   float *q_mut;
   int *step;         // device step counter (read at start, incremented by the last CTA)
-  int *done_ctas;    // device counter for the last-CTA increment
   float lr, beta1, beta2, eps;
 };
 cudaError_t launch_adjoint(int mode, const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t s);

@@ -184,15 +184,52 @@ struct TypeHost {
   int n_clips = 0, n_keys = 0;
   float rate = 0.f;
   std::vector<int32_t> gather;  // IK views only
+  std::vector<int4> wrec;       // walk mode: chains in level order
+  std::vector<int32_t> wlev;
+  bool walk = false;
+  bool allow_walk = false;      // chosen by the autotuner; off by default
   TypeDev dev{};
   ~TypeHost() {
     if (d_tables) cudaFree(d_tables);
     if (d_inv_bind) cudaFree(d_inv_bind);
     if (d_keys) cudaFree(d_keys);
   }
+  // Walk mode for shallow skeletons: natural chains (uncut) ordered by chain
+  // level (a chain's parent joint lies in a lower level).
+  void analyze_walk() {
+    wrec.clear();
+    wlev.clear();
+    walk = false;
+    if (!allow_walk || max_depth > kWalkMaxDepth) return;
+    std::vector<int> cs, lev;
+    std::vector<int> chain_of(n);
+    for (int i = 0; i < n; ++i) {
+      if (i == 0 || parent[i] != i - 1) cs.push_back(i);
+      chain_of[i] = (int)cs.size() - 1;
+    }
+    const int nc = (int)cs.size();
+    if (nc > kWalkMaxChains) return;
+    cs.push_back(n);
+    lev.resize(nc);
+    int nl = 0;
+    for (int c = 0; c < nc; ++c) {
+      const int lk = parent[cs[c]];
+      lev[c] = lk < 0 ? 0 : lev[chain_of[lk]] + 1;
+      nl = std::max(nl, lev[c] + 1);
+    }
+    if (nl > kWalkMaxLevels) return;
+    for (int l = 0; l < nl; ++l) {
+      wlev.push_back((int)wrec.size());
+      for (int c = 0; c < nc; ++c)
+        if (lev[c] == l) wrec.push_back(make_int4(cs[c], cs[c + 1], parent[cs[c]], 0));
+    }
+    wlev.push_back((int)wrec.size());
+    walk = true;
+  }
   cudaError_t build_tables() {
     seg = analyze_segments(parent, seg_len);
     dfsord = analyze_dfs(parent);
+    analyze_walk();
     if (d_tables) {
       cudaFree(d_tables);
       d_tables = nullptr;
@@ -210,6 +247,8 @@ struct TypeHost {
     const size_t o_g = B.add(gather.data(), gather.size() * 4);
     const size_t o_js = B.add(seg.job_start.data(), seg.job_start.size() * 4);
     const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
+    const size_t o_wr = B.add(wrec.data(), wrec.size() * sizeof(int4));
+    const size_t o_wl = B.add(wlev.data(), wlev.size() * 4);
     void *d = nullptr;
     cudaError_t e = B.upload(&d);
     if (e != cudaSuccess) {
@@ -235,6 +274,11 @@ struct TypeHost {
     dev.njobs = (int)seg.job_start.size() - 1;
     dev.job_start = (const int32_t *)(base + o_js);
     dev.jinfo = (const uint32_t *)(base + o_ji);
+    dev.walk = walk ? 1 : 0;
+    dev.nlev = walk ? (int)wlev.size() - 1 : 0;
+    dev.nwrec = (int)wrec.size();
+    dev.wrec = (const int4 *)(base + o_wr);
+    dev.wlev = (const int32_t *)(base + o_wl);
     sync_dev();
     return cudaSuccess;
   }
@@ -320,7 +364,7 @@ struct anim_ctx {
   std::set<anim_plan *> plans;
   std::set<anim_ik *> iks;
   struct TuneChoice {
-    int seg_len, ctas_per_sm, joints_per_item;
+    int seg_len, ctas_per_sm, joints_per_item, walk;
     float ms;
   };
   std::map<uint64_t, TuneChoice> tune_cache;  // (which, types, counts) hash -> best schedule
@@ -372,9 +416,9 @@ cudaError_t upload_types(anim_ctx *ctx) {
 
 size_t smem_budget(const anim_ctx *ctx) {
   // ctas_per_sm resident CTAs per SM: each also takes 1 KB of system shared
-  // memory and up to 5 KB of the kernels' static shared memory (item buffers)
+  // memory and the kernels' static shared memory (staged work items)
   const size_t per = ctx->smem_per_sm / (size_t)ctx->ctas_per_sm;
-  return std::min(ctx->smem_optin - 5120, per - 1024 - 5120);
+  return std::min(ctx->smem_optin - kStaticSmemAllowance, per - 1024 - kStaticSmemAllowance);
 }
 
 int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
@@ -384,7 +428,7 @@ int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
     return adjoint ? adjoint_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
   };
   while (C > 1 && bytes(C) > budget) --C;
-  if (bytes(C) > ctx->smem_optin - 5120) return 0;
+  if (bytes(C) > ctx->smem_optin - kStaticSmemAllowance) return 0;
   return C;
 }
 
@@ -790,9 +834,9 @@ int anim_forward_local(anim_ctx *ctx, const anim_plan *plan, const float *d_q, c
   if (!aligned16(d_q) || (d_skin && !aligned16(d_skin)) || (d_model && !aligned16(d_model)) || !aligned4(d_t))
     return fail(ctx, ANIM_EINVAL, "d_q, d_skin, d_model must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemsetAsync(plan->d_queue, 0, sizeof(int), st));
   ScanArgs a{};
   a.types = ctx->d_types;
+  a.done = plan->d_queue + 1;
   a.items = plan->d_items_scan;
   a.n_items = plan->n_items_scan;
   a.item_chars = plan->d_type_chars;
@@ -839,8 +883,8 @@ static int run_adjoint(anim_ctx *ctx, const anim_plan *plan, int mode, const flo
   if (!d_q || !d_t || !d_in || !d_grad_q || !d_grad_t) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
   if (!aligned16(d_q) || !aligned16(d_grad_q)) return fail(ctx, ANIM_EINVAL, "d_q, d_grad_q must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemsetAsync(plan->d_queue, 0, sizeof(int), st));
   AdjointArgs a{};
+  a.done = plan->d_queue + 1;
   a.types = ctx->d_types;
   a.items = plan->d_items_adj;
   a.n_items = plan->n_items_adj;
@@ -955,7 +999,6 @@ int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v,
   if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
     return fail(ctx, ANIM_EINVAL, "bad Adam hyper-parameters");
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemsetAsync(ik->d_counters, 0, sizeof(int), st));
   AdjointArgs a{};
   a.types = ik->d_views;
   a.items = ik->d_items;
@@ -974,7 +1017,7 @@ int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v,
   a.v = d_v;
   a.q_mut = d_q;
   a.step = ik->d_counters + 1;
-  a.done_ctas = ik->d_counters + 2;
+  a.done = ik->d_counters + 2;
   a.lr = lr;
   a.beta1 = beta1;
   a.beta2 = beta2;
@@ -1011,13 +1054,14 @@ static uint64_t mix_hash(const anim_ctx *ctx, const anim_plan *P, int which) {
   return h;
 }
 
-static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps, int jpi) {
+static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps, int jpi, int walk) {
   ctx->ctas_per_sm = cps;
   ctx->joints_per_item = jpi;
   for (int t : P->used) {
     TypeHost &T = *ctx->types[t];
-    if (T.seg_len != seg_len) {
+    if (T.seg_len != seg_len || T.allow_walk != (walk != 0)) {
       T.seg_len = seg_len;
+      T.allow_walk = walk != 0;
       CK(T.build_tables());
     }
   }
@@ -1041,7 +1085,8 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   const uint64_t key = mix_hash(ctx, plan, which);
   auto hit = ctx->tune_cache.find(key);
   if (hit != ctx->tune_cache.end())
-    return apply_choice(ctx, plan, hit->second.seg_len, hit->second.ctas_per_sm, hit->second.joints_per_item);
+    return apply_choice(ctx, plan, hit->second.seg_len, hit->second.ctas_per_sm, hit->second.joints_per_item,
+                        hit->second.walk);
 
   // scratch inputs (tuning may allocate; evaluation calls never do)
   const int64_t N = plan->n_chars, J = plan->total;
@@ -1088,30 +1133,32 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
     if (which == 1) return anim_forward_local(ctx, plan, d_q, d_t, d_out, nullptr, nullptr);
     return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, nullptr);
   };
-  anim_ctx::TuneChoice best{0, 0, 0, 1e30f};
+  anim_ctx::TuneChoice best{0, 0, 0, 0, 1e30f};
   const int segs[] = {8, 16, 32}, cpss[] = {1, 2}, jpis[] = {1024, 2048, 4096};
-  for (int seg : segs)
-    for (int cps : cpss)
-      for (int jpi : jpis) {
-        if (apply_choice(ctx, plan, seg, cps, jpi) != ANIM_OK) continue;  // e.g. does not fit
-        bool ok = true;
-        for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
-        cudaEventRecord(e0, nullptr);
-        for (int r = 0; r < 5 && ok; ++r) ok = run_once() == ANIM_OK;
-        cudaEventRecord(e1, nullptr);
-        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= 5.f;
-        if (ms < best.ms) best = {seg, cps, jpi, ms};
-      }
+  for (int walk = 0; walk < 2; ++walk)
+    for (int seg : segs)
+      for (int cps : cpss)
+        for (int jpi : jpis) {
+          if (walk && seg != 16) continue;  // segment length does not matter to walk-mode types
+          if (apply_choice(ctx, plan, seg, cps, jpi, walk) != ANIM_OK) continue;  // e.g. does not fit
+          bool ok = true;
+          for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
+          cudaEventRecord(e0, nullptr);
+          for (int r = 0; r < 5 && ok; ++r) ok = run_once() == ANIM_OK;
+          cudaEventRecord(e1, nullptr);
+          if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= 5.f;
+          if (ms < best.ms) best = {seg, cps, jpi, walk, ms};
+        }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   release();
   if (best.seg_len == 0) return fail(ctx, ANIM_ECUDA, "no candidate schedule ran");
   ctx->tune_cache[key] = best;
   ctx->err.clear();
-  return apply_choice(ctx, plan, best.seg_len, best.ctas_per_sm, best.joints_per_item);
+  return apply_choice(ctx, plan, best.seg_len, best.ctas_per_sm, best.joints_per_item, best.walk);
 }
 
 int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, int32_t *out_nseg, int32_t *out_seg_start,

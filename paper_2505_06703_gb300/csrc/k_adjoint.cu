@@ -19,7 +19,7 @@
 namespace anim {
 
 size_t adjoint_smem_bytes(int n, int nseg, int C) {
-  return scan_item_bytes(n, nseg, C) + 16ull * 2ull * C * (n + 1);
+  return scan_item_bytes(n, nseg, C) + 16ull * 2ull * ((size_t)C * (n + 1) + 1);
 }
 
 __device__ __forceinline__ float3 cross3(const float3 a, const float3 b) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
     float4 *Y0 = P + C * cs4;
     float4 *Y1 = Y0 + 3 * C * nseg;
     float4 *PF = Y1 + 3 * C * nseg + (4 * nseg + 15) / 16;  // [C][n+1], after pass 2's pointers
-    float4 *PT = PF + C * (n + 1);   // [C][n+1]
+    float4 *PT = PF + C * (n + 1) + 1;  // [C][n+1] (+1: the scan's total)
     const int32_t *gat = b.T.gather;
     const bool gath = gat != nullptr;
     const int CN = C * n;
@@ -136,18 +136,22 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
     // ---- forward recompute: the segmented scan from (q, t), model poses in place
     pass1a_qt(b, P, cs4, a.q, a.t, tid);
     compute_sync();
-    pass1b(b, P, cs4, tid);
-    compute_sync();
-    const float4 *Y = pass2(b, P, cs4, Y0, Y1, tid);
-    for (int idx = tid; idx < CN; idx += kComputeThreads) {
-      const int c = (int)b.divN.div(idx), j = idx - c * n;
-      const uint32_t info = __ldg(b.T.jinfo + j);
-      if (info & kJLink) {
-        float4 *slot = P + c * cs4 + 3 * j;
-        sts_aff(slot, aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & 0xFFFFu))), lds_aff(slot)));
+    if (b.T.walk) {
+      pass_walk(b, P, cs4, tid);
+    } else {
+      pass1b(b, P, cs4, tid);
+      compute_sync();
+      const float4 *Y = pass2(b, P, cs4, Y0, Y1, tid);
+      for (int idx = tid; idx < CN; idx += kComputeThreads) {
+        const int c = (int)b.divN.div(idx), j = idx - c * n;
+        const uint32_t info = __ldg(b.T.jinfo + j);
+        if (info & kJLink) {
+          float4 *slot = P + c * cs4 + 3 * j;
+          sts_aff(slot, aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & 0xFFFFu))), lds_aff(slot)));
+        }
       }
+      compute_sync();
     }
-    compute_sync();
 
     // ---- per-slot (g, p x g) in depth-first order; loss terms in F.w
     for (int idx = tid; idx < CN; idx += kComputeThreads) {
@@ -187,8 +191,16 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
       }
       compute_sync();
     }
-    for (int c = 0; c < C; ++c) prefix_pairs(PF + c * (n + 1), PT + c * (n + 1), n, wsF, wsT);
-    if (MODE != 0 && a.loss != nullptr && tid < C) a.loss[b.cid[tid]] = PF[tid * (n + 1) + n].w;
+    // one exclusive prefix over all characters' slots (slot n of each
+    // character is zero); subtree sums are differences inside a character
+    for (int c = tid; c < C; c += kComputeThreads) {
+      PF[c * (n + 1) + n] = make_float4(0.f, 0.f, 0.f, 0.f);
+      PT[c * (n + 1) + n] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    compute_sync();
+    prefix_pairs(PF, PT, C * (n + 1), wsF, wsT);
+    if (MODE != 0 && a.loss != nullptr && tid < C)
+      a.loss[b.cid[tid]] = PF[tid * (n + 1) + n].w - PF[tid * (n + 1)].w;
 
     // ---- per-joint gradients (and the Adam update in IK mode)
     float bc2s = 1.f, step_size = 0.f;
@@ -251,12 +263,12 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
     handoff_sync();
   }
 
-  if (MODE == 2 && tid == 0) {
+  if (tid == 0) {  // the last CTA resets the queue (and advances the IK step)
     __threadfence();
-    const int done = atomicAdd(a.done_ctas, 1);
-    if (done == (int)gridDim.x - 1) {
-      *a.step = *a.step + 1;
-      *a.done_ctas = 0;
+    if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
+      if (MODE == 2) *a.step = *a.step + 1;
+      *a.queue_head = 0;
+      *a.done = 0;
       __threadfence();
     }
   }

@@ -245,11 +245,11 @@ extern "C" ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return set_msg(ANIM_ECUDA, "device attribute query failed");
-  const size_t budget = std::min((size_t)optin - 5120, (size_t)smem_sm / 2 - 1024 - 5120);
+  const size_t budget = std::min((size_t)optin - kStaticSmemAllowance, (size_t)smem_sm / 2 - 1024 - kStaticSmemAllowance);
   int C = std::max(1, std::min(kCMax, 2048 / n_joints));
   while (C > 1 && scan_item_bytes(n_joints, nseg, C) > budget) --C;
   const size_t smem = scan_item_bytes(n_joints, nseg, C);
-  if (smem > (size_t)optin - 5120) return set_msg(ANIM_EUNSUPPORTED, "skeleton does not fit in shared memory");
+  if (smem > (size_t)optin - kStaticSmemAllowance) return set_msg(ANIM_EUNSUPPORTED, "skeleton does not fit in shared memory");
   static size_t set_smem = 0;
   if (smem > set_smem) {
     e = cudaFuncSetAttribute(k_scan_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

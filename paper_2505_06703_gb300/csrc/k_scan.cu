@@ -104,12 +104,18 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
     }
     compute_sync();
 
-    // ---- pass 1b: running products along segments
-    pass1b(b, P, cs4, tid);
-    compute_sync();
-
-    // ---- pass 2: pointer jumping over segments
-    const float4 *Y = pass2(b, P, cs4, Y0, Y1, tid);
+    const bool walk = b.T.walk != 0;
+    const float4 *Y = Y0;
+    if (walk) {
+      // ---- shallow skeleton: level-ordered chain walks give M_j in place
+      pass_walk(b, P, cs4, tid);
+    } else {
+      // ---- pass 1b: running products along segments
+      pass1b(b, P, cs4, tid);
+      compute_sync();
+      // ---- pass 2: pointer jumping over segments
+      Y = pass2(b, P, cs4, Y0, Y1, tid);
+    }
 
     // ---- pass 3: model pose, bind, stage in place
     {
@@ -124,7 +130,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
         for (int c = grp * cpt; c < c1; ++c) {
           float4 *slot = P + c * cs4 + 3 * j;
           Aff m = lds_aff(slot);
-          if (info & kJLink) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
+          if (!walk && (info & kJLink)) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
           if (MODEL && SKIN) stg_aff(reinterpret_cast<float4 *>(a.model) + (b.off[c] + j) * 3, m);
           if (SKIN) m = aff_mul(m, B);
           sts_aff(slot, m);
@@ -144,6 +150,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
     handoff_sync();
   }
   if (tid == 0 && pending) bulk_wait_all();
+  if (tid == 0 && a.done) last_cta_reset(a.queue_head, a.done);
 }
 
 template <int MODE, bool SKIN, bool MODEL>
