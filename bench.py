@@ -50,7 +50,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes per launch of the persistent frame kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources it was taken on; reported as null once the sources change.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"c04d5847136cbe29": 1360896 + 39827200}  # profiles/frame_kernel_config2.md
 
 
 # ------------------------------------------------------------------ helpers
@@ -229,7 +229,11 @@ def run_ours(args) -> dict:
 
     w = rank_workload(rank)
     ctx, plan = setup_ctx(w, local)
-    ctx.tune(plan, 0)  # the library's autotuner picks the schedule for this mix
+    if args.schedule:
+        ctx.set_schedule(plan, [int(x) for x in args.schedule.split(",")])
+    else:
+        ctx.tune(plan, 0)  # the library's autotuner picks the schedule for this mix
+    schedule = ctx.get_schedule(plan)
     joints = plan.total
     n_chars = plan.n_chars
     out_bytes = joints * 48
@@ -322,7 +326,8 @@ def run_ours(args) -> dict:
                          "joints_per_step_per_gpu": joints, "characters_per_gpu": n_chars,
                          "l2": f"output rotated over {n_out} buffers ({n_out * out_bytes / 1e6:.0f} MB > 129 MB L2)",
                          "timing": "CUDA graphs (work queue + persistent kernel), CUDA events",
-                         "schedule": "anim_tune (segment length, CTAs/SM, item size)",
+                         "schedule": {"seg_len,ctas_per_sm,joints_per_item,walk": schedule,
+                                      "source": "--schedule" if args.schedule else "anim_tune"},
                          "parallelism": f"replicas x{world} (independent character batches)"},
               "roofline": roofline, "gpu_launches": 2 * steps, "clocks": clock}
 
@@ -358,7 +363,7 @@ def run_ours(args) -> dict:
                            "ms_per_step": p_ms / p_steps, "kernel": "k_levelsync (1 CTA/char, barrier per level)",
                            "speedup_fused_vs_plain": (p_ms / p_steps) / ms_step}
         result["fwd_bwd"] = run_fwd_bwd(ctx_factory=setup_ctx, device=local, dev=dev, steps=steps,
-                                        warmup=warmup, world=world, peak=peak)
+                                        warmup=warmup, world=world, peak=peak, schedule=args.schedule_bwd)
     del ctx
     if world > 1:
         import torch.distributed as dist
@@ -366,13 +371,16 @@ def run_ours(args) -> dict:
     return result
 
 
-def run_fwd_bwd(ctx_factory, device, dev, steps, warmup, world, peak):
+def run_fwd_bwd(ctx_factory, device, dev, steps, warmup, world, peak, schedule=None):
     """Fused forward + adjoint (anim_loss_backward) on 1,024 characters of the
     256-joint type: read q, t, target; write dq, dt (and per-character loss)."""
     import torch
     w = synth.config4()
     ctx, plan = ctx_factory(w, device)
-    ctx.tune(plan, 2)
+    if schedule:
+        ctx.set_schedule(plan, [int(x) for x in schedule.split(",")])
+    else:
+        ctx.tune(plan, 2)
     joints = plan.total
     n_sets = max(2, math.ceil(2.5 * L2_BYTES / (joints * 68)))
     sets = []
@@ -391,6 +399,7 @@ def run_fwd_bwd(ctx_factory, device, dev, steps, warmup, world, peak):
     alg = fwd_bwd_algorithmic_bytes(w)
     achieved = alg / (ms_step / 1e3) / 1e9
     return {"value": world * joints / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step,
+            "schedule": ctx.get_schedule(plan),
             "workload": "1,024 chars x 256-joint tree (depth 96), loss sum |p - target|^2",
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes": alg,
@@ -446,6 +455,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain-kernel and fwd+bwd measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--schedule", default="", help="seg_len,ctas_per_sm,joints_per_item,walk for the frame "
+                                                   "instead of running the autotuner")
+    ap.add_argument("--schedule-bwd", default="", help="the same for the forward+adjoint measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

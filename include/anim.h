@@ -214,6 +214,14 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
  * which = 0 needs clips for every type of the plan. */
 ANIM_API int anim_tune(anim_ctx *ctx, anim_plan *plan, int which);
 
+/* The schedule the autotuner picked, as 4 integers: segment length, resident
+ * CTAs per SM, work-item size in joints, walk mode (0/1) -- read with
+ * anim_get_schedule (segment length and walk mode of the plan's first type)
+ * and re-applied without timing by anim_set_schedule (for example in another
+ * process).  Synchronous; not capturable. */
+ANIM_API int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out4);
+ANIM_API int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in4);
+
 /* Read and clear the device status word (synchronizes `stream`). */
 ANIM_API int anim_get_status(anim_ctx *ctx, void *stream, int *out_status);
 

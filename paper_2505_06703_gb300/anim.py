@@ -47,6 +47,8 @@ SIGNATURES = {
     "anim_get_status": (c_int, [_P, _P, POINTER(c_int)]),
     "anim_analyze_skeleton": (c_int, [c_int, _P, c_int, POINTER(c_int32), _P, POINTER(c_int32), POINTER(c_int32)]),
     "anim_forward_local_noalloc": (c_int, [c_int, _P, c_int64, _P, _P, _P, _P, _P]),
+    "anim_get_schedule": (c_int, [_P, _P, _P]),
+    "anim_set_schedule": (c_int, [_P, _P, _P]),
 }
 
 _lib = None
@@ -227,6 +229,15 @@ class Context:
 
     def tune(self, plan, which: int = 0):
         self._ck(self.lib.anim_tune(self.h, plan.h, int(which)))
+
+    def get_schedule(self, plan):
+        out = np.zeros(4, dtype=np.int32)
+        self._ck(self.lib.anim_get_schedule(self.h, plan.h, _np_ptr(out)))
+        return [int(x) for x in out]
+
+    def set_schedule(self, plan, sched):
+        a = np.ascontiguousarray(sched, dtype=np.int32)
+        self._ck(self.lib.anim_set_schedule(self.h, plan.h, _np_ptr(a)))
 
 
 class Plan:

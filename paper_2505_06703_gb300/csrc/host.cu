@@ -1161,6 +1161,28 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   return apply_choice(ctx, plan, best.seg_len, best.ctas_per_sm, best.joints_per_item, best.walk);
 }
 
+int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out4) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (!out4) return fail(ctx, ANIM_EINVAL, "out4 is NULL");
+  const TypeHost *T = plan->used.empty() ? nullptr : ctx->types[plan->used[0]].get();
+  out4[0] = T ? T->seg_len : 16;
+  out4[1] = ctx->ctas_per_sm;
+  out4[2] = ctx->joints_per_item;
+  out4[3] = T && T->allow_walk ? 1 : 0;
+  return ANIM_OK;
+}
+
+int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in4) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (!in4 || in4[0] < 1 || in4[0] > ANIM_MAX_JOINTS || in4[1] < 1 || in4[1] > 4 || in4[2] < 1 ||
+      (in4[3] != 0 && in4[3] != 1))
+    return fail(ctx, ANIM_EINVAL, "schedule out of range");
+  CK(cudaSetDevice(ctx->device));
+  return apply_choice(ctx, plan, in4[0], in4[1], in4[2], in4[3]);
+}
+
 int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, int32_t *out_nseg, int32_t *out_seg_start,
                           int32_t *out_rounds, int32_t *out_depth) {
   if (n < 1 || n > ANIM_MAX_JOINTS || !parents || seg_len < 1 || !out_nseg || !out_seg_start || !out_rounds ||
