@@ -75,6 +75,7 @@ struct LaunchCfg {
   int threads;       // CTA size
   int ctas;          // persistent grid size
   size_t smem;       // dynamic shared memory per CTA (bytes)
+  int min_blocks = 2;  // resident CTAs per SM the kernel variant is compiled for (2 or 3)
 };
 
 // ---------------------------------------------------------------- kernels

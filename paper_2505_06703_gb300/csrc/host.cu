@@ -320,10 +320,11 @@ struct anim_plan {
   RangeDev *d_ranges = nullptr;
   int n_ranges = 0, n_slots = 0;
   int32_t *d_n_items = nullptr;
-  int *d_queue = nullptr;  // [0] queue head, [1] bucket last-CTA counter
+  int *d_queue = nullptr;  // [0] work-queue head, [1] finished-CTA counter (both back to 0 after each launch)
   int32_t *d_used = nullptr, *d_cap = nullptr;
   LaunchCfg cfg_scan{}, cfg_adj{};
   size_t smem_frame = 0;
+  int adj_unfit = -1;  // a type whose adjoint working set does not fit this schedule, else -1
   ~anim_plan() {
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
                     (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
@@ -467,17 +468,24 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   const int nt = (int)ctx->types.size();
   P->C_scan.assign(nt, 1);
   P->C_adj.assign(nt, 1);
+  P->adj_unfit = -1;
   size_t smem_s = 0, smem_a = 0;
   for (int t : P->used) {
     const TypeHost &T = *ctx->types[t];
     const int cs = choose_C(ctx, T, false), ca = choose_C(ctx, T, true);
-    if (cs == 0 || ca == 0)
+    if (cs == 0)
       return fail(ctx, ANIM_EUNSUPPORTED,
                   "type %d (%d joints, %d segments) does not fit in shared memory with one character", t, T.n,
                   T.seg.nseg);
     P->C_scan[t] = cs;
-    P->C_adj[t] = ca;
     smem_s = std::max(smem_s, scan_smem_bytes(T.n, T.seg.nseg, cs));
+    // the adjoint keeps two more vectors per joint: a schedule may fit the
+    // forward kernels and not the adjoint, which then refuses to run
+    if (ca == 0) {
+      if (P->adj_unfit < 0) P->adj_unfit = t;
+      continue;
+    }
+    P->C_adj[t] = ca;
     smem_a = std::max(smem_a, adjoint_smem_bytes(T.n, T.seg.nseg, ca));
   }
   auto is = make_items(P, P->C_scan), ia = make_items(P, P->C_adj);
@@ -510,7 +518,8 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->d_items_frame = nullptr;
   CK(cudaMalloc(&P->d_items_frame, std::max(1, slots) * sizeof(WorkItem)));
   const int grid = ctx->sm_count * ctx->ctas_per_sm;
-  P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16)};
+  P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16),
+                 ctx->ctas_per_sm >= 3 ? 3 : 2};
   P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
   P->smem_frame = std::max<size_t>(smem_s, 16);
   P->version = ctx->version;
@@ -776,6 +785,7 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
   a.item_chars = plan->d_sorted;
   a.row_off = plan->d_row_off;
   a.queue_head = plan->d_queue;
+  a.done = plan->d_queue + 1;  // the last CTA resets the head for the plan's other launches
   a.status = ctx->d_status;
   a.time = d_time;
   a.blend_w = d_blend_w;
@@ -881,6 +891,10 @@ static int run_adjoint(anim_ctx *ctx, const anim_plan *plan, int mode, const flo
   if (rc) return rc;
   if (plan->n_chars == 0) return ANIM_OK;
   if (!d_q || !d_t || !d_in || !d_grad_q || !d_grad_t) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (plan->adj_unfit >= 0)
+    return fail(ctx, ANIM_EUNSUPPORTED,
+                "the adjoint of type %d does not fit in shared memory under this schedule (segment length %d)",
+                plan->adj_unfit, ctx->types[plan->adj_unfit]->seg_len);
   if (!aligned16(d_q) || !aligned16(d_grad_q)) return fail(ctx, ANIM_EINVAL, "d_q, d_grad_q must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   AdjointArgs a{};
@@ -1134,12 +1148,13 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
     return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, nullptr);
   };
   anim_ctx::TuneChoice best{0, 0, 0, 0, 1e30f};
-  const int segs[] = {8, 16, 32}, cpss[] = {1, 2}, jpis[] = {1024, 2048, 4096};
+  const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {1024, 2048, 4096};
   for (int walk = 0; walk < 2; ++walk)
     for (int seg : segs)
       for (int cps : cpss)
         for (int jpi : jpis) {
           if (walk && seg != 16) continue;  // segment length does not matter to walk-mode types
+          if (cps == 3 && which == 2) continue;  // the adjoint kernel is built for up to 2 CTAs/SM
           if (apply_choice(ctx, plan, seg, cps, jpi, walk) != ANIM_OK) continue;  // e.g. does not fit
           bool ok = true;
           for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
@@ -1176,11 +1191,20 @@ int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out4) {
 int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in4) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
-  if (!in4 || in4[0] < 1 || in4[0] > ANIM_MAX_JOINTS || in4[1] < 1 || in4[1] > 4 || in4[2] < 1 ||
+  if (!in4 || in4[0] < 1 || in4[0] > ANIM_MAX_JOINTS || in4[1] < 1 || in4[1] > 3 || in4[2] < 1 ||
       (in4[3] != 0 && in4[3] != 1))
     return fail(ctx, ANIM_EINVAL, "schedule out of range");
   CK(cudaSetDevice(ctx->device));
-  return apply_choice(ctx, plan, in4[0], in4[1], in4[2], in4[3]);
+  int32_t prev[4];
+  anim_get_schedule(ctx, plan, prev);
+  rc = apply_choice(ctx, plan, in4[0], in4[1], in4[2], in4[3]);
+  if (rc != ANIM_OK) {
+    // keep the failure's message and put the previous schedule back
+    const std::string msg = ctx->err;
+    apply_choice(ctx, plan, prev[0], prev[1], prev[2], prev[3]);
+    ctx->err = msg;
+  }
+  return rc;
 }
 
 int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, int32_t *out_nseg, int32_t *out_seg_start,

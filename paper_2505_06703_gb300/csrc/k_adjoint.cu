@@ -124,30 +124,30 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
     if (b.item < 0) break;
     const int C = b.C, n = b.T.n, nseg = b.T.nseg;
     const int cs4 = 3 * n + 1;
-    float4 *P = sm;
-    float4 *Y0 = P + C * cs4;
-    float4 *Y1 = Y0 + 3 * C * nseg;
-    float4 *PF = Y1 + 3 * C * nseg + (4 * nseg + 15) / 16;  // [C][n+1], after pass 2's pointers
+    const ItemLayout Lt = item_layout(sm, C, n, nseg);
+    float4 *P = Lt.P;
+    float4 *PF = Lt.end;                // [C][n+1]
     float4 *PT = PF + C * (n + 1) + 1;  // [C][n+1] (+1: the scan's total)
     const int32_t *gat = b.T.gather;
     const bool gath = gat != nullptr;
     const int CN = C * n;
 
     // ---- forward recompute: the segmented scan from (q, t), model poses in place
+    stage_tables(b, Lt, tid);
     pass1a_qt(b, P, cs4, a.q, a.t, tid);
     compute_sync();
     if (b.T.walk) {
       pass_walk(b, P, cs4, tid);
     } else {
-      pass1b(b, P, cs4, tid);
+      pass1b(b, Lt, P, cs4, tid);
       compute_sync();
-      const float4 *Y = pass2(b, P, cs4, Y0, Y1, tid);
+      const float4 *Y = pass2(b, Lt, P, cs4, tid);
       for (int idx = tid; idx < CN; idx += kComputeThreads) {
         const int c = (int)b.divN.div(idx), j = idx - c * n;
-        const uint32_t info = __ldg(b.T.jinfo + j);
-        if (info & kJLink) {
+        const uint32_t info = Lt.jinfo[j];
+        if (info & kJ16Link) {
           float4 *slot = P + c * cs4 + 3 * j;
-          sts_aff(slot, aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & 0xFFFFu))), lds_aff(slot)));
+          sts_aff(slot, aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & kJ16Seg))), lds_aff(slot)));
         }
       }
       compute_sync();

@@ -118,29 +118,29 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
     if (b.item < 0) break;
     const int Cn = b.C, n = b.T.n, nseg = b.T.nseg;
     const int cs4 = 3 * n + 1;
-    float4 *P = sm;
-    float4 *Y0 = P + Cn * cs4;
-    float4 *Y1 = Y0 + 3 * Cn * nseg;
+    const ItemLayout Lt = item_layout(sm, Cn, n, nseg);
+    float4 *P = Lt.P;
     if (tid == 0 && pending) {
       bulk_wait_read_all();
       pending = false;
     }
     compute_sync();
+    stage_tables(b, Lt, tid);
     pass1a_qt(b, P, cs4, q, t, tid);
     compute_sync();
-    pass1b(b, P, cs4, tid);
+    pass1b(b, Lt, P, cs4, tid);
     compute_sync();
-    const float4 *Y = pass2(b, P, cs4, Y0, Y1, tid);
+    const float4 *Y = pass2(b, Lt, P, cs4, tid);
     const int W = n * b.cgroups, cpt = b.cpt;
     for (int idx = tid; idx < W; idx += kComputeThreads) {
       const int grp = (int)b.divN.div(idx), j = idx - grp * n;
-      const uint32_t info = __ldg(b.T.jinfo + j);
+      const uint32_t info = Lt.jinfo[j];
       const Aff B = ldg_aff(inv_bind + 3 * j);
       const int c1 = min(Cn, (grp + 1) * cpt);
       for (int c = grp * cpt; c < c1; ++c) {
         float4 *slot = P + c * cs4 + 3 * j;
         Aff m = lds_aff(slot);
-        if (info & kJLink) m = aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & 0xFFFFu))), m);
+        if (info & kJ16Link) m = aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & kJ16Seg))), m);
         sts_aff(slot, aff_mul(m, B));
       }
     }

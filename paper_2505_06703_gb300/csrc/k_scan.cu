@@ -44,8 +44,8 @@ __device__ __forceinline__ Aff sample_local(const KeyRecs &r, float al, float w,
 // stages the next item meanwhile.
 //   MODE 0: local poses sampled from the type's clips at each character's time;
 //   MODE 1: local poses read from q [total][4] (normalized here), t [total][3].
-template <int MODE, bool SKIN, bool MODEL>
-__global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
+template <int MODE, bool SKIN, bool MODEL, int MINB>
+__global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
   const int tid = threadIdx.x;
@@ -65,16 +65,17 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
     if (b.item < 0) break;
     const int C = b.C, n = b.T.n, nseg = b.T.nseg;
     const int cs4 = 3 * n + 1;  // float4 stride between characters (16 B skew against bank conflicts)
-    float4 *P = sm;
-    float4 *Y0 = P + C * cs4;
-    float4 *Y1 = Y0 + 3 * C * nseg;
+    const ItemLayout Lt = item_layout(sm, C, n, nseg);
+    float4 *P = Lt.P;
     if (tid == 0 && pending) {
       bulk_wait_read_all();  // the staging buffer of the previous item has been read out
       pending = false;
     }
     compute_sync();
 
-    // ---- pass 1a: local matrices of every (joint, character)
+    // ---- pass 1a: local matrices of every (joint, character); the type's
+    // tables are staged into shared memory alongside
+    stage_tables(b, Lt, tid);
     if (MODE == 0) {
       const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
       const float4 *KA0 = b.T.keys + (size_t)k0 * n * 2;
@@ -105,16 +106,16 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
     compute_sync();
 
     const bool walk = b.T.walk != 0;
-    const float4 *Y = Y0;
+    const float4 *Y = Lt.Y0;
     if (walk) {
       // ---- shallow skeleton: level-ordered chain walks give M_j in place
       pass_walk(b, P, cs4, tid);
     } else {
       // ---- pass 1b: running products along segments
-      pass1b(b, P, cs4, tid);
+      pass1b(b, Lt, P, cs4, tid);
       compute_sync();
       // ---- pass 2: pointer jumping over segments
-      Y = pass2(b, P, cs4, Y0, Y1, tid);
+      Y = pass2(b, Lt, P, cs4, tid);
     }
 
     // ---- pass 3: model pose, bind, stage in place
@@ -122,15 +123,15 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
       const int W = n * b.cgroups, cpt = b.cpt;
       for (int idx = tid; idx < W; idx += kComputeThreads) {
         const int grp = (int)b.divN.div(idx), j = idx - grp * n;
-        const uint32_t info = __ldg(b.T.jinfo + j);
-        const int g = (int)(info & 0xFFFFu);
+        const uint32_t info = Lt.jinfo[j];
+        const int g = (int)(info & kJ16Seg);
         Aff B;
         if (SKIN) B = ldg_aff(b.T.inv_bind + 3 * j);
         const int c1 = min(C, (grp + 1) * cpt);
         for (int c = grp * cpt; c < c1; ++c) {
           float4 *slot = P + c * cs4 + 3 * j;
           Aff m = lds_aff(slot);
-          if (!walk && (info & kJLink)) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
+          if (!walk && (info & kJ16Link)) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
           if (MODEL && SKIN) stg_aff(reinterpret_cast<float4 *>(a.model) + (b.off[c] + j) * 3, m);
           if (SKIN) m = aff_mul(m, B);
           sts_aff(slot, m);
@@ -153,9 +154,9 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_scan(const ScanArgs a) {
   if (tid == 0 && a.done) last_cta_reset(a.queue_head, a.done);
 }
 
-template <int MODE, bool SKIN, bool MODEL>
+template <int MODE, bool SKIN, bool MODEL, int MINB>
 static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  auto k = k_scan<MODE, SKIN, MODEL>;
+  auto k = k_scan<MODE, SKIN, MODEL, MINB>;
   static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
   if (cfg.smem > set_smem) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
@@ -166,12 +167,17 @@ static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
+template <int MINB>
+static cudaError_t launch_scan_m(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   const bool skin = a.skin != nullptr, model = a.model != nullptr;
-  if (mode == 0) return launch_scan_t<0, true, false>(a, cfg, st);
-  if (skin && model) return launch_scan_t<1, true, true>(a, cfg, st);
-  if (skin) return launch_scan_t<1, true, false>(a, cfg, st);
-  return launch_scan_t<1, false, true>(a, cfg, st);
+  if (mode == 0) return launch_scan_t<0, true, false, MINB>(a, cfg, st);
+  if (skin && model) return launch_scan_t<1, true, true, MINB>(a, cfg, st);
+  if (skin) return launch_scan_t<1, true, false, MINB>(a, cfg, st);
+  return launch_scan_t<1, false, true, MINB>(a, cfg, st);
+}
+
+cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
+  return cfg.min_blocks >= 3 ? launch_scan_m<3>(mode, a, cfg, st) : launch_scan_m<2>(mode, a, cfg, st);
 }
 
 // ------------------------------------------------------------ work queue

@@ -139,6 +139,50 @@ __device__ __forceinline__ void producer_loop(ItemBuf *bufs, int *queue_head, in
   }
 }
 
+// Dynamic shared memory of one work item:
+//   P        [C][3n+1] float4   local -> running -> model/skin matrices
+//   Y0, Y1   [C][nseg][3] float4  pass-2 buffers
+//   ptr0/1   int16 [nseg] each    pass-2 jumping pointers (type-level)
+//   seg_start int32 [nseg+1], seg_link int32 [nseg], jinfo uint16 [n]
+//            the type's tables, staged once per item so the serial passes
+//            read shared memory instead of waiting on global loads.
+constexpr uint16_t kJ16Seg = 0x3FFFu, kJ16Start = 0x4000u, kJ16Link = 0x8000u;
+struct ItemLayout {
+  float4 *P, *Y0, *Y1;
+  int16_t *ptr0, *ptr1;
+  int32_t *seg_start, *seg_link;
+  uint16_t *jinfo;
+  float4 *end;  // first float4 after the layout
+};
+__host__ __device__ inline size_t item_table_bytes(int n, int nseg) {
+  return (4ull * nseg + 4ull * (2ull * nseg + 1) + 2ull * n + 15) / 16 * 16;
+}
+__device__ __forceinline__ ItemLayout item_layout(float4 *sm, int C, int n, int nseg) {
+  ItemLayout L;
+  L.P = sm;
+  L.Y0 = L.P + C * (3 * n + 1);
+  L.Y1 = L.Y0 + 3 * C * nseg;
+  char *t = reinterpret_cast<char *>(L.Y1 + 3 * C * nseg);
+  L.ptr0 = reinterpret_cast<int16_t *>(t);
+  L.ptr1 = L.ptr0 + nseg;
+  L.seg_start = reinterpret_cast<int32_t *>(t + 4 * nseg);
+  L.seg_link = L.seg_start + nseg + 1;
+  L.jinfo = reinterpret_cast<uint16_t *>(L.seg_link + nseg);
+  L.end = reinterpret_cast<float4 *>(t + item_table_bytes(n, nseg));
+  return L;
+}
+// Copy the type's segment tables into the item's shared memory (all compute
+// threads; issued at the start of pass 1a so the loads overlap its work).
+__device__ __forceinline__ void stage_tables(const ItemBuf &b, const ItemLayout &L, int tid) {
+  const int n = b.T.n, nseg = b.T.nseg;
+  for (int k = tid; k <= nseg; k += kComputeThreads) L.seg_start[k] = __ldg(b.T.seg_start + k);
+  for (int k = tid; k < nseg; k += kComputeThreads) L.seg_link[k] = __ldg(b.T.seg_link + k);
+  for (int j = tid; j < n; j += kComputeThreads) {
+    const uint32_t i = __ldg(b.T.jinfo + j);
+    L.jinfo[j] = (uint16_t)((i & kJ16Seg) | ((i & kJStart) ? kJ16Start : 0u) | ((i & kJLink) ? kJ16Link : 0u));
+  }
+}
+
 // Pass 1a from given local poses (q normalized here, t), optionally through a
 // gather map (IK views).  Character-major so consecutive lanes read
 // consecutive rows.
@@ -158,11 +202,11 @@ __device__ __forceinline__ void pass1a_qt(const ItemBuf &b, float4 *P, int cs4, 
 }
 
 // Pass 1b: running products along each segment, in place.
-__device__ __forceinline__ void pass1b(const ItemBuf &b, float4 *P, int cs4, int tid) {
+__device__ __forceinline__ void pass1b(const ItemBuf &b, const ItemLayout &Lt, float4 *P, int cs4, int tid) {
   const int C = b.C, NS = b.T.nseg * C;
   for (int idx = tid; idx < NS; idx += kComputeThreads) {
     const int g = (int)b.divC.div(idx), c = idx - g * C;
-    const int a0 = __ldg(b.T.seg_start + g), a1 = __ldg(b.T.seg_start + g + 1);
+    const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1];
     float4 *Pc = P + c * cs4;
     Aff acc = lds_aff(Pc + 3 * a0);
     if (a0 + 1 >= a1) continue;
@@ -209,17 +253,17 @@ __device__ __forceinline__ void pass_walk(const ItemBuf &b, float4 *P, int cs4, 
 // Pass 2 + its barriers.  Returns the buffer holding the final Y.  The
 // jumping pointers depend only on the skeleton, so one copy per item lives
 // in shared memory (ptr0/ptr1, double-buffered) next to the Y buffers.
-__device__ __forceinline__ float4 *pass2(const ItemBuf &b, float4 *P, int cs4, float4 *Y0, float4 *Y1, int tid) {
+__device__ __forceinline__ float4 *pass2(const ItemBuf &b, const ItemLayout &Lt, float4 *P, int cs4, int tid) {
   const int nseg = b.T.nseg;
   const int CS = b.C * nseg;
-  int16_t *ptr0 = reinterpret_cast<int16_t *>(Y1 + 3 * CS);
-  int16_t *ptr1 = ptr0 + nseg;
+  float4 *Y0 = Lt.Y0, *Y1 = Lt.Y1;
+  int16_t *ptr0 = Lt.ptr0, *ptr1 = Lt.ptr1;
   for (int idx = tid; idx < CS; idx += kComputeThreads) {
     const int c = (int)b.divS.div(idx), g = idx - c * nseg;
-    const int lk = __ldg(b.T.seg_link + g);
+    const int lk = Lt.seg_link[g];
     const Aff y = lk < 0 ? aff_identity() : lds_aff(P + c * cs4 + 3 * lk);
     sts_aff(Y0 + 3 * idx, y);
-    if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(__ldg(b.T.jinfo + lk) & 0xFFFFu));
+    if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(Lt.jinfo[lk] & kJ16Seg));
   }
   compute_sync();
   float4 *cur = Y0, *nxt = Y1;
@@ -258,7 +302,7 @@ __device__ __forceinline__ void last_cta_reset(int *queue_head, int *done) {
 
 // Bytes of shared memory a work item of C characters needs.
 __host__ __device__ inline size_t scan_item_bytes(int n, int nseg, int C) {
-  return 16ull * ((size_t)C * (3 * (size_t)n + 1) + 6ull * C * nseg) + 16ull * ((4ull * nseg + 15) / 16);
+  return 16ull * ((size_t)C * (3 * (size_t)n + 1) + 6ull * C * nseg) + item_table_bytes(n, nseg);
 }
 
 }  // namespace anim

@@ -110,6 +110,48 @@ def test_autotuned_frame_parity(torch):
     ctx.tune(plan, 2)  # the adjoint's schedule search runs too
 
 
+@pytest.mark.parametrize("sched", [[4, 1, 1024, 0], [8, 2, 2048, 0], [32, 3, 4096, 0], [16, 2, 2048, 1],
+                                   [16, 3, 1024, 1]])
+def test_every_schedule_variant_parity(torch, sched):
+    """Each schedule the autotuner may pick (segment length, CTAs per SM --
+    3 selects the other compiled kernel variant --, item size, walk mode)
+    gives oracle results for the frame, the forward and the adjoint, run one
+    after another on the same plan (they share its work-queue counters)."""
+    import paper_2505_06703_gb300 as pk
+    w = synth.subset(synth.config3(), list(range(0, 10000, 25)) + [i for i in range(10000) if i % 997 == 3])
+    ctx, plan = _gpu.setup(w)
+    ctx.set_schedule(plan, sched)
+    assert ctx.get_schedule(plan) == sched
+    out = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"]))
+    _gpu.assert_skin_close(out.cpu().numpy(), oracle.frame(w), w)
+    rng = np.random.default_rng(sched[0] * 10 + sched[1])
+    types, ct = w["types"], w["char_type"]
+    off = oracle.offsets(ct, types)
+    q, t = synth.local_poses(rng, int(off[-1]), t_half=0.0005)
+    ref, mref = oracle.forward_qt(types, ct, q, t)
+    s_, m_ = ctx.forward_local(plan, _gpu.cuda(q), _gpu.cuda(t), skin=True, model=True)
+    _gpu.assert_skin_close(s_.cpu().numpy(), ref, w)
+    _gpu.assert_skin_close(m_.cpu().numpy(), mref, w)
+    g = rng.normal(size=(int(off[-1]), 3))
+    dq_ref, dt_ref = oracle.grad(types, ct, q, t, g)
+    args = (plan, _gpu.cuda(q), _gpu.cuda(t), _gpu.cuda(g.astype(np.float32)))
+    if sched[0] == 4:
+        # 512 segments of the 2,048-joint chain: the forward fits one CTA's
+        # shared memory, the adjoint's two extra vectors per joint do not
+        with pytest.raises(pk.AnimError, match="EUNSUPPORTED"):
+            ctx.backward(*args)
+        # a schedule the forward cannot take either is refused and the
+        # previous one stays in force
+        with pytest.raises(pk.AnimError, match="EUNSUPPORTED"):
+            ctx.set_schedule(plan, [1, 2, 2048, 0])
+        assert ctx.get_schedule(plan) == sched
+        ctx.set_schedule(plan, [8] + sched[1:])
+    gq, gt = ctx.backward(*args)
+    tol = _grad_tol(dq_ref, dt_ref, w)
+    assert (np.abs(gq.cpu().numpy() - dq_ref).max(axis=1) <= tol).all()
+    assert (np.abs(gt.cpu().numpy() - dt_ref).max(axis=1) <= tol).all()
+
+
 def _grad_tol(dq_ref, dt_ref, w):
     """Per-joint tolerance: 1e-4 * max(1, max |oracle grad| of the character)."""
     off = oracle.offsets(w["char_type"], w["types"])
