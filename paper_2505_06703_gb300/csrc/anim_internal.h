@@ -39,18 +39,30 @@ struct TypeDev {
   // IK views: the active subtree of a type; view joint j reads row gather[j]
   // of the full type (nullptr = identity).
   const int32_t *gather;
-  // Walk mode (shallow skeletons): natural chains (uncut) in level order;
-  // record k = (first joint, end joint, parent of the first joint, 0).
-  int walk;                  // 1: scan by level-ordered chain walks, 0: pointer jumping over segments
-  int nlev;                  // chain levels
-  int nwrec;                 // chains
+  // Chain-walk frame kernel (k_walk): a static lane schedule of wk_S steps
+  // for wk_P lanes per character; entry [s][slot] names the joint lane `slot`
+  // composes at step s (kWInvalid: idle).  wk_mode 1: natural chains walked
+  // parent-first, branch-point matrices passed through shared memory;
+  // wk_mode 2: a pure chain cut into wk_P pieces joined by a warp-shuffle
+  // scan; 0: the type runs on the segmented CTA kernels only.
+  int wk_mode, wk_P, wk_logP, wk_S;
+  int wk_nbs;                // branch-point slots per character (mode 1)
   int pad2;
-  const int4 *wrec;          // [nwrec]
-  const int32_t *wlev;       // [nlev + 1] first record of each level
+  const uint32_t *wk_tab;    // [wk_S][wk_P]
+  const float4 *wk_keys;     // [clip][key][wk_S][4][wk_P] key-pair records in schedule order
+  const float4 *wk_bind;     // [wk_S][3][wk_P] inverse-bind rows in schedule order
 };
-constexpr int kWalkMaxChains = 256;
-constexpr int kWalkMaxLevels = 64;
-constexpr int kWalkMaxDepth = 160;
+// Chain-walk schedule entries: joint | flags | load slot | store slot; bit 31
+// set marks an idle entry.
+constexpr uint32_t kWInvalid = 0xFFFFFFFFu;
+constexpr uint32_t kWJoint = 0xFFFu;        // bits 0-11
+constexpr uint32_t kWStart = 1u << 12;      // first joint of a chain: M = slot[load] * L (or L at a root)
+constexpr uint32_t kWStore = 1u << 13;      // branch point: keep M in slot[store]
+constexpr int kWLoadShift = 15;             // bits 15-22
+constexpr int kWStoreShift = 23;            // bits 23-30
+constexpr uint32_t kWRootSlot = 255;        // load slot of a chain that starts at a root
+constexpr int kWalkMaxSteps = 160;          // longest schedule the walk kernel takes (latency bound)
+constexpr int kWalkMaxSmem = 12 * 1024;     // shared memory of one walk CTA (branch slots)
 // Static shared memory the persistent kernels may use besides the dynamic
 // item buffers (two staged work items, scan scratch); the host subtracts it
 // from the per-CTA budget.
@@ -172,6 +184,30 @@ struct AdjointArgs {
   float lr, beta1, beta2, eps;
 };
 cudaError_t launch_adjoint(int mode, const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+
+// Chain-walk frame kernel: one-warp CTAs, each pulling work items (at most
+// 32 / wk_P characters of one walk type sharing the key index k0) from the
+// queue and composing them lane-parallel along the type's schedule.
+struct WalkArgs {
+  const TypeDev *types;
+  const WorkItem *items;
+  int n_items;
+  int nbs_max;                 // branch-point slot capacity per character
+  const int32_t *item_chars;
+  const int64_t *row_off;
+  int *queue_head;             // 0 at launch; reset by the last CTA
+  int *done;
+  int *status;
+  const float *time, *blend_w;
+  float *skin;
+};
+size_t walk_smem_bytes(int chars_per_item, int nbs);
+cudaError_t launch_walk(const WalkArgs &a, int ctas, size_t smem, cudaStream_t s);
+int walk_blocks_per_sm(size_t smem);  // resident one-warp CTAs per SM at this shared-memory size
+// Fill a type's schedule-ordered key records and inverse-bind rows from its
+// key table ([clip][key][n][2] float4) and inverse binds ([n][3] float4).
+cudaError_t launch_build_walk(const TypeDev &T, const float4 *keys, float4 *wk_keys, float4 *wk_bind,
+                              cudaStream_t s);
 
 // Setup kernels.
 cudaError_t launch_prepare_keys(float4 *keys, int n_clips, int n_keys, int n, cudaStream_t s);

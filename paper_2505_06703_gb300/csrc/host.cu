@@ -141,6 +141,210 @@ std::vector<int32_t> depths_of(const std::vector<int32_t> &par) {
 
 int default_seg_len(int) { return 16; }
 
+// ------------------------------------------------------------ walk schedules
+// Static lane schedule of the chain-walk frame kernel for one character on
+// P lanes.  mode 1: natural chains (consecutive joints, parent[i+1] == i),
+// list-scheduled on P lanes: a free lane takes the ready chain with the
+// longest path to a leaf; a chain is ready one step after its link joint
+// was composed.  Joints that chains hang from keep their model pose in a
+// branch slot from their step to the last start that reads it (slots reused
+// by interval colouring).  mode 2: a pure chain cut into P pieces.
+struct WalkSched {
+  int mode = 0, P = 0, logP = 0, S = 0, nbs = 0;
+  std::vector<uint32_t> tab;  // [S][P]
+};
+
+static int ilog2(int p) {
+  int l = 0;
+  while ((1 << l) < p) ++l;
+  return l;
+}
+
+WalkSched walk_chain(int n, int P) {
+  WalkSched W;
+  W.mode = 2;
+  W.P = P;
+  W.logP = ilog2(P);
+  const int L = (n + P - 1) / P;
+  W.S = L;
+  W.tab.assign((size_t)L * P, kWInvalid);
+  for (int l = 0; l < P; ++l) {
+    const int a0 = l * L, a1 = std::min(n, a0 + L);
+    for (int j = a0; j < a1; ++j) W.tab[(size_t)(j - a0) * P + l] = (uint32_t)j;
+  }
+  return W;
+}
+
+WalkSched walk_tree(const std::vector<int32_t> &par, int P) {
+  WalkSched W;
+  const int n = (int)par.size();
+  std::vector<int> cs;
+  for (int i = 0; i < n; ++i)
+    if (i == 0 || par[i] != i - 1) cs.push_back(i);
+  const int nc = (int)cs.size();
+  cs.push_back(n);
+  std::vector<int> h(n, 1);  // joints on the longest downward path
+  for (int j = n - 1; j > 0; --j)
+    if (par[j] >= 0) h[par[j]] = std::max(h[par[j]], h[j] + 1);
+  std::vector<std::vector<int>> kids(n);  // chains hanging from each joint
+  const int kNever = 1 << 30;
+  std::vector<int> ready(nc, kNever), start(nc, -1), lane_of(nc, -1), step(n, -1);
+  for (int c = 0; c < nc; ++c) {
+    const int lk = par[cs[c]];
+    if (lk < 0)
+      ready[c] = 0;
+    else
+      kids[lk].push_back(c);
+  }
+  std::vector<int> lane_free(P, 0);
+  for (int it = 0; it < nc; ++it) {
+    const int l = (int)(std::min_element(lane_free.begin(), lane_free.end()) - lane_free.begin());
+    const int f = lane_free[l];
+    int best = -1;
+    for (int c = 0; c < nc; ++c)
+      if (start[c] < 0 && ready[c] <= f && (best < 0 || h[cs[c]] > h[cs[best]])) best = c;
+    if (best < 0)
+      for (int c = 0; c < nc; ++c)
+        if (start[c] < 0 && ready[c] < kNever &&
+            (best < 0 || ready[c] < ready[best] || (ready[c] == ready[best] && h[cs[c]] > h[cs[best]])))
+          best = c;
+    if (best < 0) return W;  // unreachable for a forest with parent[i] < i
+    const int st = std::max(f, ready[best]);
+    start[best] = st;
+    lane_of[best] = l;
+    for (int j = cs[best]; j < cs[best + 1]; ++j) {
+      step[j] = st + (j - cs[best]);
+      for (int k : kids[j]) ready[k] = step[j] + 1;
+    }
+    lane_free[l] = st + (cs[best + 1] - cs[best]);
+  }
+  const int S = *std::max_element(lane_free.begin(), lane_free.end());
+  // branch slots: store at step[j], free after the last child chain start
+  std::vector<int> bps;
+  for (int j = 0; j < n; ++j)
+    if (!kids[j].empty()) bps.push_back(j);
+  std::sort(bps.begin(), bps.end(), [&](int x, int y) { return step[x] < step[y]; });
+  std::vector<int> slot_of(n, -1), slot_free;  // slot_free[s]: last step the slot is read
+  for (int j : bps) {
+    int last = 0;
+    for (int k : kids[j]) last = std::max(last, start[k]);
+    int sl = -1;
+    for (size_t q = 0; q < slot_free.size(); ++q)
+      if (slot_free[q] < step[j]) {
+        sl = (int)q;
+        break;
+      }
+    if (sl < 0) {
+      sl = (int)slot_free.size();
+      slot_free.push_back(0);
+    }
+    slot_free[sl] = last;
+    slot_of[j] = sl;
+  }
+  if ((int)slot_free.size() > (int)kWRootSlot - 1) return W;
+  W.mode = 1;
+  W.P = P;
+  W.logP = ilog2(P);
+  W.S = S;
+  W.nbs = (int)slot_free.size();
+  W.tab.assign((size_t)S * P, kWInvalid);
+  for (int c = 0; c < nc; ++c) {
+    const int len = cs[c + 1] - cs[c], lk = par[cs[c]];
+    for (int i = 0; i < len; ++i) {
+      const int j = cs[c] + i;
+      uint32_t e = (uint32_t)j;
+      if (i == 0) e |= kWStart | ((lk < 0 ? kWRootSlot : (uint32_t)slot_of[lk]) << kWLoadShift);
+      if (slot_of[j] >= 0) e |= kWStore | ((uint32_t)slot_of[j] << kWStoreShift);
+      W.tab[(size_t)(start[c] + i) * P + lane_of[c]] = e;
+    }
+  }
+  return W;
+}
+
+// Replays a schedule on the host: every joint exactly once, a chain start
+// reads the slot its link joint wrote at an earlier step and nobody
+// overwrote since, no slot is written and read in the same step, a chain
+// continues on its lane at the next step.  Returns false on any violation.
+bool walk_check(const WalkSched &W, const std::vector<int32_t> &par) {
+  const int n = (int)par.size();
+  if (W.mode == 0 || W.P < 1 || W.P > 32 || (W.P & (W.P - 1)) || W.S < 1) return false;
+  std::vector<int> seen(n, 0), done_step(n, -1), lane_at(n, -1), owner(std::max(W.nbs, 1), -1);
+  const int L = W.S;  // mode 2: piece length
+  for (int s = 0; s < W.S; ++s) {
+    std::vector<int> read_slot, write_slot;
+    for (int l = 0; l < W.P; ++l) {
+      const uint32_t e = W.tab[(size_t)s * W.P + l];
+      if (e == kWInvalid) continue;
+      const int j = (int)(e & kWJoint);
+      if (j >= n || seen[j]++) return false;
+      done_step[j] = s;
+      lane_at[j] = l;
+      if (W.mode == 2) {
+        if (j != l * L + s) return false;  // piece l = joints [l L, l L + L) in lane order
+        continue;
+      }
+      if (e & kWStart) {
+        const uint32_t ls = (e >> kWLoadShift) & 0xFFu;
+        if (par[j] < 0) {
+          if (ls != kWRootSlot) return false;
+        } else {
+          if (ls >= (uint32_t)W.nbs || owner[ls] != par[j] || done_step[par[j]] < 0 || done_step[par[j]] >= s)
+            return false;
+          read_slot.push_back((int)ls);
+        }
+      } else if (j == 0 || par[j] != j - 1 || done_step[j - 1] != s - 1 || lane_at[j - 1] != l) {
+        return false;
+      }
+      if (e & kWStore) write_slot.push_back((int)((e >> kWStoreShift) & 0xFFu));
+    }
+    for (int w : write_slot) {
+      if (w >= W.nbs || std::count(read_slot.begin(), read_slot.end(), w)) return false;
+    }
+    for (int l = 0; l < W.P; ++l) {
+      const uint32_t e = W.tab[(size_t)s * W.P + l];
+      if (e != kWInvalid && (e & kWStore)) owner[(e >> kWStoreShift) & 0xFFu] = (int)(e & kWJoint);
+    }
+  }
+  for (int j = 0; j < n; ++j)
+    if (seen[j] != 1) return false;
+  if (W.mode == 2)
+    for (int j = 1; j < n; ++j)
+      if (par[j] != j - 1) return false;
+  return true;
+}
+
+// Pick the type's walk schedule: a pure chain takes mode 2 beyond
+// kWalkMaxSteps joints; otherwise mode 1 on the lane count whose schedule
+// keeps lanes busiest, preferring fewer steps among counts within 15 % of
+// the best lane utilization.  A type whose best utilization is below 60 %,
+// or whose schedule is longer than kWalkMaxSteps, stays off the walk kernel.
+WalkSched choose_walk(const std::vector<int32_t> &par) {
+  const int n = (int)par.size();
+  bool chain = par[0] < 0;
+  for (int j = 1; j < n && chain; ++j) chain = par[j] == j - 1;
+  if (chain && n > kWalkMaxSteps) {
+    int P = 1;
+    while (P < 32 && n / (2 * P) >= 16) P *= 2;
+    WalkSched W = walk_chain(n, P);
+    return walk_check(W, par) ? W : WalkSched{};
+  }
+  std::vector<WalkSched> cand;
+  double best = 0.0;
+  for (int P = 1; P <= 32; P *= 2) {
+    WalkSched W = walk_tree(par, P);
+    if (W.mode == 0 || W.S > kWalkMaxSteps) continue;
+    if (walk_smem_bytes(32 / P, W.nbs) > kWalkMaxSmem) continue;
+    if (!walk_check(W, par)) continue;
+    best = std::max(best, (double)n / ((double)W.S * P));
+    cand.push_back(std::move(W));
+  }
+  if (best < 0.6) return WalkSched{};
+  WalkSched *pick = nullptr;
+  for (auto &W : cand)
+    if ((double)n / ((double)W.S * W.P) >= 0.85 * best && (!pick || W.S < pick->S)) pick = &W;
+  return pick ? std::move(*pick) : WalkSched{};
+}
+
 // ------------------------------------------------------------ device blocks
 struct DevBlock {
   void *ptr = nullptr;
@@ -184,52 +388,22 @@ struct TypeHost {
   int n_clips = 0, n_keys = 0;
   float rate = 0.f;
   std::vector<int32_t> gather;  // IK views only
-  std::vector<int4> wrec;       // walk mode: chains in level order
-  std::vector<int32_t> wlev;
-  bool walk = false;
-  bool allow_walk = false;      // chosen by the autotuner; off by default
+  WalkSched ws;                 // chain-walk schedule (mode 0: not walkable)
+  bool ws_done = false;
+  float4 *d_wkeys = nullptr;    // schedule-ordered key records
+  float4 *d_wbind = nullptr;    // schedule-ordered inverse binds
   TypeDev dev{};
   ~TypeHost() {
-    if (d_tables) cudaFree(d_tables);
-    if (d_inv_bind) cudaFree(d_inv_bind);
-    if (d_keys) cudaFree(d_keys);
-  }
-  // Walk mode for shallow skeletons: natural chains (uncut) ordered by chain
-  // level (a chain's parent joint lies in a lower level).
-  void analyze_walk() {
-    wrec.clear();
-    wlev.clear();
-    walk = false;
-    if (!allow_walk || max_depth > kWalkMaxDepth) return;
-    std::vector<int> cs, lev;
-    std::vector<int> chain_of(n);
-    for (int i = 0; i < n; ++i) {
-      if (i == 0 || parent[i] != i - 1) cs.push_back(i);
-      chain_of[i] = (int)cs.size() - 1;
-    }
-    const int nc = (int)cs.size();
-    if (nc > kWalkMaxChains) return;
-    cs.push_back(n);
-    lev.resize(nc);
-    int nl = 0;
-    for (int c = 0; c < nc; ++c) {
-      const int lk = parent[cs[c]];
-      lev[c] = lk < 0 ? 0 : lev[chain_of[lk]] + 1;
-      nl = std::max(nl, lev[c] + 1);
-    }
-    if (nl > kWalkMaxLevels) return;
-    for (int l = 0; l < nl; ++l) {
-      wlev.push_back((int)wrec.size());
-      for (int c = 0; c < nc; ++c)
-        if (lev[c] == l) wrec.push_back(make_int4(cs[c], cs[c + 1], parent[cs[c]], 0));
-    }
-    wlev.push_back((int)wrec.size());
-    walk = true;
+    for (void *p : {(void *)d_tables, (void *)d_inv_bind, (void *)d_keys, (void *)d_wkeys, (void *)d_wbind})
+      if (p) cudaFree(p);
   }
   cudaError_t build_tables() {
     seg = analyze_segments(parent, seg_len);
     dfsord = analyze_dfs(parent);
-    analyze_walk();
+    if (!ws_done) {
+      ws = choose_walk(parent);
+      ws_done = true;
+    }
     if (d_tables) {
       cudaFree(d_tables);
       d_tables = nullptr;
@@ -247,8 +421,7 @@ struct TypeHost {
     const size_t o_g = B.add(gather.data(), gather.size() * 4);
     const size_t o_js = B.add(seg.job_start.data(), seg.job_start.size() * 4);
     const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
-    const size_t o_wr = B.add(wrec.data(), wrec.size() * sizeof(int4));
-    const size_t o_wl = B.add(wlev.data(), wlev.size() * 4);
+    const size_t o_wt = B.add(ws.tab.data(), ws.tab.size() * 4);
     void *d = nullptr;
     cudaError_t e = B.upload(&d);
     if (e != cudaSuccess) {
@@ -274,11 +447,12 @@ struct TypeHost {
     dev.njobs = (int)seg.job_start.size() - 1;
     dev.job_start = (const int32_t *)(base + o_js);
     dev.jinfo = (const uint32_t *)(base + o_ji);
-    dev.walk = walk ? 1 : 0;
-    dev.nlev = walk ? (int)wlev.size() - 1 : 0;
-    dev.nwrec = (int)wrec.size();
-    dev.wrec = (const int4 *)(base + o_wr);
-    dev.wlev = (const int32_t *)(base + o_wl);
+    dev.wk_mode = ws.mode;
+    dev.wk_P = ws.P;
+    dev.wk_logP = ws.logP;
+    dev.wk_S = ws.S;
+    dev.wk_nbs = ws.nbs;
+    dev.wk_tab = ws.mode ? (const uint32_t *)(base + o_wt) : nullptr;
     sync_dev();
     return cudaSuccess;
   }
@@ -288,6 +462,26 @@ struct TypeHost {
     dev.rate = rate;
     dev.inv_bind = d_inv_bind;
     dev.keys = d_keys;
+    dev.wk_keys = d_wkeys;
+    dev.wk_bind = d_wbind;
+  }
+  // Schedule-ordered key records (when clips are uploaded) and inverse binds
+  // of a walkable type; synchronous.
+  cudaError_t build_walk_data() {
+    if (ws.mode == 0 || !d_inv_bind) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!d_wbind) e = cudaMalloc(&d_wbind, (size_t)ws.S * ws.P * 3 * sizeof(float4));
+    if (e != cudaSuccess) return e;
+    if (n_clips > 0) {
+      if (d_wkeys) cudaFree(d_wkeys);
+      d_wkeys = nullptr;
+      e = cudaMalloc(&d_wkeys, (size_t)n_clips * n_keys * ws.S * ws.P * 4 * sizeof(float4));
+      if (e != cudaSuccess) return e;
+    }
+    sync_dev();
+    e = launch_build_walk(dev, d_keys, n_clips > 0 ? d_wkeys : nullptr, d_wbind, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e;
   }
 };
 
@@ -324,7 +518,13 @@ struct anim_plan {
   int32_t *d_used = nullptr, *d_cap = nullptr;
   LaunchCfg cfg_scan{}, cfg_adj{};
   size_t smem_frame = 0;
-  int adj_unfit = -1;  // a type whose adjoint working set does not fit this schedule, else -1
+  int adj_unfit = -1;
+  // frame: item slots [0, n_slots_walk) belong to the chain-walk kernel
+  // (queue counters d_queue[0..1]), the rest to the segmented CTA kernel
+  // (d_queue[2..3])
+  int n_slots_walk = 0;
+  int walk_ctas = 0, walk_nbs = 0;
+  size_t walk_smem = 0;  // a type whose adjoint working set does not fit this schedule, else -1
   ~anim_plan() {
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
                     (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
@@ -361,6 +561,9 @@ struct anim_ctx {
   int *d_status = nullptr;
   int version = 0;  // bumps when types/schedules change
   int ctas_per_sm = 2;            // resident persistent CTAs per SM the schedule is sized for
+  int use_walk = 1;               // frame: walkable types run on the chain-walk kernel
+  cudaStream_t side = nullptr;    // frame: the CTA kernel's stream when both kernels have work
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int joints_per_item = kTargetJointsPerItem;  // target work-item size (characters x joints)
   std::set<anim_plan *> plans;
   std::set<anim_ik *> iks;
@@ -374,6 +577,9 @@ struct anim_ctx {
     for (auto *k : iks) delete k;
     if (d_types) cudaFree(d_types);
     if (d_status) cudaFree(d_status);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
   }
 };
 
@@ -493,23 +699,50 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->n_items_adj = (int)ia.size();
   CK(upload_vec(&P->d_items_scan, is));
   CK(upload_vec(&P->d_items_adj, ia));
-  CK(upload_vec(&P->d_cap, P->C_scan));
+  // frame: walkable types (chain-walk kernel, 32 / P characters per item)
+  // take the first item regions, the others follow
+  std::vector<int32_t> cap(P->C_scan);
+  std::vector<char> walk_t(nt, 0);
+  int wcmax = 0;
+  P->walk_nbs = 0;
+  for (int t : P->used) {
+    const TypeHost &T = *ctx->types[t];
+    if (!ctx->use_walk || T.ws.mode == 0) continue;
+    walk_t[t] = 1;
+    cap[t] = 32 / T.ws.P;
+    wcmax = std::max(wcmax, cap[t]);
+    P->walk_nbs = std::max(P->walk_nbs, T.ws.nbs);
+  }
+  CK(upload_vec(&P->d_cap, cap));
   // frame work queue: ranges of <= kRangeChars characters of one type, each
   // with an item slot region large enough for any key distribution
   std::vector<RangeDev> ranges;
   int slots = 0;
-  for (size_t u = 0; u < P->used.size(); ++u) {
-    const int t = P->used[u];
-    const int cnt = (int)P->by_type[u].size(), C = P->C_scan[t], nk = ctx->types[t]->n_keys;
-    for (int k = 0; k < cnt; k += kRangeChars) {
-      RangeDev r;
-      r.type = t;
-      r.start = P->type_chars_start[u] + k;
-      r.count = std::min(kRangeChars, cnt - k);
-      r.region = slots;
-      slots += (r.count + C - 1) / C + std::min(r.count, std::max(nk, 1));
-      ranges.push_back(r);
+  P->n_slots_walk = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (size_t u = 0; u < P->used.size(); ++u) {
+      const int t = P->used[u];
+      if (walk_t[t] != (pass == 0)) continue;
+      const int cnt = (int)P->by_type[u].size(), C = cap[t], nk = ctx->types[t]->n_keys;
+      for (int k = 0; k < cnt; k += kRangeChars) {
+        RangeDev r;
+        r.type = t;
+        r.start = P->type_chars_start[u] + k;
+        r.count = std::min(kRangeChars, cnt - k);
+        r.region = slots;
+        slots += (r.count + C - 1) / C + std::min(r.count, std::max(nk, 1));
+        ranges.push_back(r);
+      }
     }
+    if (pass == 0) P->n_slots_walk = slots;
+  }
+  P->walk_smem = P->n_slots_walk > 0 ? walk_smem_bytes(wcmax, P->walk_nbs) : 0;
+  P->walk_ctas = 0;
+  if (P->n_slots_walk > 0) {
+    const int nb = walk_blocks_per_sm(P->walk_smem);
+    if (nb < 1) return fail(ctx, ANIM_ECUDA, "chain-walk kernel: no resident CTA at %zu bytes of shared memory",
+                            P->walk_smem);
+    P->walk_ctas = ctx->sm_count * nb;
   }
   P->n_ranges = (int)ranges.size();
   P->n_slots = slots;
@@ -617,6 +850,7 @@ int anim_create_skeletons(anim_ctx *ctx, int n_types, const int32_t *joint_count
       if (e != cudaSuccess) return fail(ctx, ANIM_ECUDA, "inverse bind from rest pose: %s", cudaGetErrorString(e));
     }
     T->sync_dev();
+    CK(T->build_walk_data());
     ctx->types.push_back(std::move(T));
     off += n;
   }
@@ -644,6 +878,7 @@ int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, f
   T.n_clips = n_clips;
   T.n_keys = n_keys;
   T.rate = rate_hz;
+  CK(T.build_walk_data());
   CK(upload_types(ctx));
   return ANIM_OK;
 }
@@ -778,22 +1013,57 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
   if (!d_blend_w || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
   if (!aligned16(d_skin) || !aligned4(d_blend_w))
     return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned, d_blend_w 4-byte aligned");
-  ScanArgs a{};
-  a.types = ctx->d_types;
-  a.items = plan->d_items_frame;
-  a.n_items = plan->n_slots;
-  a.item_chars = plan->d_sorted;
-  a.row_off = plan->d_row_off;
-  a.queue_head = plan->d_queue;
-  a.done = plan->d_queue + 1;  // the last CTA resets the head for the plan's other launches
-  a.status = ctx->d_status;
-  a.time = d_time;
-  a.blend_w = d_blend_w;
-  a.skin = d_skin;
-  LaunchCfg cfg = plan->cfg_scan;
-  cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
-  cfg.smem = plan->smem_frame;
-  CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
+  cudaStream_t st = (cudaStream_t)stream, cta_st = st;
+  const bool has_walk = plan->n_slots_walk > 0, has_cta = plan->n_slots > plan->n_slots_walk;
+  if (has_walk && has_cta) {
+    // the two kernels run side by side: fork onto the context's side stream
+    if (!ctx->side) {
+      CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ctx->ev_fork, st));
+    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    cta_st = ctx->side;
+  }
+  if (has_cta) {
+    ScanArgs a{};
+    a.types = ctx->d_types;
+    a.items = plan->d_items_frame + plan->n_slots_walk;
+    a.n_items = plan->n_slots - plan->n_slots_walk;
+    a.item_chars = plan->d_sorted;
+    a.row_off = plan->d_row_off;
+    a.queue_head = plan->d_queue + 2;
+    a.done = plan->d_queue + 3;  // the last CTA resets the head
+    a.status = ctx->d_status;
+    a.time = d_time;
+    a.blend_w = d_blend_w;
+    a.skin = d_skin;
+    LaunchCfg cfg = plan->cfg_scan;
+    cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
+    cfg.smem = plan->smem_frame;
+    CK(launch_scan(0, a, cfg, cta_st));
+  }
+  if (has_walk) {
+    WalkArgs w{};
+    w.types = ctx->d_types;
+    w.items = plan->d_items_frame;
+    w.n_items = plan->n_slots_walk;
+    w.nbs_max = plan->walk_nbs;
+    w.item_chars = plan->d_sorted;
+    w.row_off = plan->d_row_off;
+    w.queue_head = plan->d_queue;
+    w.done = plan->d_queue + 1;
+    w.status = ctx->d_status;
+    w.time = d_time;
+    w.blend_w = d_blend_w;
+    w.skin = d_skin;
+    CK(launch_walk(w, plan->walk_ctas, plan->walk_smem, st));
+  }
+  if (has_walk && has_cta) {
+    CK(cudaEventRecord(ctx->ev_join, ctx->side));
+    CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  }
   return ANIM_OK;
 }
 
@@ -1071,11 +1341,11 @@ static uint64_t mix_hash(const anim_ctx *ctx, const anim_plan *P, int which) {
 static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps, int jpi, int walk) {
   ctx->ctas_per_sm = cps;
   ctx->joints_per_item = jpi;
+  ctx->use_walk = walk != 0;
   for (int t : P->used) {
     TypeHost &T = *ctx->types[t];
-    if (T.seg_len != seg_len || T.allow_walk != (walk != 0)) {
+    if (T.seg_len != seg_len) {
       T.seg_len = seg_len;
-      T.allow_walk = walk != 0;
       CK(T.build_tables());
     }
   }
@@ -1149,11 +1419,13 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   };
   anim_ctx::TuneChoice best{0, 0, 0, 0, 1e30f};
   const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {1024, 2048, 4096};
-  for (int walk = 0; walk < 2; ++walk)
+  // the chain-walk kernel serves the frame only: other searches keep the
+  // context's setting
+  const int walk_lo = which == 0 ? 0 : ctx->use_walk, walk_hi = which == 0 ? 1 : ctx->use_walk;
+  for (int walk = walk_lo; walk <= walk_hi; ++walk)
     for (int seg : segs)
       for (int cps : cpss)
         for (int jpi : jpis) {
-          if (walk && seg != 16) continue;  // segment length does not matter to walk-mode types
           if (cps == 3 && which == 2) continue;  // the adjoint kernel is built for up to 2 CTAs/SM
           if (apply_choice(ctx, plan, seg, cps, jpi, walk) != ANIM_OK) continue;  // e.g. does not fit
           bool ok = true;
@@ -1184,7 +1456,7 @@ int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out4) {
   out4[0] = T ? T->seg_len : 16;
   out4[1] = ctx->ctas_per_sm;
   out4[2] = ctx->joints_per_item;
-  out4[3] = T && T->allow_walk ? 1 : 0;
+  out4[3] = ctx->use_walk;
   return ANIM_OK;
 }
 

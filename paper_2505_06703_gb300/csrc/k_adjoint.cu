@@ -136,11 +136,9 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
     stage_tables(b, Lt, tid);
     pass1a_qt(b, P, cs4, a.q, a.t, tid);
     compute_sync();
-    if (b.T.walk) {
-      pass_walk(b, P, cs4, tid);
-    } else {
-      pass1b(b, Lt, P, cs4, tid);
-      compute_sync();
+    pass1b(b, Lt, P, cs4, tid);
+    compute_sync();
+    {
       const float4 *Y = pass2(b, Lt, P, cs4, tid);
       for (int idx = tid; idx < CN; idx += kComputeThreads) {
         const int c = (int)b.divN.div(idx), j = idx - c * n;

@@ -105,18 +105,11 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     }
     compute_sync();
 
-    const bool walk = b.T.walk != 0;
-    const float4 *Y = Lt.Y0;
-    if (walk) {
-      // ---- shallow skeleton: level-ordered chain walks give M_j in place
-      pass_walk(b, P, cs4, tid);
-    } else {
-      // ---- pass 1b: running products along segments
-      pass1b(b, Lt, P, cs4, tid);
-      compute_sync();
-      // ---- pass 2: pointer jumping over segments
-      Y = pass2(b, Lt, P, cs4, tid);
-    }
+    // ---- pass 1b: running products along segments
+    pass1b(b, Lt, P, cs4, tid);
+    compute_sync();
+    // ---- pass 2: pointer jumping over segments
+    const float4 *Y = pass2(b, Lt, P, cs4, tid);
 
     // ---- pass 3: model pose, bind, stage in place
     {
@@ -131,7 +124,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
         for (int c = grp * cpt; c < c1; ++c) {
           float4 *slot = P + c * cs4 + 3 * j;
           Aff m = lds_aff(slot);
-          if (!walk && (info & kJ16Link)) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
+          if (info & kJ16Link) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
           if (MODEL && SKIN) stg_aff(reinterpret_cast<float4 *>(a.model) + (b.off[c] + j) * 3, m);
           if (SKIN) m = aff_mul(m, B);
           sts_aff(slot, m);

@@ -51,8 +51,6 @@ struct ItemBuf {
   int cid[kCMax];
   float alpha[kCMax];        // frame: fraction between keys k0 and k0+1
   float blend[kCMax];        // frame: clip blend weight
-  int4 wrec[kWalkMaxChains];  // walk mode: the type's chain records
-  int wlev[kWalkMaxLevels + 1];
 };
 static_assert(2 * sizeof(ItemBuf) + 2048 <= kStaticSmemAllowance, "item buffers exceed the static allowance");
 
@@ -80,13 +78,6 @@ __device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_it
   int *dst = reinterpret_cast<int *>(&b.T);
   for (int k = lane; k < (int)(sizeof(TypeDev) / 4); k += 32) dst[k] = src[k];
   const float rate = types[wi.type].rate;
-  if (types[wi.type].walk) {
-    const int nrec = types[wi.type].nwrec, nlev = types[wi.type].nlev;
-    const int4 *wr = types[wi.type].wrec;
-    const int32_t *wl = types[wi.type].wlev;
-    for (int k = lane; k < nrec; k += 32) b.wrec[k] = __ldg(wr + k);
-    for (int k = lane; k <= nlev; k += 32) b.wlev[k] = __ldg(wl + k);
-  }
   for (int c = lane; c < wi.count; c += 32) {
     const int cid = __ldg(item_chars + wi.start + c);
     b.cid[c] = cid;
@@ -217,36 +208,6 @@ __device__ __forceinline__ void pass1b(const ItemBuf &b, const ItemLayout &Lt, f
       acc = aff_mul(acc, L);
       sts_aff(Pc + 3 * j, acc);
     }
-  }
-}
-
-// Walk mode (replaces passes 1b and 2 on shallow skeletons): chains in level
-// order; a chain's parent joint belongs to a lower level, so its model pose
-// is final and the walk forms M_j = M_prev L_j directly, in place.
-__device__ __forceinline__ void pass_walk(const ItemBuf &b, float4 *P, int cs4, int tid) {
-  const int C = b.C;
-  for (int l = 0; l < b.T.nlev; ++l) {
-    const int s0 = b.wlev[l], NL = (b.wlev[l + 1] - s0) * C;
-    for (int idx = tid; idx < NL; idx += kComputeThreads) {
-      const int k = (int)b.divC.div(idx), c = idx - k * C;
-      const int4 r = b.wrec[s0 + k];
-      float4 *Pc = P + c * cs4;
-      Aff m = lds_aff(Pc + 3 * r.x);
-      if (r.z >= 0) {
-        m = aff_mul(lds_aff(Pc + 3 * r.z), m);
-        sts_aff(Pc + 3 * r.x, m);
-      }
-      if (r.x + 1 < r.y) {
-        Aff nxt = lds_aff(Pc + 3 * (r.x + 1));
-        for (int j = r.x + 1; j < r.y; ++j) {
-          const Aff L = nxt;
-          if (j + 1 < r.y) nxt = lds_aff(Pc + 3 * (j + 1));
-          m = aff_mul(m, L);
-          sts_aff(Pc + 3 * j, m);
-        }
-      }
-    }
-    compute_sync();
   }
 }
 
