@@ -201,9 +201,11 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
 
 /* Autotuner (no counterpart in the paper; it picks the schedule of the
  * scan): times every candidate schedule -- segment length 4/8/16/32 for the
- * pointer-jumping scan or level-ordered chain walks for skeletons of depth
- * <= 160, 1, 2 or 3 resident CTAs per SM (3 for the frame and forward only),
- * work items of about 1,024/2,048/4,096 joints -- of
+ * pointer-jumping scan, 1, 2 or 3 resident CTAs per SM (3 for the frame and
+ * forward only), work items of about 1,024/2,048/4,096 joints, and for the
+ * frame whether walkable types (chain schedules of at most 160 steps with
+ * most lanes busy, and pure chains) run on the one-warp chain-walk kernel
+ * beside the segmented kernel -- of
  * `which` (0 = fused frame, 1 = forward_local, 2 = loss_backward) with CUDA
  * events on scratch inputs it allocates, and keeps the fastest.  The result
  * is cached in the context per hash of (which, type ids, joint counts,
@@ -214,19 +216,21 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
  * which = 0 needs clips for every type of the plan. */
 ANIM_API int anim_tune(anim_ctx *ctx, anim_plan *plan, int which);
 
-/* The schedule the autotuner picked, as 4 integers: segment length, resident
- * CTAs per SM, work-item size in joints, walk mode (0/1) -- read with
- * anim_get_schedule (segment length and walk mode of the plan's first type)
- * and re-applied without timing by anim_set_schedule (for example in another
- * process); CTAs per SM is 1, 2 or 3.  anim_set_schedule returns
- * ANIM_EUNSUPPORTED and keeps the previous schedule when one character of a
- * type does not fit in a CTA's shared memory under the new one; a schedule
- * that fits the forward kernels but not the adjoint (which keeps two more
- * vectors per joint) is accepted, and anim_backward / anim_loss_backward
- * then return ANIM_EUNSUPPORTED until a schedule that fits is set.
- * Synchronous; not capturable. */
-ANIM_API int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out4);
-ANIM_API int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in4);
+/* The schedule the autotuner picked, as 5 integers: segment length, resident
+ * CTAs per SM, work-item size in joints, chain-walk kernel for the frame
+ * (0/1), adjoint kernel (0: persistent, k = 1..8: one work item per CTA,
+ * items sized so k CTAs share an SM) -- read with anim_get_schedule (segment
+ * length of the plan's first type) and re-applied without timing by
+ * anim_set_schedule (for example in another process); CTAs per SM is 1, 2
+ * or 3.  anim_set_schedule returns ANIM_EUNSUPPORTED and keeps the previous
+ * schedule when one character of a type does not fit in a CTA's shared
+ * memory under the new one; a schedule that fits the forward kernels but
+ * not the adjoint (which keeps two more vectors per joint) is accepted, and
+ * anim_backward / anim_loss_backward then return ANIM_EUNSUPPORTED until a
+ * schedule that fits is set.  An IK object keeps the adjoint kernel of the
+ * schedule it was created under.  Synchronous; not capturable. */
+ANIM_API int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out5);
+ANIM_API int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in5);
 
 /* Read and clear the device status word (synchronizes `stream`). */
 ANIM_API int anim_get_status(anim_ctx *ctx, void *stream, int *out_status);

@@ -231,11 +231,18 @@ class Context:
         self._ck(self.lib.anim_tune(self.h, plan.h, int(which)))
 
     def get_schedule(self, plan):
-        out = np.zeros(4, dtype=np.int32)
+        """[seg_len, ctas_per_sm, joints_per_item, walk, adj_ctas]"""
+        out = np.zeros(5, dtype=np.int32)
         self._ck(self.lib.anim_get_schedule(self.h, plan.h, _np_ptr(out)))
         return [int(x) for x in out]
 
     def set_schedule(self, plan, sched):
+        """Five values as get_schedule returns; four keep the current adjoint kernel."""
+        sched = list(sched)
+        if len(sched) == 4:
+            sched.append(self.get_schedule(plan)[4])
+        if len(sched) != 5:
+            raise ValueError("a schedule has 5 values")
         a = np.ascontiguousarray(sched, dtype=np.int32)
         self._ck(self.lib.anim_set_schedule(self.h, plan.h, _np_ptr(a)))
 

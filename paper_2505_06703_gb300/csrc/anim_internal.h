@@ -82,6 +82,9 @@ struct WorkItem {
 
 // Persistent kernels: 8 compute warps + 1 producer warp per CTA.
 constexpr int kPersistentThreads = 288;
+// One-item adjoint kernel: 4 warps, no producer; its static shared memory.
+constexpr int kAdjSmallThreads = 128;
+constexpr int kAdjSmallStatic = 2 * 1024;
 
 struct LaunchCfg {
   int threads;       // CTA size

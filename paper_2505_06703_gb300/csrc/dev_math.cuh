@@ -156,6 +156,65 @@ struct FastDiv {
   __device__ __forceinline__ uint32_t div(uint32_t x) const { return (__umulhi(x, m) + x) >> s; }
 };
 
+// ---- key-pair records (built once per clip upload from the raw keys)
+// Record of (clip, key k, joint j): keys k and k1 = (k + 1) mod n_keys of
+// the clip, normalized, b on a's hemisphere; theta = 2 atan2(|a - b|,
+// |a + b|); q_perp = (b - (a.b) a) / |b - (a.b) a| (0 when b == a); so the
+// slerp at fraction al is cos(al theta) a + sin(al theta) q_perp.
+//   r[0] = a, r[1] = q_perp, r[2] = (t_k, theta), r[3] = (t_k1 - t_k, 0).
+// keys: [clip][key][n][2] float4 (q xyzw, t xyz + pad).
+__device__ __forceinline__ void make_rec(const float4 *keys, int clip, int k, int nk, int n, int j, float4 *r) {
+  const int k1 = (k + 1 == nk) ? 0 : k + 1;
+  const float4 *ra = keys + (((size_t)clip * nk + k) * n + j) * 2;
+  const float4 *rb = keys + (((size_t)clip * nk + k1) * n + j) * 2;
+  const float4 qa = normalize4(ra[0]);
+  float4 qb = normalize4(rb[0]);
+  const float d = dot4(qa, qb);
+  if (d < 0.f) qb = make_float4(-qb.x, -qb.y, -qb.z, -qb.w);
+  const float ad = fabsf(d);
+  float dm = 0.f, dp = 0.f, t;
+  t = qa.x - qb.x; dm += t * t; t = qa.x + qb.x; dp += t * t;
+  t = qa.y - qb.y; dm += t * t; t = qa.y + qb.y; dp += t * t;
+  t = qa.z - qb.z; dm += t * t; t = qa.z + qb.z; dp += t * t;
+  t = qa.w - qb.w; dm += t * t; t = qa.w + qb.w; dp += t * t;
+  const float theta = 2.f * atan2f(sqrtf(dm), sqrtf(dp));
+  float4 v = make_float4(qb.x - ad * qa.x, qb.y - ad * qa.y, qb.z - ad * qa.z, qb.w - ad * qa.w);
+  const float nv = sqrtf(dot4(v, v));
+  v = nv > 0.f ? make_float4(v.x / nv, v.y / nv, v.z / nv, v.w / nv) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 ta = ra[1], tb = rb[1];
+  r[0] = qa;
+  r[1] = v;
+  r[2] = make_float4(ta.x, ta.y, ta.z, theta);
+  r[3] = make_float4(tb.x - ta.x, tb.y - ta.y, tb.z - ta.z, 0.f);
+}
+
+struct Rec {
+  float4 q0, qp, t0, dt;
+};
+
+// Key slerp from a precomputed record: cos(a theta) q0 + sin(a theta) q_perp,
+// which equals the normalized slerp between the two unit keys; lerp for t.
+__device__ __forceinline__ float4 rec_q(const Rec &r, float al) {
+  float s, c;
+  __sincosf(al * r.t0.w, &s, &c);
+  return make_float4(fmaf(c, r.q0.x, s * r.qp.x), fmaf(c, r.q0.y, s * r.qp.y), fmaf(c, r.q0.z, s * r.qp.z),
+                     fmaf(c, r.q0.w, s * r.qp.w));
+}
+
+__device__ __forceinline__ Aff sample_rec(const Rec &a, const Rec &b, float al, float w, bool two) {
+  float4 q = rec_q(a, al);
+  float tx = fmaf(al, a.dt.x, a.t0.x), ty = fmaf(al, a.dt.y, a.t0.y), tz = fmaf(al, a.dt.z, a.t0.z);
+  if (two) {
+    const float4 qb = rec_q(b, al);
+    const float bx = fmaf(al, b.dt.x, b.t0.x), by = fmaf(al, b.dt.y, b.t0.y), bz = fmaf(al, b.dt.z, b.t0.z);
+    q = slerp_unit(q, qb, w);
+    tx = fmaf(w, bx - tx, tx);
+    ty = fmaf(w, by - ty, ty);
+    tz = fmaf(w, bz - tz, tz);
+  }
+  return aff_from_qt(q, tx, ty, tz);
+}
+
 // ---- bulk copy shared -> global (cp.async.bulk, bulk-group completion)
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

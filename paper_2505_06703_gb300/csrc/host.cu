@@ -379,6 +379,8 @@ struct BlockBuilder {
 // A skeleton type (or an IK view of one): host analysis + device tables.
 struct TypeHost {
   int n = 0, max_depth = 0, seg_len = 8;
+  bool is_view = false;             // an internal relabelling of (part of) another type
+  std::unique_ptr<TypeHost> adj;    // the adjoint's view of this type (longest path first)
   std::vector<int32_t> parent, depth;
   Segments seg;
   DfsOrder dfsord;
@@ -401,8 +403,12 @@ struct TypeHost {
     seg = analyze_segments(parent, seg_len);
     dfsord = analyze_dfs(parent);
     if (!ws_done) {
-      ws = choose_walk(parent);
+      if (!is_view) ws = choose_walk(parent);
       ws_done = true;
+    }
+    if (!is_view) {
+      cudaError_t ev = build_adjoint_view();
+      if (ev != cudaSuccess) return ev;
     }
     if (d_tables) {
       cudaFree(d_tables);
@@ -456,6 +462,7 @@ struct TypeHost {
     sync_dev();
     return cudaSuccess;
   }
+  cudaError_t build_adjoint_view();
   void sync_dev() {
     dev.n_clips = n_clips;
     dev.n_keys = n_keys;
@@ -484,6 +491,59 @@ struct TypeHost {
     return e;
   }
 };
+
+// A view of the joints j with keep[j] (closed under parent) of type T,
+// numbered in depth-first pre-order that visits the child with the longest
+// path to a leaf first: natural chains then follow the longest paths, which
+// shortens the segment tree (fewer pointer-jumping rounds).  gather maps a
+// view joint to T's joint; vid (if given) receives T's joint -> view joint.
+std::unique_ptr<TypeHost> make_view(const TypeHost &T, const std::vector<char> &keep, std::vector<int> *vid_out,
+                                    cudaError_t *err) {
+  const int n = T.n;
+  std::vector<std::vector<int>> kids(n);
+  std::vector<int> roots, h(n, 1);
+  for (int j = n - 1; j >= 0; --j) {
+    if (!keep[j]) continue;
+    const int p = T.parent[j];
+    if (p < 0)
+      roots.push_back(j);
+    else {
+      kids[p].push_back(j);
+      h[p] = std::max(h[p], h[j] + 1);
+    }
+  }
+  std::reverse(roots.begin(), roots.end());
+  auto V = std::make_unique<TypeHost>();
+  V->is_view = true;
+  std::vector<int> vid(n, -1), st(roots.rbegin(), roots.rend());
+  while (!st.empty()) {
+    const int u = st.back();
+    st.pop_back();
+    vid[u] = (int)V->gather.size();
+    V->gather.push_back(u);
+    auto &k = kids[u];
+    std::stable_sort(k.begin(), k.end(), [&](int a, int b) { return h[a] != h[b] ? h[a] > h[b] : a < b; });
+    for (auto it = k.rbegin(); it != k.rend(); ++it) st.push_back(*it);
+  }
+  V->n = (int)V->gather.size();
+  for (int j : V->gather) V->parent.push_back(T.parent[j] < 0 ? -1 : vid[T.parent[j]]);
+  V->depth = depths_of(V->parent);
+  V->max_depth = *std::max_element(V->depth.begin(), V->depth.end());
+  V->seg_len = T.seg_len;
+  *err = V->build_tables();
+  // the adjoint kernel relies on the view's depth-first slots being its
+  // joint indices
+  for (int i = 0; i < V->n && *err == cudaSuccess; ++i)
+    if (V->dfsord.dfs[i] != i) *err = cudaErrorInvalidValue;
+  if (vid_out) *vid_out = std::move(vid);
+  return V;
+}
+
+cudaError_t TypeHost::build_adjoint_view() {
+  cudaError_t e = cudaSuccess;
+  adj = make_view(*this, std::vector<char>(n, 1), nullptr, &e);
+  return e;
+}
 
 struct Sched {
   int C = 1;  // characters per item
@@ -558,17 +618,19 @@ struct anim_ctx {
   std::string err;
   std::vector<std::unique_ptr<TypeHost>> types;
   TypeDev *d_types = nullptr;
+  TypeDev *d_adj_types = nullptr;  // the types' adjoint views, same ids
   int *d_status = nullptr;
   int version = 0;  // bumps when types/schedules change
   int ctas_per_sm = 2;            // resident persistent CTAs per SM the schedule is sized for
   int use_walk = 1;               // frame: walkable types run on the chain-walk kernel
+  int adj_ctas = 0;               // adjoint: 0 = persistent kernel, k = one-item kernel sized for k CTAs per SM
   cudaStream_t side = nullptr;    // frame: the CTA kernel's stream when both kernels have work
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int joints_per_item = kTargetJointsPerItem;  // target work-item size (characters x joints)
   std::set<anim_plan *> plans;
   std::set<anim_ik *> iks;
   struct TuneChoice {
-    int seg_len, ctas_per_sm, joints_per_item, walk;
+    int seg_len, ctas_per_sm, joints_per_item, walk, adj_ctas;
     float ms;
   };
   std::map<uint64_t, TuneChoice> tune_cache;  // (which, types, counts) hash -> best schedule
@@ -576,6 +638,7 @@ struct anim_ctx {
     for (auto *p : plans) delete p;
     for (auto *k : iks) delete k;
     if (d_types) cudaFree(d_types);
+    if (d_adj_types) cudaFree(d_adj_types);
     if (d_status) cudaFree(d_status);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
@@ -608,17 +671,22 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
 
 cudaError_t upload_types(anim_ctx *ctx) {
-  std::vector<TypeDev> host(ctx->types.size());
+  std::vector<TypeDev> host(ctx->types.size()), hadj(ctx->types.size());
   for (size_t t = 0; t < ctx->types.size(); ++t) {
     ctx->types[t]->sync_dev();
     host[t] = ctx->types[t]->dev;
+    hadj[t] = ctx->types[t]->adj->dev;
   }
-  if (ctx->d_types) cudaFree(ctx->d_types);
-  ctx->d_types = nullptr;
-  cudaError_t e = cudaMalloc(&ctx->d_types, std::max<size_t>(1, host.size()) * sizeof(TypeDev));
-  if (e != cudaSuccess) return e;
+  for (TypeDev **d : {&ctx->d_types, &ctx->d_adj_types}) {
+    if (*d) cudaFree(*d);
+    *d = nullptr;
+    cudaError_t e = cudaMalloc(d, std::max<size_t>(1, host.size()) * sizeof(TypeDev));
+    if (e != cudaSuccess) return e;
+  }
   ++ctx->version;
-  return cudaMemcpy(ctx->d_types, host.data(), host.size() * sizeof(TypeDev), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy(ctx->d_types, host.data(), host.size() * sizeof(TypeDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(ctx->d_adj_types, hadj.data(), hadj.size() * sizeof(TypeDev), cudaMemcpyHostToDevice);
 }
 
 size_t smem_budget(const anim_ctx *ctx) {
@@ -628,8 +696,15 @@ size_t smem_budget(const anim_ctx *ctx) {
   return std::min(ctx->smem_optin - kStaticSmemAllowance, per - 1024 - kStaticSmemAllowance);
 }
 
+// Shared memory one work item of the adjoint may use: the persistent
+// kernel's budget, or a 1/adj_ctas share of the SM for the one-item kernel.
+size_t adj_budget(const anim_ctx *ctx) {
+  if (ctx->adj_ctas <= 0) return smem_budget(ctx);
+  return ctx->smem_per_sm / (size_t)ctx->adj_ctas - 1024 - kAdjSmallStatic;
+}
+
 int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
-  const size_t budget = smem_budget(ctx);
+  const size_t budget = adjoint ? adj_budget(ctx) : smem_budget(ctx);
   int C = std::max(1, std::min(kCMax, ctx->joints_per_item / std::max(1, T.n)));
   auto bytes = [&](int c) {
     return adjoint ? adjoint_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
@@ -678,7 +753,7 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   size_t smem_s = 0, smem_a = 0;
   for (int t : P->used) {
     const TypeHost &T = *ctx->types[t];
-    const int cs = choose_C(ctx, T, false), ca = choose_C(ctx, T, true);
+    const int cs = choose_C(ctx, T, false), ca = choose_C(ctx, *T.adj, true);
     if (cs == 0)
       return fail(ctx, ANIM_EUNSUPPORTED,
                   "type %d (%d joints, %d segments) does not fit in shared memory with one character", t, T.n,
@@ -692,7 +767,7 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
       continue;
     }
     P->C_adj[t] = ca;
-    smem_a = std::max(smem_a, adjoint_smem_bytes(T.n, T.seg.nseg, ca));
+    smem_a = std::max(smem_a, adjoint_smem_bytes(T.adj->n, T.adj->seg.nseg, ca));
   }
   auto is = make_items(P, P->C_scan), ia = make_items(P, P->C_adj);
   P->n_items_scan = (int)is.size();
@@ -753,7 +828,10 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   const int grid = ctx->sm_count * ctx->ctas_per_sm;
   P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16),
                  ctx->ctas_per_sm >= 3 ? 3 : 2};
-  P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
+  if (ctx->adj_ctas > 0)
+    P->cfg_adj = {kAdjSmallThreads, std::max(1, P->n_items_adj), std::max<size_t>(smem_a, 16)};
+  else
+    P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
   P->smem_frame = std::max<size_t>(smem_s, 16);
   P->version = ctx->version;
   return ANIM_OK;
@@ -1169,7 +1247,7 @@ static int run_adjoint(anim_ctx *ctx, const anim_plan *plan, int mode, const flo
   cudaStream_t st = (cudaStream_t)stream;
   AdjointArgs a{};
   a.done = plan->d_queue + 1;
-  a.types = ctx->d_types;
+  a.types = ctx->d_adj_types;
   a.items = plan->d_items_adj;
   a.n_items = plan->n_items_adj;
   a.item_chars = plan->d_type_chars;
@@ -1223,19 +1301,10 @@ int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_
       if (j < 0 || j >= T.n) return fail(ctx, ANIM_EINVAL, "effector %d of type %d out of range", j, t);
       for (int a = j; a >= 0 && !act[a]; a = T.parent[a]) act[a] = 1;
     }
-    auto V = std::make_unique<TypeHost>();
-    std::vector<int> vid(T.n, -1);
-    for (int j = 0; j < T.n; ++j)
-      if (act[j]) {
-        vid[j] = (int)V->gather.size();
-        V->gather.push_back(j);
-      }
-    V->n = (int)V->gather.size();
-    for (int j : V->gather) V->parent.push_back(T.parent[j] < 0 ? -1 : vid[T.parent[j]]);
-    V->depth = depths_of(V->parent);
-    V->max_depth = *std::max_element(V->depth.begin(), V->depth.end());
-    V->seg_len = default_seg_len(V->n);
-    CK(V->build_tables());
+    std::vector<int> vid;
+    cudaError_t ev = cudaSuccess;
+    auto V = make_view(T, act, &vid, &ev);
+    CK(ev);
     for (int e = 0; e < n_eff; ++e) eff_slot[(size_t)t * n_eff + e] = vid[effectors[(size_t)t * n_eff + e]];
     vdev[t] = V->dev;
     const int C = choose_C(ctx, *V, true);
@@ -1251,7 +1320,10 @@ int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_
   CK(upload_vec(&K->d_items, items));
   CK(cudaMalloc(&K->d_counters, 4 * sizeof(int)));
   CK(cudaMemset(K->d_counters, 0, 4 * sizeof(int)));
-  K->cfg = {kAdjThreads, std::max(1, std::min(ctx->sm_count * ctx->ctas_per_sm, K->n_items)), smem};
+  if (ctx->adj_ctas > 0)
+    K->cfg = {kAdjSmallThreads, std::max(1, K->n_items), smem};
+  else
+    K->cfg = {kAdjThreads, std::max(1, std::min(ctx->sm_count * ctx->ctas_per_sm, K->n_items)), smem};
   ctx->iks.insert(K.get());
   *out = K.release();
   return ANIM_OK;
@@ -1338,10 +1410,12 @@ static uint64_t mix_hash(const anim_ctx *ctx, const anim_plan *P, int which) {
   return h;
 }
 
-static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps, int jpi, int walk) {
+static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps, int jpi, int walk,
+                        int adj_ctas) {
   ctx->ctas_per_sm = cps;
   ctx->joints_per_item = jpi;
   ctx->use_walk = walk != 0;
+  ctx->adj_ctas = adj_ctas;
   for (int t : P->used) {
     TypeHost &T = *ctx->types[t];
     if (T.seg_len != seg_len) {
@@ -1370,7 +1444,7 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   auto hit = ctx->tune_cache.find(key);
   if (hit != ctx->tune_cache.end())
     return apply_choice(ctx, plan, hit->second.seg_len, hit->second.ctas_per_sm, hit->second.joints_per_item,
-                        hit->second.walk);
+                        hit->second.walk, hit->second.adj_ctas);
 
   // scratch inputs (tuning may allocate; evaluation calls never do)
   const int64_t N = plan->n_chars, J = plan->total;
@@ -1417,17 +1491,25 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
     if (which == 1) return anim_forward_local(ctx, plan, d_q, d_t, d_out, nullptr, nullptr);
     return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, nullptr);
   };
-  anim_ctx::TuneChoice best{0, 0, 0, 0, 1e30f};
-  const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {1024, 2048, 4096};
-  // the chain-walk kernel serves the frame only: other searches keep the
-  // context's setting
+  anim_ctx::TuneChoice best{0, 0, 0, 0, 0, 1e30f};
+  const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {256, 512, 1024, 2048, 4096};
+  const int adjs[] = {0, 4, 6, 8};
+  // the chain-walk kernel serves the frame only, the adjoint kernel choice
+  // the adjoint only: other searches keep the context's settings
   const int walk_lo = which == 0 ? 0 : ctx->use_walk, walk_hi = which == 0 ? 1 : ctx->use_walk;
+  const int adj_keep = ctx->adj_ctas;
   for (int walk = walk_lo; walk <= walk_hi; ++walk)
-    for (int seg : segs)
-      for (int cps : cpss)
-        for (int jpi : jpis) {
-          if (cps == 3 && which == 2) continue;  // the adjoint kernel is built for up to 2 CTAs/SM
-          if (apply_choice(ctx, plan, seg, cps, jpi, walk) != ANIM_OK) continue;  // e.g. does not fit
+    for (int adj : adjs)
+      for (int seg : segs)
+        for (int cps : cpss)
+          for (int jpi : jpis) {
+          if (which != 2 && adj != adjs[0]) continue;
+          const int adj_c = which == 2 ? adj : adj_keep;
+          if (which != 2 && jpi < 1024) continue;        // small items only pay off in the one-item adjoint
+          if (which == 2 && adj_c == 0 && jpi < 1024) continue;
+          if (which == 2 && adj_c > 0 && cps != 2) continue;  // CTAs per SM of the persistent kernels: unused
+          if (cps == 3 && which == 2) continue;  // the persistent adjoint kernel is built for up to 2 CTAs/SM
+          if (apply_choice(ctx, plan, seg, cps, jpi, walk, adj_c) != ANIM_OK) continue;  // e.g. does not fit
           bool ok = true;
           for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
           cudaEventRecord(e0, nullptr);
@@ -1437,7 +1519,7 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
           float ms = 0.f;
           cudaEventElapsedTime(&ms, e0, e1);
           ms /= 5.f;
-          if (ms < best.ms) best = {seg, cps, jpi, walk, ms};
+          if (ms < best.ms) best = {seg, cps, jpi, walk, adj_c, ms};
         }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1445,35 +1527,37 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   if (best.seg_len == 0) return fail(ctx, ANIM_ECUDA, "no candidate schedule ran");
   ctx->tune_cache[key] = best;
   ctx->err.clear();
-  return apply_choice(ctx, plan, best.seg_len, best.ctas_per_sm, best.joints_per_item, best.walk);
+  return apply_choice(ctx, plan, best.seg_len, best.ctas_per_sm, best.joints_per_item, best.walk,
+                      best.adj_ctas);
 }
 
-int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out4) {
+int anim_get_schedule(anim_ctx *ctx, const anim_plan *plan, int32_t *out5) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
-  if (!out4) return fail(ctx, ANIM_EINVAL, "out4 is NULL");
+  if (!out5) return fail(ctx, ANIM_EINVAL, "out5 is NULL");
   const TypeHost *T = plan->used.empty() ? nullptr : ctx->types[plan->used[0]].get();
-  out4[0] = T ? T->seg_len : 16;
-  out4[1] = ctx->ctas_per_sm;
-  out4[2] = ctx->joints_per_item;
-  out4[3] = ctx->use_walk;
+  out5[0] = T ? T->seg_len : 16;
+  out5[1] = ctx->ctas_per_sm;
+  out5[2] = ctx->joints_per_item;
+  out5[3] = ctx->use_walk;
+  out5[4] = ctx->adj_ctas;
   return ANIM_OK;
 }
 
-int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in4) {
+int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in5) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
-  if (!in4 || in4[0] < 1 || in4[0] > ANIM_MAX_JOINTS || in4[1] < 1 || in4[1] > 3 || in4[2] < 1 ||
-      (in4[3] != 0 && in4[3] != 1))
+  if (!in5 || in5[0] < 1 || in5[0] > ANIM_MAX_JOINTS || in5[1] < 1 || in5[1] > 3 || in5[2] < 1 ||
+      (in5[3] != 0 && in5[3] != 1) || in5[4] < 0 || in5[4] > 8)
     return fail(ctx, ANIM_EINVAL, "schedule out of range");
   CK(cudaSetDevice(ctx->device));
-  int32_t prev[4];
+  int32_t prev[5];
   anim_get_schedule(ctx, plan, prev);
-  rc = apply_choice(ctx, plan, in4[0], in4[1], in4[2], in4[3]);
+  rc = apply_choice(ctx, plan, in5[0], in5[1], in5[2], in5[3], in5[4]);
   if (rc != ANIM_OK) {
     // keep the failure's message and put the previous schedule back
     const std::string msg = ctx->err;
-    apply_choice(ctx, plan, prev[0], prev[1], prev[2], prev[3]);
+    apply_choice(ctx, plan, prev[0], prev[1], prev[2], prev[3], prev[4]);
     ctx->err = msg;
   }
   return rc;

@@ -18,8 +18,11 @@
 
 namespace anim {
 
+// Item layout of the adjoint: the scan's layout, then F and T [C][n+1]
+// float4 each (+1 spare), then the view's subtree ends, parents and gather
+// map as int16 [n] each.
 size_t adjoint_smem_bytes(int n, int nseg, int C) {
-  return scan_item_bytes(n, nseg, C) + 16ull * 2ull * ((size_t)C * (n + 1) + 1);
+  return scan_item_bytes(n, nseg, C) + 16ull * 2ull * ((size_t)C * (n + 1) + 1) + (6ull * n + 15) / 16 * 16;
 }
 
 __device__ __forceinline__ float3 cross3(const float3 a, const float3 b) {
@@ -40,11 +43,12 @@ __device__ __forceinline__ void add4(float4 &a, const float4 b) {
   a.w += b.w;
 }
 
-// Exclusive prefix of the (F, T) float4 pairs over slots [0, n] of one
-// character (entry n receives the total).  All compute threads take part.
+// Exclusive prefix of the (F, T) float4 pairs over slots [0, n] (entry n
+// receives the total).  All NT pass threads take part.
+template <int NT>
 __device__ void prefix_pairs(float4 *F, float4 *T, int n, float4 *wsF, float4 *wsT) {
-  const int tid = threadIdx.x, nth = kComputeThreads;
-  const int lane = tid & 31, wid = tid >> 5, nw = kComputeWarps;
+  const int tid = threadIdx.x, nth = NT;
+  const int lane = tid & 31, wid = tid >> 5, nw = NT / 32;
   const int per = (n + nth - 1) / nth;
   const int i0 = min(n, tid * per), i1 = min(n, i0 + per);
   float4 sf = make_float4(0.f, 0.f, 0.f, 0.f), st = sf;
@@ -64,7 +68,7 @@ __device__ void prefix_pairs(float4 *F, float4 *T, int n, float4 *wsF, float4 *w
     wsF[wid] = xf;
     wsT[wid] = xt;
   }
-  compute_sync();
+  pass_sync<NT>();
   if (wid == 0) {
     float4 wf = lane < nw ? wsF[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 wt = lane < nw ? wsT[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -80,7 +84,7 @@ __device__ void prefix_pairs(float4 *F, float4 *T, int n, float4 *wsF, float4 *w
       wsT[lane] = wt;
     }
   }
-  compute_sync();
+  pass_sync<NT>();
   float4 pf = make_float4(xf.x - sf.x, xf.y - sf.y, xf.z - sf.z, xf.w - sf.w);
   float4 pt = make_float4(xt.x - st.x, xt.y - st.y, xt.z - st.z, 0.f);
   if (wid > 0) {
@@ -98,12 +102,173 @@ __device__ void prefix_pairs(float4 *F, float4 *T, int n, float4 *wsF, float4 *w
     F[n] = pf;
     T[n] = pt;
   }
-  compute_sync();
+  pass_sync<NT>();
 }
 
-// MODE 0: grad_pos given; MODE 1: loss sum |p - target|^2; MODE 2: IK step
-// (effector loss, adjoint, Adam update of q, m, v).  Same CTA layout as the
-// frame kernel: 8 compute warps and one producer warp staging the next item.
+// One work item: MODE 0 grad_pos given; MODE 1 loss sum |p - target|^2;
+// MODE 2 IK step (effector loss, adjoint, Adam update of q, m, v).  NT
+// threads run the passes (tid < NT); `step` is the 1-based Adam step.
+template <int MODE, int NT>
+__device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf &b, float4 *sm, float4 *wsF,
+                                             float4 *wsT, int tid, int step) {
+  const int C = b.C, n = b.T.n, nseg = b.T.nseg;
+  const int cs4 = 3 * n + 1;
+  const ItemLayout Lt = item_layout(sm, C, n, nseg);
+  float4 *P = Lt.P;
+  float4 *PF = Lt.end;                // [C][n+1]
+  float4 *PT = PF + C * (n + 1) + 1;  // [C][n+1] (+1: the scan's total)
+  // The adjoint runs on views numbered in depth-first pre-order, so a
+  // joint's slot is its index and its subtree is [j, sub_end[j]).
+  int16_t *sub16 = reinterpret_cast<int16_t *>(PT + C * (n + 1) + 1);
+  int16_t *par16 = sub16 + n, *gat16 = par16 + n;
+  const int32_t *gat = b.T.gather;
+  const bool gath = gat != nullptr;
+  const int CN = C * n;
+  for (int j = tid; j < n; j += NT) {
+    sub16[j] = (int16_t)__ldg(b.T.sub_end + j);
+    par16[j] = (int16_t)__ldg(b.T.parent + j);
+    gat16[j] = (int16_t)(gath ? __ldg(gat + j) : j);
+  }
+
+  // ---- pass 1a: local matrices from (q, t); the joint's loss input
+  // (dLoss/dp or target) is fetched alongside into its depth-first slot
+  stage_tables<NT>(b, Lt, tid);
+  {
+    const float4 *q4 = reinterpret_cast<const float4 *>(a.q);
+#pragma unroll 2
+    for (int idx = tid; idx < CN; idx += NT) {
+      const int c = (int)b.divN.div(idx), j = idx - c * n;
+      const long long row = b.off[c] + (gath ? __ldg(gat + j) : j);
+      const float4 q = normalize4(__ldg(q4 + row));
+      const float *tp = a.t + 3 * row;
+      sts_aff(P + c * cs4 + 3 * j, aff_from_qt(q, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2)));
+      if (MODE != 2) {
+        const float *src = (MODE == 0 ? a.grad_pos : a.target) + 3 * row;
+        PF[c * (n + 1) + j] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), 0.f);
+      }
+    }
+  }
+  pass_sync<NT>();
+  pass1b<NT>(b, Lt, P, cs4, tid);
+  pass_sync<NT>();
+  const float4 *Y = pass2<NT>(b, Lt, P, cs4, tid);
+
+  // ---- model poses in place and the per-slot terms (g, p x g) in the same
+  // pass; loss terms in F.w; slot n of each character is zero
+  for (int idx = tid; idx < CN; idx += NT) {
+    const int c = (int)b.divN.div(idx), j = idx - c * n;
+    const uint32_t info = Lt.jinfo[j];
+    float4 *slot = P + c * cs4 + 3 * j;
+    float3 p;
+    if (info & kJ16Link) {
+      const Aff m = aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & kJ16Seg))), lds_aff(slot));
+      sts_aff(slot, m);
+      p = make_float3(m.r0.w, m.r1.w, m.r2.w);
+    } else {
+      p = make_float3(slot[0].w, slot[1].w, slot[2].w);
+    }
+    const int i = j;
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    float lterm = 0.f;
+    if (MODE == 0) {
+      const float4 v = PF[c * (n + 1) + i];
+      g = make_float3(v.x, v.y, v.z);
+    } else if (MODE == 1) {
+      const float4 v = PF[c * (n + 1) + i];
+      const float dx = p.x - v.x, dy = p.y - v.y, dz = p.z - v.z;
+      g = make_float3(2.f * dx, 2.f * dy, 2.f * dz);
+      lterm = dx * dx + dy * dy + dz * dz;
+    }
+    const float3 pg = cross3(p, g);
+    PF[c * (n + 1) + i] = make_float4(g.x, g.y, g.z, lterm);
+    PT[c * (n + 1) + i] = make_float4(pg.x, pg.y, pg.z, 0.f);
+    if (j == 0) {
+      PF[c * (n + 1) + n] = make_float4(0.f, 0.f, 0.f, 0.f);
+      PT[c * (n + 1) + n] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  pass_sync<NT>();
+  if (MODE == 2) {
+    const int CE = C * a.n_eff;
+    for (int idx = tid; idx < CE; idx += NT) {
+      const int c = idx / a.n_eff, e = idx - c * a.n_eff;
+      const int j = __ldg(a.eff_slot + b.type * a.n_eff + e);
+      const int i = j;
+      const float3 p = make_float3(P[c * cs4 + 3 * j].w, P[c * cs4 + 3 * j + 1].w, P[c * cs4 + 3 * j + 2].w);
+      const float *tg = a.target + ((size_t)b.cid[c] * a.n_eff + e) * 3;
+      const float dx = p.x - __ldg(tg), dy = p.y - __ldg(tg + 1), dz = p.z - __ldg(tg + 2);
+      const float3 g = make_float3(2.f * dx, 2.f * dy, 2.f * dz);
+      const float3 pg = cross3(p, g);
+      PF[c * (n + 1) + i] = make_float4(g.x, g.y, g.z, dx * dx + dy * dy + dz * dz);
+      PT[c * (n + 1) + i] = make_float4(pg.x, pg.y, pg.z, 0.f);
+    }
+    pass_sync<NT>();
+  }
+  // one exclusive prefix over all characters' slots; subtree sums are
+  // differences inside a character
+  prefix_pairs<NT>(PF, PT, C * (n + 1), wsF, wsT);
+  if (MODE != 0 && a.loss != nullptr && tid < C) a.loss[b.cid[tid]] = PF[tid * (n + 1) + n].w - PF[tid * (n + 1)].w;
+
+  // ---- per-joint gradients (and the Adam update in IK mode)
+  float bc2s = 1.f, step_size = 0.f;
+  if (MODE == 2) {
+    bc2s = sqrtf(1.f - powf(a.beta2, (float)step));
+    step_size = a.lr / (1.f - powf(a.beta1, (float)step));
+  }
+  for (int idx = tid; idx < CN; idx += NT) {
+    const int c = (int)b.divN.div(idx), j = idx - c * n;
+    const int i = j, e = sub16[j];
+    const float4 f0 = PF[c * (n + 1) + i], f1 = PF[c * (n + 1) + e];
+    const float4 t0 = PT[c * (n + 1) + i], t1 = PT[c * (n + 1) + e];
+    const float3 F = make_float3(f1.x - f0.x, f1.y - f0.y, f1.z - f0.z);
+    const float3 Tq = make_float3(t1.x - t0.x, t1.y - t0.y, t1.z - t0.z);
+    const float3 p = make_float3(P[c * cs4 + 3 * j].w, P[c * cs4 + 3 * j + 1].w, P[c * cs4 + 3 * j + 2].w);
+    const float3 pf = cross3(p, F);
+    const float3 tw = make_float3(Tq.x - pf.x, Tq.y - pf.y, Tq.z - pf.z);
+    const int par = par16[j];
+    float3 tau = tw, dt = F;
+    if (par >= 0) {
+      const float4 r0 = P[c * cs4 + 3 * par], r1 = P[c * cs4 + 3 * par + 1], r2 = P[c * cs4 + 3 * par + 2];
+      tau = make_float3(r0.x * tw.x + r1.x * tw.y + r2.x * tw.z, r0.y * tw.x + r1.y * tw.y + r2.y * tw.z,
+                        r0.z * tw.x + r1.z * tw.y + r2.z * tw.z);
+      dt = make_float3(r0.x * F.x + r1.x * F.y + r2.x * F.z, r0.y * F.x + r1.y * F.y + r2.y * F.z,
+                       r0.z * F.x + r1.z * F.y + r2.z * F.z);
+    }
+    const long long row = b.off[c] + gat16[j];
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(a.q) + row);
+    const float inv = rsqrtf(dot4(q, q));
+    const float4 u = make_float4(q.x * inv, q.y * inv, q.z * inv, q.w * inv);
+    const float4 r = qmul(make_float4(tau.x, tau.y, tau.z, 0.f), u);
+    const float k2 = 2.f * inv;
+    const float4 dq = make_float4(k2 * r.x, k2 * r.y, k2 * r.z, k2 * r.w);
+    if (MODE != 2) {
+      reinterpret_cast<float4 *>(a.grad_q)[row] = dq;
+      a.grad_t[3 * row] = dt.x;
+      a.grad_t[3 * row + 1] = dt.y;
+      a.grad_t[3 * row + 2] = dt.z;
+    } else {
+      float4 m = reinterpret_cast<float4 *>(a.m)[row];
+      float4 v = reinterpret_cast<float4 *>(a.v)[row];
+      float4 qn = q;
+      const float b1 = a.beta1, b2 = a.beta2;
+      const float gq[4] = {dq.x, dq.y, dq.z, dq.w};
+      float *mm = &m.x, *vv = &v.x, *qq = &qn.x;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        mm[k] = b1 * mm[k] + (1.f - b1) * gq[k];
+        vv[k] = b2 * vv[k] + (1.f - b2) * gq[k] * gq[k];
+        const float denom = sqrtf(vv[k]) / bc2s + a.eps;
+        qq[k] = qq[k] - step_size * (mm[k] / denom);
+      }
+      reinterpret_cast<float4 *>(a.m)[row] = m;
+      reinterpret_cast<float4 *>(a.v)[row] = v;
+      reinterpret_cast<float4 *>(a.q_mut)[row] = qn;
+    }
+  }
+}
+
+// Persistent kernel: 8 compute warps and one producer warp staging the next
+// item, items from the queue (the frame kernel's CTA layout).
 template <int MODE>
 __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a) {
   extern __shared__ __align__(128) float4 sm[];
@@ -122,140 +287,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
   for (;;) {
     const ItemBuf &b = bufs[cur];
     if (b.item < 0) break;
-    const int C = b.C, n = b.T.n, nseg = b.T.nseg;
-    const int cs4 = 3 * n + 1;
-    const ItemLayout Lt = item_layout(sm, C, n, nseg);
-    float4 *P = Lt.P;
-    float4 *PF = Lt.end;                // [C][n+1]
-    float4 *PT = PF + C * (n + 1) + 1;  // [C][n+1] (+1: the scan's total)
-    const int32_t *gat = b.T.gather;
-    const bool gath = gat != nullptr;
-    const int CN = C * n;
-
-    // ---- forward recompute: the segmented scan from (q, t), model poses in place
-    stage_tables(b, Lt, tid);
-    pass1a_qt(b, P, cs4, a.q, a.t, tid);
-    compute_sync();
-    pass1b(b, Lt, P, cs4, tid);
-    compute_sync();
-    {
-      const float4 *Y = pass2(b, Lt, P, cs4, tid);
-      for (int idx = tid; idx < CN; idx += kComputeThreads) {
-        const int c = (int)b.divN.div(idx), j = idx - c * n;
-        const uint32_t info = Lt.jinfo[j];
-        if (info & kJ16Link) {
-          float4 *slot = P + c * cs4 + 3 * j;
-          sts_aff(slot, aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & kJ16Seg))), lds_aff(slot)));
-        }
-      }
-      compute_sync();
-    }
-
-    // ---- per-slot (g, p x g) in depth-first order; loss terms in F.w
-    for (int idx = tid; idx < CN; idx += kComputeThreads) {
-      const int c = (int)b.divN.div(idx), i = idx - c * n;
-      const int j = __ldg(b.T.dfs + i);
-      float3 g = make_float3(0.f, 0.f, 0.f);
-      float lterm = 0.f;
-      const float3 p = make_float3(P[c * cs4 + 3 * j].w, P[c * cs4 + 3 * j + 1].w, P[c * cs4 + 3 * j + 2].w);
-      if (MODE == 0) {
-        const long long row = b.off[c] + j;
-        g = make_float3(__ldg(a.grad_pos + 3 * row), __ldg(a.grad_pos + 3 * row + 1), __ldg(a.grad_pos + 3 * row + 2));
-      } else if (MODE == 1) {
-        const long long row = b.off[c] + j;
-        const float dx = p.x - __ldg(a.target + 3 * row), dy = p.y - __ldg(a.target + 3 * row + 1),
-                    dz = p.z - __ldg(a.target + 3 * row + 2);
-        g = make_float3(2.f * dx, 2.f * dy, 2.f * dz);
-        lterm = dx * dx + dy * dy + dz * dz;
-      }
-      const float3 pg = cross3(p, g);
-      PF[c * (n + 1) + i] = make_float4(g.x, g.y, g.z, lterm);
-      PT[c * (n + 1) + i] = make_float4(pg.x, pg.y, pg.z, 0.f);
-    }
-    compute_sync();
-    if (MODE == 2) {
-      const int CE = C * a.n_eff;
-      for (int idx = tid; idx < CE; idx += kComputeThreads) {
-        const int c = idx / a.n_eff, e = idx - c * a.n_eff;
-        const int j = __ldg(a.eff_slot + b.type * a.n_eff + e);
-        const int i = __ldg(b.T.dfs_slot + j);
-        const float3 p = make_float3(P[c * cs4 + 3 * j].w, P[c * cs4 + 3 * j + 1].w, P[c * cs4 + 3 * j + 2].w);
-        const float *tg = a.target + ((size_t)b.cid[c] * a.n_eff + e) * 3;
-        const float dx = p.x - __ldg(tg), dy = p.y - __ldg(tg + 1), dz = p.z - __ldg(tg + 2);
-        const float3 g = make_float3(2.f * dx, 2.f * dy, 2.f * dz);
-        const float3 pg = cross3(p, g);
-        PF[c * (n + 1) + i] = make_float4(g.x, g.y, g.z, dx * dx + dy * dy + dz * dz);
-        PT[c * (n + 1) + i] = make_float4(pg.x, pg.y, pg.z, 0.f);
-      }
-      compute_sync();
-    }
-    // one exclusive prefix over all characters' slots (slot n of each
-    // character is zero); subtree sums are differences inside a character
-    for (int c = tid; c < C; c += kComputeThreads) {
-      PF[c * (n + 1) + n] = make_float4(0.f, 0.f, 0.f, 0.f);
-      PT[c * (n + 1) + n] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    compute_sync();
-    prefix_pairs(PF, PT, C * (n + 1), wsF, wsT);
-    if (MODE != 0 && a.loss != nullptr && tid < C)
-      a.loss[b.cid[tid]] = PF[tid * (n + 1) + n].w - PF[tid * (n + 1)].w;
-
-    // ---- per-joint gradients (and the Adam update in IK mode)
-    float bc2s = 1.f, step_size = 0.f;
-    if (MODE == 2) {
-      bc2s = sqrtf(1.f - powf(a.beta2, (float)step));
-      step_size = a.lr / (1.f - powf(a.beta1, (float)step));
-    }
-    for (int idx = tid; idx < CN; idx += kComputeThreads) {
-      const int c = (int)b.divN.div(idx), j = idx - c * n;
-      const int i = __ldg(b.T.dfs_slot + j), e = __ldg(b.T.sub_end + i);
-      const float4 f0 = PF[c * (n + 1) + i], f1 = PF[c * (n + 1) + e];
-      const float4 t0 = PT[c * (n + 1) + i], t1 = PT[c * (n + 1) + e];
-      const float3 F = make_float3(f1.x - f0.x, f1.y - f0.y, f1.z - f0.z);
-      const float3 Tq = make_float3(t1.x - t0.x, t1.y - t0.y, t1.z - t0.z);
-      const float3 p = make_float3(P[c * cs4 + 3 * j].w, P[c * cs4 + 3 * j + 1].w, P[c * cs4 + 3 * j + 2].w);
-      const float3 pf = cross3(p, F);
-      const float3 tw = make_float3(Tq.x - pf.x, Tq.y - pf.y, Tq.z - pf.z);
-      const int par = __ldg(b.T.parent + j);
-      float3 tau = tw, dt = F;
-      if (par >= 0) {
-        const float4 r0 = P[c * cs4 + 3 * par], r1 = P[c * cs4 + 3 * par + 1], r2 = P[c * cs4 + 3 * par + 2];
-        tau = make_float3(r0.x * tw.x + r1.x * tw.y + r2.x * tw.z, r0.y * tw.x + r1.y * tw.y + r2.y * tw.z,
-                          r0.z * tw.x + r1.z * tw.y + r2.z * tw.z);
-        dt = make_float3(r0.x * F.x + r1.x * F.y + r2.x * F.z, r0.y * F.x + r1.y * F.y + r2.y * F.z,
-                         r0.z * F.x + r1.z * F.y + r2.z * F.z);
-      }
-      const long long row = b.off[c] + (gath ? __ldg(gat + j) : j);
-      const float4 q = __ldg(reinterpret_cast<const float4 *>(a.q) + row);
-      const float inv = rsqrtf(dot4(q, q));
-      const float4 u = make_float4(q.x * inv, q.y * inv, q.z * inv, q.w * inv);
-      const float4 r = qmul(make_float4(tau.x, tau.y, tau.z, 0.f), u);
-      const float k2 = 2.f * inv;
-      const float4 dq = make_float4(k2 * r.x, k2 * r.y, k2 * r.z, k2 * r.w);
-      if (MODE != 2) {
-        reinterpret_cast<float4 *>(a.grad_q)[row] = dq;
-        a.grad_t[3 * row] = dt.x;
-        a.grad_t[3 * row + 1] = dt.y;
-        a.grad_t[3 * row + 2] = dt.z;
-      } else {
-        float4 m = reinterpret_cast<float4 *>(a.m)[row];
-        float4 v = reinterpret_cast<float4 *>(a.v)[row];
-        float4 qn = q;
-        const float b1 = a.beta1, b2 = a.beta2;
-        const float gq[4] = {dq.x, dq.y, dq.z, dq.w};
-        float *mm = &m.x, *vv = &v.x, *qq = &qn.x;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          mm[k] = b1 * mm[k] + (1.f - b1) * gq[k];
-          vv[k] = b2 * vv[k] + (1.f - b2) * gq[k] * gq[k];
-          const float denom = sqrtf(vv[k]) / bc2s + a.eps;
-          qq[k] = qq[k] - step_size * (mm[k] / denom);
-        }
-        reinterpret_cast<float4 *>(a.m)[row] = m;
-        reinterpret_cast<float4 *>(a.v)[row] = v;
-        reinterpret_cast<float4 *>(a.q_mut)[row] = qn;
-      }
-    }
+    adjoint_item<MODE, kComputeThreads>(a, b, sm, wsF, wsT, tid, step);
     compute_sync();
     cur ^= 1;
     handoff_sync();
@@ -272,8 +304,48 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
   }
 }
 
+static_assert(sizeof(ItemBuf) + 2 * (kAdjSmallThreads / 32) * 16 <= kAdjSmallStatic, "one-item kernel statics");
+
+// One-item kernel: CTA b processes item b with kAdjSmallThreads threads and
+// no producer warp, small enough that several CTAs share an SM; the
+// hardware schedules the items in waves.  Suits many small items, where the
+// persistent kernel would run each CTA's items one after another.
+template <int MODE>
+__global__ void __launch_bounds__(kAdjSmallThreads, 4) k_adjoint_small(const AdjointArgs a) {
+  extern __shared__ __align__(128) float4 sm[];
+  __shared__ ItemBuf b;
+  __shared__ float4 wsF[kAdjSmallThreads / 32], wsT[kAdjSmallThreads / 32];
+  const int tid = threadIdx.x;
+  const int step = (MODE == 2) ? *a.step + 1 : 0;
+  if (tid < 32) {
+    const WorkItem wi = a.items[blockIdx.x];
+    stage_item<1>(b, (int)blockIdx.x, wi, a.types, a.item_chars, a.row_off, nullptr, nullptr, a.status);
+  }
+  __syncthreads();
+  adjoint_item<MODE, kAdjSmallThreads>(a, b, sm, wsF, wsT, tid, step);
+  if (MODE == 2 && tid == 0) {  // the last CTA advances the IK step
+    __threadfence();
+    if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
+      *a.step = *a.step + 1;
+      *a.done = 0;
+      __threadfence();
+    }
+  }
+}
+
 template <int MODE>
 static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
+  if (cfg.threads == kAdjSmallThreads) {
+    static size_t set_small = 0;
+    if (cfg.smem > set_small) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k_adjoint_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+      if (e != cudaSuccess) return e;
+      set_small = cfg.smem;
+    }
+    k_adjoint_small<MODE><<<a.n_items, kAdjSmallThreads, cfg.smem, st>>>(a);
+    return cudaGetLastError();
+  }
   static size_t set_smem = 0;
   if (cfg.smem > set_smem) {
     cudaError_t e = cudaFuncSetAttribute(k_adjoint<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);

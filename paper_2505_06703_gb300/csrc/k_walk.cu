@@ -33,10 +33,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-struct Rec {
-  float4 q0, qp, t0, dt;
-};
-
 __device__ __forceinline__ Rec ld_rec(const float4 *p, int P) {
   Rec r;
   r.q0 = __ldg(p);
@@ -44,29 +40,6 @@ __device__ __forceinline__ Rec ld_rec(const float4 *p, int P) {
   r.t0 = __ldg(p + 2 * P);
   r.dt = __ldg(p + 3 * P);
   return r;
-}
-
-// Key slerp from a precomputed record: cos(a theta) q0 + sin(a theta) q_perp,
-// which equals the normalized slerp between the two unit keys; lerp for t.
-__device__ __forceinline__ float4 rec_q(const Rec &r, float al) {
-  float s, c;
-  __sincosf(al * r.t0.w, &s, &c);
-  return make_float4(fmaf(c, r.q0.x, s * r.qp.x), fmaf(c, r.q0.y, s * r.qp.y), fmaf(c, r.q0.z, s * r.qp.z),
-                     fmaf(c, r.q0.w, s * r.qp.w));
-}
-
-__device__ __forceinline__ Aff walk_sample(const Rec &a, const Rec &b, float al, float w, bool two) {
-  float4 q = rec_q(a, al);
-  float tx = fmaf(al, a.dt.x, a.t0.x), ty = fmaf(al, a.dt.y, a.t0.y), tz = fmaf(al, a.dt.z, a.t0.z);
-  if (two) {
-    const float4 qb = rec_q(b, al);
-    const float bx = fmaf(al, b.dt.x, b.t0.x), by = fmaf(al, b.dt.y, b.t0.y), bz = fmaf(al, b.dt.z, b.t0.z);
-    q = slerp_unit(q, qb, w);
-    tx = fmaf(w, bx - tx, tx);
-    ty = fmaf(w, by - ty, ty);
-    tz = fmaf(w, bz - tz, tz);
-  }
-  return aff_from_qt(q, tx, ty, tz);
 }
 
 __device__ __forceinline__ Aff ld_bind(const float4 *p, int P) {
@@ -120,7 +93,7 @@ __device__ __forceinline__ Aff walk_steps(const uint32_t *tab, const float4 *ka,
       }
     }
     if (act && !(e & 0x80000000u)) {
-      const Aff L = walk_sample(ra, rb, al, w, two);
+      const Aff L = sample_rec(ra, rb, al, w, two);
       Aff Mp = M;
       if (KIND == 0 && (e & kWStart)) {
         const uint32_t ls = (e >> kWLoadShift) & 0xFFu;
@@ -219,29 +192,9 @@ __global__ void k_build_walk_keys(const TypeDev T, const float4 *keys, float4 *o
       for (int f = 0; f < 4; ++f) o[f * P] = make_float4(0.f, 0.f, 0.f, 0.f);
       continue;
     }
-    const int j = (int)(e & kWJoint);
-    const int k1 = (k + 1 == nk) ? 0 : k + 1;
-    const float4 *ra = keys + (((size_t)clip * nk + k) * n + j) * 2;
-    const float4 *rb = keys + (((size_t)clip * nk + k1) * n + j) * 2;
-    const float4 qa = normalize4(ra[0]);
-    float4 qb = normalize4(rb[0]);
-    const float d = dot4(qa, qb);
-    if (d < 0.f) qb = make_float4(-qb.x, -qb.y, -qb.z, -qb.w);
-    const float ad = fabsf(d);
-    float dm = 0.f, dp = 0.f, t;
-    t = qa.x - qb.x; dm += t * t; t = qa.x + qb.x; dp += t * t;
-    t = qa.y - qb.y; dm += t * t; t = qa.y + qb.y; dp += t * t;
-    t = qa.z - qb.z; dm += t * t; t = qa.z + qb.z; dp += t * t;
-    t = qa.w - qb.w; dm += t * t; t = qa.w + qb.w; dp += t * t;
-    const float theta = 2.f * atan2f(sqrtf(dm), sqrtf(dp));
-    float4 v = make_float4(qb.x - ad * qa.x, qb.y - ad * qa.y, qb.z - ad * qa.z, qb.w - ad * qa.w);
-    const float nv = sqrtf(dot4(v, v));
-    v = nv > 0.f ? make_float4(v.x / nv, v.y / nv, v.z / nv, v.w / nv) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 ta = ra[1], tb = rb[1];
-    o[0] = qa;
-    o[P] = v;
-    o[2 * P] = make_float4(ta.x, ta.y, ta.z, theta);
-    o[3 * P] = make_float4(tb.x - ta.x, tb.y - ta.y, tb.z - ta.z, 0.f);
+    float4 rec[4];
+    make_rec(keys, clip, k, nk, n, (int)(e & kWJoint), rec);
+    for (int f = 0; f < 4; ++f) o[f * P] = rec[f];
   }
 }
 

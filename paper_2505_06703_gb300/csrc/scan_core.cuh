@@ -39,6 +39,16 @@ __device__ __forceinline__ void compute_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kComputeThreads) : "memory");
 }
 __device__ __forceinline__ void handoff_sync() { asm volatile("bar.sync 2, %0;" ::"n"(kCtaThreads) : "memory"); }
+// Barrier among the NT threads that run the passes: the persistent kernels'
+// compute warps (named barrier 1), or the whole CTA of a kernel whose
+// threads all compute.
+template <int NT>
+__device__ __forceinline__ void pass_sync() {
+  if constexpr (NT == kComputeThreads)
+    compute_sync();
+  else
+    __syncthreads();
+}
 
 // Everything one work item needs besides the big buffers (double-buffered).
 struct ItemBuf {
@@ -53,6 +63,11 @@ struct ItemBuf {
   float blend[kCMax];        // frame: clip blend weight
 };
 static_assert(2 * sizeof(ItemBuf) + 2048 <= kStaticSmemAllowance, "item buffers exceed the static allowance");
+
+template <int MODE>
+__device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &wi, const TypeDev *types,
+                                           const int32_t *item_chars, const int64_t *row_off, const float *time,
+                                           const float *blend_w, int *status);
 
 // Producer warp: grab the next item from the queue and stage its data.
 // MODE 0 (frame) also computes each character's key fraction.
@@ -74,6 +89,15 @@ __device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_it
     wi = items[it];
     if (wi.count > 0) break;
   }
+  stage_item<MODE>(b, it, wi, types, item_chars, row_off, time, blend_w, status);
+}
+
+// One warp stages work item `it` (descriptor wi) into b.
+template <int MODE>
+__device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &wi, const TypeDev *types,
+                                           const int32_t *item_chars, const int64_t *row_off, const float *time,
+                                           const float *blend_w, int *status) {
+  const int lane = threadIdx.x & 31;
   const int *src = reinterpret_cast<const int *>(types + wi.type);
   int *dst = reinterpret_cast<int *>(&b.T);
   for (int k = lane; k < (int)(sizeof(TypeDev) / 4); k += 32) dst[k] = src[k];
@@ -164,11 +188,12 @@ __device__ __forceinline__ ItemLayout item_layout(float4 *sm, int C, int n, int 
 }
 // Copy the type's segment tables into the item's shared memory (all compute
 // threads; issued at the start of pass 1a so the loads overlap its work).
+template <int NT = kComputeThreads>
 __device__ __forceinline__ void stage_tables(const ItemBuf &b, const ItemLayout &L, int tid) {
   const int n = b.T.n, nseg = b.T.nseg;
-  for (int k = tid; k <= nseg; k += kComputeThreads) L.seg_start[k] = __ldg(b.T.seg_start + k);
-  for (int k = tid; k < nseg; k += kComputeThreads) L.seg_link[k] = __ldg(b.T.seg_link + k);
-  for (int j = tid; j < n; j += kComputeThreads) {
+  for (int k = tid; k <= nseg; k += NT) L.seg_start[k] = __ldg(b.T.seg_start + k);
+  for (int k = tid; k < nseg; k += NT) L.seg_link[k] = __ldg(b.T.seg_link + k);
+  for (int j = tid; j < n; j += NT) {
     const uint32_t i = __ldg(b.T.jinfo + j);
     L.jinfo[j] = (uint16_t)((i & kJ16Seg) | ((i & kJStart) ? kJ16Start : 0u) | ((i & kJLink) ? kJ16Link : 0u));
   }
@@ -177,13 +202,14 @@ __device__ __forceinline__ void stage_tables(const ItemBuf &b, const ItemLayout 
 // Pass 1a from given local poses (q normalized here, t), optionally through a
 // gather map (IK views).  Character-major so consecutive lanes read
 // consecutive rows.
+template <int NT = kComputeThreads>
 __device__ __forceinline__ void pass1a_qt(const ItemBuf &b, float4 *P, int cs4, const float *q_all,
                                           const float *t_all, int tid) {
   const int n = b.T.n, CN = b.C * n;
   const int32_t *gat = b.T.gather;
   const float4 *q4 = reinterpret_cast<const float4 *>(q_all);
 #pragma unroll 2
-  for (int idx = tid; idx < CN; idx += kComputeThreads) {
+  for (int idx = tid; idx < CN; idx += NT) {
     const int c = (int)b.divN.div(idx), j = idx - c * n;
     const long long row = b.off[c] + (gat ? __ldg(gat + j) : j);
     const float4 q = normalize4(__ldg(q4 + row));
@@ -193,9 +219,10 @@ __device__ __forceinline__ void pass1a_qt(const ItemBuf &b, float4 *P, int cs4, 
 }
 
 // Pass 1b: running products along each segment, in place.
+template <int NT = kComputeThreads>
 __device__ __forceinline__ void pass1b(const ItemBuf &b, const ItemLayout &Lt, float4 *P, int cs4, int tid) {
   const int C = b.C, NS = b.T.nseg * C;
-  for (int idx = tid; idx < NS; idx += kComputeThreads) {
+  for (int idx = tid; idx < NS; idx += NT) {
     const int g = (int)b.divC.div(idx), c = idx - g * C;
     const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1];
     float4 *Pc = P + c * cs4;
@@ -214,23 +241,24 @@ __device__ __forceinline__ void pass1b(const ItemBuf &b, const ItemLayout &Lt, f
 // Pass 2 + its barriers.  Returns the buffer holding the final Y.  The
 // jumping pointers depend only on the skeleton, so one copy per item lives
 // in shared memory (ptr0/ptr1, double-buffered) next to the Y buffers.
+template <int NT = kComputeThreads>
 __device__ __forceinline__ float4 *pass2(const ItemBuf &b, const ItemLayout &Lt, float4 *P, int cs4, int tid) {
   const int nseg = b.T.nseg;
   const int CS = b.C * nseg;
   float4 *Y0 = Lt.Y0, *Y1 = Lt.Y1;
   int16_t *ptr0 = Lt.ptr0, *ptr1 = Lt.ptr1;
-  for (int idx = tid; idx < CS; idx += kComputeThreads) {
+  for (int idx = tid; idx < CS; idx += NT) {
     const int c = (int)b.divS.div(idx), g = idx - c * nseg;
     const int lk = Lt.seg_link[g];
     const Aff y = lk < 0 ? aff_identity() : lds_aff(P + c * cs4 + 3 * lk);
     sts_aff(Y0 + 3 * idx, y);
     if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(Lt.jinfo[lk] & kJ16Seg));
   }
-  compute_sync();
+  pass_sync<NT>();
   float4 *cur = Y0, *nxt = Y1;
   int16_t *pc = ptr0, *pn = ptr1;
   for (int r = 0; r < b.T.rounds; ++r) {
-    for (int idx = tid; idx < CS; idx += kComputeThreads) {
+    for (int idx = tid; idx < CS; idx += NT) {
       const int c = (int)b.divS.div(idx), g = idx - c * nseg;
       const int p = pc[g];
       Aff y = lds_aff(cur + 3 * idx);
@@ -238,7 +266,7 @@ __device__ __forceinline__ float4 *pass2(const ItemBuf &b, const ItemLayout &Lt,
       sts_aff(nxt + 3 * idx, y);
       if (c == 0) pn[g] = (int16_t)(p >= 0 ? pc[p] : -1);
     }
-    compute_sync();
+    pass_sync<NT>();
     float4 *tmp = cur;
     cur = nxt;
     nxt = tmp;

@@ -110,11 +110,12 @@ def test_autotuned_frame_parity(torch):
     ctx.tune(plan, 2)  # the adjoint's schedule search runs too
 
 
-@pytest.mark.parametrize("sched", [[4, 1, 1024, 0], [8, 2, 2048, 0], [32, 3, 4096, 0], [16, 2, 2048, 1],
-                                   [16, 3, 1024, 1]])
+@pytest.mark.parametrize("sched", [[4, 1, 1024, 0, 0], [8, 2, 2048, 0, 6], [32, 3, 4096, 0, 4], [16, 2, 2048, 1, 8],
+                                   [16, 3, 1024, 1, 0], [16, 2, 256, 1, 6]])
 def test_every_schedule_variant_parity(torch, sched):
     """Each schedule the autotuner may pick (segment length, CTAs per SM --
-    3 selects the other compiled kernel variant --, item size, walk mode)
+    3 selects the other compiled kernel variant --, item size, chain-walk
+    frame kernel, persistent or one-item adjoint kernel)
     gives oracle results for the frame, the forward and the adjoint, run one
     after another on the same plan (they share its work-queue counters)."""
     import paper_2505_06703_gb300 as pk
