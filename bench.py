@@ -50,7 +50,8 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes per launch of the persistent frame kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources it was taken on; reported as null once the sources change.
-NCU_TRAFFIC = {"c04d5847136cbe29": 1360896 + 39827200}  # profiles/frame_kernel_config2.md
+# dram read + write bytes of one k_scan launch from one ncu capture, per kernel-source hash
+NCU_TRAFFIC = {"7700f5e04a11ee1d": 1835776 + 41493248}
 
 
 # ------------------------------------------------------------------ helpers
