@@ -365,11 +365,126 @@ def run_ours(args) -> dict:
                            "speedup_fused_vs_plain": (p_ms / p_steps) / ms_step}
         result["fwd_bwd"] = run_fwd_bwd(ctx_factory=setup_ctx, device=local, dev=dev, steps=steps,
                                         warmup=warmup, world=world, peak=peak, schedule=args.schedule_bwd)
+        if not args.schedule:  # the extra workloads run the autotuner
+            result["frame_mixed"] = run_mixed_frame(local, dev, world, peak)
+            result["ik"] = run_ik(local, dev, world, peak)
     del ctx
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
+
+
+def run_mixed_frame(device, dev, world, peak) -> dict:
+    """Batched heterogeneous frame (10,000 characters of 5 types, 32 to 2,048
+    joints, depths 8 to 2,048): the autotuned schedule, frames replayed from
+    one CUDA graph with outputs rotated over buffers larger than L2."""
+    import torch
+    w = synth.config3()
+    ctx, plan = setup_ctx(w, device)
+    ctx.tune(plan, 0)
+    joints = plan.total
+    n_out = max(2, math.ceil(2.5 * L2_BYTES / (joints * 48)))
+    outs = [torch.empty((joints, 12), dtype=torch.float32, device=dev) for _ in range(n_out)]
+    tm = torch.as_tensor(w["time"], device=dev)
+    bw = torch.as_tensor(w["weight"], device=dev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for o in outs:
+            ctx.evaluate_frame(plan, tm, bw, out=o)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for o in outs:
+            ctx.evaluate_frame(plan, tm, bw, out=o)
+    torch.cuda.synchronize()
+    reps = 5
+    ms = aggregate_max(time_events(lambda s: graph.replay(), reps, 2), world)
+    ms_step = ms / (reps * n_out)
+    alg = frame_algorithmic_bytes(w)
+    achieved = alg / (ms_step / 1e3) / 1e9
+    return {"value": world * joints / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step,
+            "workload": "frame: 10,000 chars of 32/128/512/1,024/2,048-joint types (depths 8/16/70/256/2,048) "
+                        "at 40/30/15/10/5 %, shuffled",
+            "schedule": ctx.get_schedule(plan),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes": alg,
+                         "note": "whole frame (work queue + kernels), frames back to back in one CUDA graph"}}
+
+
+def run_ik(device, dev, world, peak) -> dict:
+    """Batched IK (8,192 characters, 128- and 1,024-joint types, 8 effectors
+    each): 200 Adam steps, each one fused launch (forward over the effector
+    ancestors, effector loss, adjoint, Adam), the whole run one CUDA graph.
+    The final effector error is the GPU run's own distance to its targets;
+    the agreement with the FP64 run of the same schedule is a parity test."""
+    import torch
+    w = synth.config5()
+    ctx, plan = setup_ctx(w, device)
+    types, ct, eff = w["types"], np.asarray(w["char_type"]), np.asarray(w["effectors"])
+    t = torch.as_tensor(w["t"], device=dev)
+    _, mt = ctx.forward_local(plan, torch.as_tensor(w["q_target"], device=dev), t, skin=False, model=True)
+    mt = mt.view(-1, 3, 4)[:, :, 3]
+    off = torch.as_tensor(plan.row_off[:-1], device=dev)
+    eff_t = torch.as_tensor(eff, device=dev).long()[torch.as_tensor(ct, device=dev).long()]
+    targets = mt[off[:, None] + eff_t].contiguous()
+    active = 0  # joints the step touches: the effectors' ancestors
+    for ty in range(len(types)):
+        par, act = types[ty]["parents"], set()
+        for j in eff[ty]:
+            a = int(j)
+            while a >= 0 and a not in act:
+                act.add(a)
+                a = int(par[a])
+        active += len(act) * int(np.sum(ct == ty))
+    q0 = torch.as_tensor(w["q0"], device=dev)
+    q, m, v = q0.clone(), torch.zeros_like(q0), torch.zeros_like(q0)
+    loss = torch.zeros(plan.n_chars, device=dev)
+    ctx.tune(plan, 2)  # the adjoint's schedule; the IK object keeps it
+    ik = ctx.ik(plan, eff)
+    n_steps = int(w["n_steps"])
+    stream = torch.cuda.Stream()
+
+    def run_all():
+        ik.reset()
+        q.copy_(q0)
+        m.zero_()
+        v.zero_()
+        for _ in range(n_steps):
+            ik.step(q, m, v, t, targets, lr=w["lr"], betas=w["betas"], eps=w["eps"], loss=loss)
+
+    with torch.cuda.stream(stream):
+        run_all()  # warm outside capture (kernel attributes)
+    stream.synchronize()
+
+    def eff_err():
+        _, mq = ctx.forward_local(plan, q, t, skin=False, model=True)
+        pe = mq.view(-1, 3, 4)[:, :, 3][off[:, None] + eff_t]
+        d = torch.linalg.norm(pe - targets, dim=-1)
+        return float(d.mean()), float(d.max())
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        run_all()
+    torch.cuda.synchronize()
+    reps = 3
+    ms = aggregate_max(time_events(lambda s: graph.replay(), reps, 1), world)
+    ms_step = ms / (reps * n_steps)
+    e_mean, e_max = eff_err()
+    q.copy_(q0)
+    e0_mean, _ = eff_err()
+    alg = active * 108 + plan.n_chars * eff.shape[1] * 12
+    achieved = alg / (ms_step / 1e3) / 1e9
+    return {"steps_per_s": world / (ms_step / 1e3), "active_joints_per_s": world * active / (ms_step / 1e3),
+            "ms_per_step": ms_step, "steps": n_steps, "active_joints": active, "characters": plan.n_chars,
+            "workload": "IK: 4,096 x 128-joint (depth 16) + 4,096 x 1,024-joint (depth 256) chars, 8 effectors "
+                        "each, 200 Adam steps (lr 1e-2)",
+            "schedule": ctx.get_schedule(plan),
+            "effector_error": {"start_mean": e0_mean, "final_mean": e_mean, "final_max": e_max,
+                               "note": "distance to targets (skeletons of unit extent)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes_per_step": alg,
+                         "note": "108 B per active joint (q, t, m, v in; q, m, v out) + targets"}}
 
 
 def run_fwd_bwd(ctx_factory, device, dev, steps, warmup, world, peak, schedule=None):
