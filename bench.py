@@ -368,6 +368,12 @@ def run_ours(args) -> dict:
         if not args.schedule:  # the extra workloads run the autotuner
             result["frame_mixed"] = run_mixed_frame(local, dev, world, peak)
             result["ik"] = run_ik(local, dev, world, peak)
+            cmp_ = time_forward_methods(rank_workload(rank), local, dev, world)
+            result["scan_comparison"] = {
+                "workload": "forward from local poses (scan + bind) on the frame's 2,098,176 joints",
+                "ms_per_launch": {k: v for k, v in cmp_.items() if k != "schedule"},
+                "speedup_ours_vs": {k: v / cmp_["ours"] for k, v in cmp_.items() if k not in ("schedule", "ours")},
+                "schedule": cmp_["schedule"]}
     del ctx
     if world > 1:
         import torch.distributed as dist
@@ -487,6 +493,69 @@ def run_ik(device, dev, world, peak) -> dict:
                          "note": "108 B per active joint (q, t, m, v in; q, m, v out) + targets"}}
 
 
+def time_forward_methods(w: dict, device: int, dev: str, world: int, algs=(1, 2, 3, 4)) -> dict:
+    """Hierarchy-Scan + bind from given local poses on workload w: our
+    autotuned forward kernel, the plain level-synchronous kernel and the
+    paper's Algorithms 1-4 (one CTA per character, one thread per joint), each
+    as back-to-back launches in one CUDA graph over output buffers rotated
+    past the L2 size.  Milliseconds per launch."""
+    import torch
+    ctx, plan = setup_ctx(w, device)
+    ctx.tune(plan, 1)
+    q, t = synth.local_poses(np.random.default_rng(7), plan.total, t_half=0.0005)
+    q, t = torch.as_tensor(q, device=dev), torch.as_tensor(t, device=dev)
+    n_out = max(2, math.ceil(2.5 * L2_BYTES / (plan.total * 48)))
+    outs = [torch.empty((plan.total, 12), dtype=torch.float32, device=dev) for _ in range(n_out)]
+    methods = {"ours": lambda o: ctx.forward_local(plan, q, t, skin=True),
+               "levelsync": lambda o: ctx.forward_local(plan, q, t, levelsync=True)}
+    for a in algs:
+        methods[f"paper_alg{a}"] = (lambda a: lambda o: ctx.forward_local_paper(plan, a, q, t, out=o))(a)
+    res = {}
+    for name, fn in methods.items():
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            for o in outs:
+                fn(o)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for o in outs:
+                fn(o)
+        torch.cuda.synchronize()
+        reps = 3
+        res[name] = aggregate_max(time_events(lambda s: graph.replay(), reps, 1), world) / (reps * n_out)
+    res["schedule"] = ctx.get_schedule(plan)
+    return res
+
+
+def run_paper_sweep(args) -> dict:
+    """The paper's experiment shape (Sec. 4, Fig. 7): 10,000 characters of
+    about 300 joints, the tree depth swept from 15 to 120 levels; per depth
+    four seeded random 300-joint trees (a spine of that depth, the other
+    joints on uniform earlier parents), 2,500 characters each.  Our forward
+    kernel against the plain kernel and the paper's Algorithms 1-4."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    rows = []
+    for depth in (15, 30, 60, 90, 120):
+        rng = np.random.default_rng(1000 + depth)
+        types = [synth.make_type(synth.relabel_dfs(synth.random_tree(300, depth, rng, spine=depth), rng)[0], rng,
+                                 with_clips=False) for _ in range(4)]
+        ct = np.repeat(np.arange(4, dtype=np.int32), 2500)
+        rng.shuffle(ct)
+        r = time_forward_methods({"types": types, "char_type": ct}, local, dev, world)
+        joints = 10000 * 300
+        rows.append({"depth": depth, "ms": {k: v for k, v in r.items() if k != "schedule"},
+                     "g_joints_per_s": {k: joints / (v / 1e3) / 1e9 for k, v in r.items() if k != "schedule"},
+                     "schedule": r["schedule"]})
+    return {"metric": "Hierarchy-Scan + bind from local poses, ms per batch of 10,000 x 300-joint characters",
+            "impl": "ours", "n_gpus": world, "sweep": rows,
+            "config": {"workload": "depth sweep 15-120, 4 random 300-joint trees x 2,500 characters per depth",
+                       "timing": "CUDA graphs, outputs rotated past L2, CUDA events"}}
+
+
 def run_fwd_bwd(ctx_factory, device, dev, steps, warmup, world, peak, schedule=None):
     """Fused forward + adjoint (anim_loss_backward) on 1,024 characters of the
     256-joint type: read q, t, target; write dq, dt (and per-character loss)."""
@@ -589,12 +658,20 @@ def main():
     ap.add_argument("--schedule", default="", help="seg_len,ctas_per_sm,joints_per_item,walk[,adj_ctas] for the frame "
                                                    "instead of running the autotuner")
     ap.add_argument("--schedule-bwd", default="", help="the same for the forward+adjoint measurement")
+    ap.add_argument("--paper-sweep", action="store_true",
+                    help="print the depth sweep of the paper's experiment (our forward kernel, the plain kernel, "
+                         "the paper's Algorithms 1-4) instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         r = run_reference(args)
         if r is not None:
+            print(json.dumps(r))
+        return
+    if args.paper_sweep:
+        r = run_paper_sweep(args)
+        if dist_env()[1] == 0:
             print(json.dumps(r))
         return
     world, rank, _ = dist_env()

@@ -166,6 +166,21 @@ ANIM_API int anim_forward_local(anim_ctx *ctx, const anim_plan *plan, const floa
 ANIM_API int anim_forward_local_levelsync(anim_ctx *ctx, const anim_plan *plan, const float *d_q, const float *d_t,
                                  float *d_skin, void *stream);
 
+/* The paper's own Hierarchy-Scan schedules as GPU comparators of
+ * anim_forward_local (skin output only): one CTA per character, one thread
+ * per joint, joints in shared memory, a block barrier between phases.
+ * algorithm 1: every joint walks to the root multiplying its ancestors'
+ * local matrices (Sec. 2, Alg. 1); 2: pointer doubling over joints,
+ * ceil(log2 depth) rounds (Sec. 3.1, Alg. 2 and Eq. 2); 3: 64-node blocks,
+ * 6 in-block doubling rounds, then a walk over the nearest out-of-block
+ * ancestors' partial products (Sec. 3.2.1, Alg. 3); 4: a joint and up to 7
+ * in-block ancestors serially, up to 7 jumps of stride 8, then the
+ * out-of-block walk (Sec. 3.2.2, Alg. 4).  Same inputs and outputs as
+ * anim_forward_local.  ANIM_EUNSUPPORTED if a type of the plan has more than
+ * 1,024 joints; ANIM_EINVAL for another algorithm number. */
+ANIM_API int anim_forward_local_paper(anim_ctx *ctx, const anim_plan *plan, int algorithm, const float *d_q,
+                                      const float *d_t, float *d_skin, void *stream);
+
 /* Adjoint of anim_forward_local's model positions p_j (translation column
  * of M_j): given d_grad_pos [total][3] = dLoss/dp, writes d_grad_q [total][4]
  * (w.r.t. the unnormalized q) and d_grad_t [total][3].  The forward pass is

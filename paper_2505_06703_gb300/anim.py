@@ -37,6 +37,7 @@ SIGNATURES = {
     "anim_frame_run_queue": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_forward_local": (c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "anim_forward_local_levelsync": (c_int, [_P, _P, _P, _P, _P, _P]),
+    "anim_forward_local_paper": (c_int, [_P, _P, c_int, _P, _P, _P, _P]),
     "anim_backward": (c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "anim_loss_backward": (c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "anim_ik_create": (c_int, [_P, _P, c_int, _P, POINTER(_P)]),
@@ -206,6 +207,14 @@ class Context:
             self._ck(self.lib.anim_forward_local(self.h, plan.h, _dptr(q), _dptr(t), _dptr(s), _dptr(m),
                                                  _stream(stream)))
         return s, m
+
+    def forward_local_paper(self, plan, algorithm, q, t, out=None, stream=None):
+        """Skin matrices from local poses with the paper's Algorithm 1-4
+        (one CTA per character, one thread per joint): a comparator."""
+        s = self._out(plan, 12, out)
+        self._ck(self.lib.anim_forward_local_paper(self.h, plan.h, int(algorithm), _dptr(q), _dptr(t), _dptr(s),
+                                                   _stream(stream)))
+        return s
 
     def backward(self, plan, q, t, grad_pos, grad_q=None, grad_t=None, stream=None):
         grad_q = self._out(plan, 4, grad_q)

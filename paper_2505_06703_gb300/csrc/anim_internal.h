@@ -39,6 +39,9 @@ struct TypeDev {
   // IK views: the active subtree of a type; view joint j reads row gather[j]
   // of the full type (nullptr = identity).
   const int32_t *gather;
+  // The paper's 64-node blocks (comparator kernels): nearest ancestor of
+  // each joint outside its block of 64 consecutive indices, -1 at the top.
+  const int32_t *blk_out;
   // Chain-walk frame kernel (k_walk): a static lane schedule of wk_S steps
   // for wk_P lanes per character; entry [s][slot] names the joint lane `slot`
   // composes at step s (kWInvalid: idle).  wk_mode 1: natural chains walked
@@ -211,6 +214,19 @@ int walk_blocks_per_sm(size_t smem);  // resident one-warp CTAs per SM at this s
 // key table ([clip][key][n][2] float4) and inverse binds ([n][3] float4).
 cudaError_t launch_build_walk(const TypeDev &T, const float4 *keys, float4 *wk_keys, float4 *wk_bind,
                               cudaStream_t s);
+
+// The paper's Algorithms 1-4 (comparators): one CTA per character.
+constexpr int kPaperMaxJoints = 1024;
+struct PaperArgs {
+  const TypeDev *types;
+  const int32_t *char_type;
+  const int64_t *row_off;
+  int algo;  // 1..4
+  const float *q, *t;
+  float *skin;
+};
+size_t paper_smem_bytes(int n);
+cudaError_t launch_paper(const PaperArgs &a, int n_chars, int threads, size_t smem, cudaStream_t s);
 
 // Setup kernels.
 cudaError_t launch_prepare_keys(float4 *keys, int n_clips, int n_keys, int n, cudaStream_t s);

@@ -428,6 +428,13 @@ struct TypeHost {
     const size_t o_js = B.add(seg.job_start.data(), seg.job_start.size() * 4);
     const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
     const size_t o_wt = B.add(ws.tab.data(), ws.tab.size() * 4);
+    std::vector<int32_t> blk_out(n);
+    for (int j = 0; j < n; ++j) {  // parent of the block-local root of j
+      int r = j;
+      while (parent[r] >= 0 && parent[r] / 64 == r / 64) r = parent[r];
+      blk_out[j] = parent[r];
+    }
+    const size_t o_bo = B.add(blk_out.data(), blk_out.size() * 4);
     void *d = nullptr;
     cudaError_t e = B.upload(&d);
     if (e != cudaSuccess) {
@@ -459,6 +466,7 @@ struct TypeHost {
     dev.wk_S = ws.S;
     dev.wk_nbs = ws.nbs;
     dev.wk_tab = ws.mode ? (const uint32_t *)(base + o_wt) : nullptr;
+    dev.blk_out = (const int32_t *)(base + o_bo);
     sync_dev();
     return cudaSuccess;
   }
@@ -1230,6 +1238,33 @@ int anim_forward_local_levelsync(anim_ctx *ctx, const anim_plan *plan, const flo
     const int threads = T.n <= 1024 ? std::max(32, (T.n + 31) / 32 * 32) : 1024;
     CK(launch_levelsync(1, a, threads, (cudaStream_t)stream));
   }
+  return ANIM_OK;
+}
+
+int anim_forward_local_paper(anim_ctx *ctx, const anim_plan *plan, int algorithm, const float *d_q,
+                             const float *d_t, float *d_skin, void *stream) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (algorithm < 1 || algorithm > 4) return fail(ctx, ANIM_EINVAL, "algorithm must be 1, 2, 3 or 4");
+  if (plan->n_chars == 0) return ANIM_OK;
+  if (!d_q || !d_t || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_q) || !aligned16(d_skin) || !aligned4(d_t))
+    return fail(ctx, ANIM_EINVAL, "d_q, d_skin must be 16-byte aligned");
+  int nmax = 0;
+  for (int t : plan->used) nmax = std::max(nmax, ctx->types[t]->n);
+  if (nmax > kPaperMaxJoints)
+    return fail(ctx, ANIM_EUNSUPPORTED, "the paper's schedules run one thread per joint: at most %d joints",
+                kPaperMaxJoints);
+  PaperArgs a{};
+  a.types = ctx->d_types;
+  a.char_type = plan->d_char_type;
+  a.row_off = plan->d_row_off;
+  a.algo = algorithm;
+  a.q = d_q;
+  a.t = d_t;
+  a.skin = d_skin;
+  const int threads = std::min(kPaperMaxJoints, (nmax + 31) / 32 * 32);
+  CK(launch_paper(a, (int)plan->n_chars, threads, paper_smem_bytes(nmax), (cudaStream_t)stream));
   return ANIM_OK;
 }
 

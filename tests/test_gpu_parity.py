@@ -327,6 +327,36 @@ def test_edge_types_frame_and_local(torch):
     assert (np.abs(gt.cpu().numpy() - dt_ref).max(axis=1) <= tol).all()
 
 
+@pytest.mark.parametrize("algorithm", [1, 2, 3, 4])
+def test_paper_algorithms_parity(torch, algorithm):
+    """The paper's Algorithms 1-4 as GPU kernels give the oracle's skin
+    matrices: the 64-joint trees of the plain forward workload, the biped
+    (depth 70), the 256-joint depth-96 tree, a 1,000-joint tree numbered in
+    random topological order (blocks of 64 indices span many subtrees) and a
+    1,024-joint chain (depth 1,024)."""
+    import paper_2505_06703_gb300 as pk
+    rng = np.random.default_rng(50 + algorithm)
+    w1, w2, w4 = synth.config1(), synth.config2(), synth.config4()
+    types = [w1["types"][0], w2["types"][0], w2["types"][1], w4["types"][0],
+             synth.make_type(synth.relabel_random_topological(synth.random_tree(1000, 40, rng, spine=40), rng)[0],
+                             rng, with_clips=False)]
+    ct = np.array([0] * 40 + [1] * 12 + [2] * 2 + [3] * 20 + [4] * 3, np.int32)
+    rng.shuffle(ct)
+    w = {"types": types, "char_type": ct}
+    off = oracle.offsets(ct, types)
+    q, t = synth.local_poses(rng, int(off[-1]), t_half=0.0005)
+    ref, _ = oracle.forward_qt(types, ct, q, t)
+    ctx, plan = _gpu.setup(w, with_clips=False)
+    s = ctx.forward_local_paper(plan, algorithm, _gpu.cuda(q), _gpu.cuda(t))
+    _gpu.assert_skin_close(s.cpu().numpy(), ref, w)
+    # one thread per joint: types above 1,024 joints are refused
+    big = {"types": [synth.make_type(synth.chain(2048), rng, with_clips=False)], "char_type": np.zeros(2, np.int32)}
+    ctx2, plan2 = _gpu.setup(big, with_clips=False)
+    with pytest.raises(pk.AnimError, match="EUNSUPPORTED"):
+        ctx2.forward_local_paper(plan2, algorithm, _gpu.cuda(np.tile([0, 0, 0, 1.0], (4096, 1))),
+                                 _gpu.cuda(np.zeros((4096, 3))))
+
+
 def test_empty_plan_and_errors(torch):
     import paper_2505_06703_gb300 as pk
     rng = np.random.default_rng(5)
