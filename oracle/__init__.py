@@ -80,6 +80,7 @@ def _load():
         _lib.oracle_ik.argtypes = [c_int, i32, i32, i32, c_int, c_int64, i32, d, d, i64, c_int, c_double,
                                    c_double, c_double, c_double, d, d]
         _lib.oracle_ik.restype = c_int
+        _lib.oracle_lbs.argtypes = [c_int, f, f, i32, f, d, d]
     return _lib
 
 
@@ -276,4 +277,34 @@ def ik_targets(w: dict) -> np.ndarray:
     out = np.empty((len(w["char_type"]), eff.shape[1], 3))
     for c, ty in enumerate(w["char_type"]):
         out[c] = model[off[c] + eff[ty], :, 3]
+    return out
+
+
+def lbs(mesh: dict, skin) -> np.ndarray:
+    """Linear blend skinning of one character's mesh with its skin matrices
+    skin [n][3][4]: [n_verts][6] fp64 (skinned position, unit normal)."""
+    lib = _load()
+    pos, nrm = _f32(mesh["pos"]), _f32(mesh["nrm"])
+    bones, wts = _i32(mesh["bones"]), _f32(mesh["weights"])
+    S = _f64(np.asarray(skin).reshape(-1, 12))
+    out = np.empty((len(pos), 6))
+    lib.oracle_lbs(len(pos), _p(pos, c_float), _p(nrm, c_float), _p(bones, c_int32), _p(wts, c_float),
+                   _p(S, c_double), _p(out, c_double))
+    return out
+
+
+def vertex_offsets(char_type, types) -> np.ndarray:
+    """Exclusive prefix of the characters' vertex counts (n_chars + 1)."""
+    nv = np.array([len(types[int(t)]["mesh"]["pos"]) for t in char_type], np.int64)
+    return np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
+
+
+def skin_vertices(w: dict, skin) -> np.ndarray:
+    """Skinned vertices [sum of vertex counts][6] of a workload whose types
+    carry meshes, from the skin matrices [sum][3][4] of its characters."""
+    types, ct = w["types"], w["char_type"]
+    off, voff = offsets(ct, types), vertex_offsets(ct, types)
+    out = np.empty((int(voff[-1]), 6))
+    for c, ty in enumerate(ct):
+        out[voff[c]:voff[c + 1]] = lbs(types[int(ty)]["mesh"], skin[off[c]:off[c + 1]])
     return out

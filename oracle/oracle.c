@@ -566,3 +566,36 @@ int oracle_ik(int n_types, const int32_t *counts, const int32_t *parents_cat, co
   free(m); free(v); free(g); free(toff); free(L); free(M); free(G);
   return 0;
 }
+
+/*
+ * Linear blend skinning: the skinning step that follows Bind MeshPose in the
+ * paper's pipeline (Sec. 1; Table 1 lists meshes of 1,000-3,000 faces).  The
+ * paper does not spell it out, so this is the textbook form.  Vertex v with
+ * rest position p, rest normal nrm, bones b_k and weights w_k (k < 4, weights
+ * summing to 1, zero weights ignored):
+ *     p' = sum_k w_k S_{b_k} [p; 1]
+ *     n' = normalize(sum_k w_k R_{b_k} nrm)      (S = [R | t], rigid)
+ * S: the character's skin matrices [n][12]; out [n_verts][6] = p', n'.
+ */
+void oracle_lbs(int n_verts, const float *pos, const float *nrm, const int32_t *bones, const float *weights,
+                const double *S, double *out) {
+  for (int v = 0; v < n_verts; ++v) {
+    const double p[3] = {pos[3 * v], pos[3 * v + 1], pos[3 * v + 2]};
+    const double q[3] = {nrm[3 * v], nrm[3 * v + 1], nrm[3 * v + 2]};
+    double pp[3] = {0.0, 0.0, 0.0}, nn[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 4; ++k) {
+      const double w = weights[4 * v + k];
+      if (w == 0.0) continue;
+      const double *M = S + 12 * (int64_t)bones[4 * v + k];
+      for (int r = 0; r < 3; ++r) {
+        pp[r] += w * (M[4 * r] * p[0] + M[4 * r + 1] * p[1] + M[4 * r + 2] * p[2] + M[4 * r + 3]);
+        nn[r] += w * (M[4 * r] * q[0] + M[4 * r + 1] * q[1] + M[4 * r + 2] * q[2]);
+      }
+    }
+    const double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    for (int r = 0; r < 3; ++r) {
+      out[6 * (int64_t)v + r] = pp[r];
+      out[6 * (int64_t)v + 3 + r] = len > 0.0 ? nn[r] / len : 0.0;
+    }
+  }
+}

@@ -199,6 +199,35 @@ def make_type(parents: np.ndarray, rng: np.random.Generator, *, with_clips: bool
     return typ
 
 
+def make_mesh(n_joints: int, n_verts: int, rng: np.random.Generator, max_influences: int = 4) -> dict:
+    """A synthetic skinned mesh in bind space: positions uniform in
+    [-0.5, 0.5]^3, unit normals uniform on the sphere, up to 4 distinct bones
+    per vertex with positive weights summing to 1 (a quarter of the vertices
+    use fewer influences; the unused slots have weight 0)."""
+    pos = rng.uniform(-0.5, 0.5, size=(n_verts, 3))
+    nrm = rng.normal(size=(n_verts, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    k = min(max_influences, n_joints)
+    bones = np.zeros((n_verts, 4), np.int32)
+    wts = np.zeros((n_verts, 4))
+    for v in range(n_verts):
+        m = int(rng.integers(1, k + 1)) if rng.uniform() < 0.25 else k
+        bones[v, :m] = rng.choice(n_joints, size=m, replace=False)
+        w = rng.uniform(0.05, 1.0, size=m)
+        wts[v, :m] = w / w.sum()
+    return {"pos": pos.astype(np.float32), "nrm": nrm.astype(np.float32), "bones": bones,
+            "weights": wts.astype(np.float32)}
+
+
+def with_meshes(w: dict, n_verts: int = 1500, seed: int = 11) -> dict:
+    """The workload with a mesh attached to every type (1,500 vertices by
+    default: about 3,000 faces, the top of the paper's Table 1 range)."""
+    rng = np.random.default_rng(seed)
+    w = dict(w)
+    w["types"] = [dict(t, mesh=make_mesh(len(t["parents"]), n_verts, rng)) for t in w["types"]]
+    return w
+
+
 def char_offsets(char_type: np.ndarray, types: list) -> np.ndarray:
     """Exclusive prefix of joint counts in character order (row offsets of
     each character's joints in the [sum n][...] arrays)."""
