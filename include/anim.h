@@ -80,6 +80,7 @@ enum {
 /* Limits.  A skeleton type has at most ANIM_MAX_JOINTS joints. */
 #define ANIM_MAX_JOINTS 2048
 #define ANIM_MAX_KEYS 1024
+#define ANIM_MAX_VERTS (1 << 20)
 
 typedef struct anim_ctx anim_ctx;
 typedef struct anim_plan anim_plan;
@@ -131,6 +132,20 @@ ANIM_API int anim_plan_total_joints(const anim_plan *plan, int64_t *out_total);
 /* Host copy of the row offsets: out[0..n_chars] (exclusive prefix). */
 ANIM_API int anim_plan_row_offsets(const anim_plan *plan, int64_t *out);
 
+/* Skinned mesh of a type (no counterpart in the paper beyond the skinning
+ * step its pipeline ends with, Sec. 1, and Table 1's 1,000-3,000-face
+ * meshes): n_verts in [1, ANIM_MAX_VERTS] vertices in bind space, host
+ * arrays copied in: rest_pos [n_verts][3], rest_nrm [n_verts][3] (unit),
+ * bones [n_verts][4] joint ids in [0, n), weights [n_verts][4] (finite,
+ * summing to 1; zero-weight slots are skipped).  Replaces an earlier mesh of
+ * the type.  ANIM_EINVAL on an out-of-range bone or a non-finite weight. */
+ANIM_API int anim_upload_mesh(anim_ctx *ctx, int32_t type_id, int n_verts, const float *rest_pos,
+                              const float *rest_nrm, const int32_t *bones, const float *weights);
+
+/* Host copy of the plan's vertex offsets: out[0..n_chars], the exclusive
+ * prefix of the characters' vertex counts (0 for a type without a mesh). */
+ANIM_API int anim_plan_vertex_offsets(anim_ctx *ctx, const anim_plan *plan, int64_t *out);
+
 /* The fused frame (Sec. 1 steps 1-3): for each character c, sample its
  * type's clips at d_time[c] seconds, blend clip 0 -> clip 1 with
  * d_blend_w[c], compose down the hierarchy (Eq. 1) and multiply by the inverse
@@ -139,6 +154,17 @@ ANIM_API int anim_plan_row_offsets(const anim_plan *plan, int64_t *out);
  * work-queue launch on `stream`. */
 ANIM_API int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
                         float *d_skin, void *stream);
+
+/* The fused frame followed by linear blend skinning of every character's
+ * mesh, fused into the same kernel: vertex v of character c goes to
+ * sum_k w_k S_{b_k} [p; 1] with normal normalize(sum_k w_k R_{b_k} n), where
+ * S = [R | t] are the character's skin matrices (rigid), still in shared
+ * memory.  d_verts: device [total vertices][6] float (position, normal) at
+ * the plan's vertex offsets, 16-byte aligned; d_skin may be NULL, and then
+ * the skin matrices never reach memory.  Every type runs on the segmented
+ * kernel here (the chain-walk kernel has no skinning pass). */
+ANIM_API int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const float *d_time,
+                                         const float *d_blend_w, float *d_skin, float *d_verts, void *stream);
 
 /* The two launches of anim_evaluate_frame, for callers that schedule them
  * apart (e.g. to time the persistent kernel alone): build_queue buckets the

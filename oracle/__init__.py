@@ -294,8 +294,9 @@ def lbs(mesh: dict, skin) -> np.ndarray:
 
 
 def vertex_offsets(char_type, types) -> np.ndarray:
-    """Exclusive prefix of the characters' vertex counts (n_chars + 1)."""
-    nv = np.array([len(types[int(t)]["mesh"]["pos"]) for t in char_type], np.int64)
+    """Exclusive prefix of the characters' vertex counts (n_chars + 1); a
+    type without a mesh has none."""
+    nv = np.array([len(types[int(t)]["mesh"]["pos"]) if "mesh" in types[int(t)] else 0 for t in char_type], np.int64)
     return np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
 
 
@@ -306,5 +307,6 @@ def skin_vertices(w: dict, skin) -> np.ndarray:
     off, voff = offsets(ct, types), vertex_offsets(ct, types)
     out = np.empty((int(voff[-1]), 6))
     for c, ty in enumerate(ct):
-        out[voff[c]:voff[c + 1]] = lbs(types[int(ty)]["mesh"], skin[off[c]:off[c + 1]])
+        if voff[c + 1] > voff[c]:
+            out[voff[c]:voff[c + 1]] = lbs(types[int(ty)]["mesh"], skin[off[c]:off[c + 1]])
     return out

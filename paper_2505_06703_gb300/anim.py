@@ -31,6 +31,9 @@ SIGNATURES = {
     "anim_plan_destroy": (c_int, [_P, _P]),
     "anim_plan_total_joints": (c_int, [_P, POINTER(c_int64)]),
     "anim_plan_row_offsets": (c_int, [_P, _P]),
+    "anim_upload_mesh": (c_int, [_P, c_int32, c_int, _P, _P, _P, _P]),
+    "anim_plan_vertex_offsets": (c_int, [_P, _P, _P]),
+    "anim_evaluate_frame_skinned": (c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame_levelsync": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_frame_build_queue": (c_int, [_P, _P, _P, _P]),
@@ -164,6 +167,31 @@ class Context:
         nc, nk, n, eight = k.shape
         assert eight == 8
         self._ck(self.lib.anim_upload_clips(self.h, int(type_id), nc, nk, float(rate_hz), _np_ptr(k)))
+
+    def upload_mesh(self, type_id: int, mesh: dict):
+        """mesh: pos [nv,3], nrm [nv,3], bones [nv,4] int, weights [nv,4]."""
+        pos = np.ascontiguousarray(mesh["pos"], dtype=np.float32)
+        nrm = np.ascontiguousarray(mesh["nrm"], dtype=np.float32)
+        bones = np.ascontiguousarray(mesh["bones"], dtype=np.int32)
+        wts = np.ascontiguousarray(mesh["weights"], dtype=np.float32)
+        self._ck(self.lib.anim_upload_mesh(self.h, int(type_id), len(pos), _np_ptr(pos), _np_ptr(nrm),
+                                           _np_ptr(bones), _np_ptr(wts)))
+
+    def vertex_offsets(self, plan):
+        out = np.zeros(plan.n_chars + 1, dtype=np.int64)
+        self._ck(self.lib.anim_plan_vertex_offsets(self.h, plan.h, _np_ptr(out)))
+        return out
+
+    def evaluate_frame_skinned(self, plan, time, blend_w, verts=None, skin=None, stream=None):
+        """Frame + fused linear blend skinning: vertices [total vertices, 6];
+        pass a skin tensor [total, 12] to also receive the skin matrices."""
+        import torch
+        if verts is None:
+            nv = int(self.vertex_offsets(plan)[-1])
+            verts = torch.empty((max(nv, 1), 6), dtype=torch.float32, device=f"cuda:{self.device}")
+        self._ck(self.lib.anim_evaluate_frame_skinned(self.h, plan.h, _dptr(time), _dptr(blend_w), _dptr(skin),
+                                                      _dptr(verts), _stream(stream)))
+        return verts
 
     def plan(self, char_type):
         return Plan(self, char_type)

@@ -42,6 +42,12 @@ struct TypeDev {
   // The paper's 64-node blocks (comparator kernels): nearest ancestor of
   // each joint outside its block of 64 consecutive indices, -1 at the top.
   const int32_t *blk_out;
+  // Skinned mesh (linear blend skinning after the bind product): 3 float4
+  // per vertex: (px py pz nx), (ny nz w0 w1), (w2 w3 bones01 bones23) with
+  // the bone ids as 16-bit pairs in the last two words' bits.
+  int n_verts;
+  int pad3;
+  const float4 *mesh;
   // Chain-walk frame kernel (k_walk): a static lane schedule of wk_S steps
   // for wk_P lanes per character; entry [s][slot] names the joint lane `slot`
   // composes at step s (kWInvalid: idle).  wk_mode 1: natural chains walked
@@ -87,7 +93,7 @@ struct WorkItem {
 constexpr int kPersistentThreads = 288;
 // One-item adjoint kernel: 4 warps, no producer; its static shared memory.
 constexpr int kAdjSmallThreads = 128;
-constexpr int kAdjSmallStatic = 2 * 1024;
+constexpr int kAdjSmallStatic = 3 * 1024;
 
 struct LaunchCfg {
   int threads;       // CTA size
@@ -118,6 +124,10 @@ struct ScanArgs {
   float *skin;
   float *model;
   int C_max_unused;
+  // frame with skinning: vertices [sum of vertex counts][6] (position,
+  // normal) at the characters' vertex offsets; skin may then be nullptr
+  float *verts;
+  const int64_t *vert_off;  // [n_chars + 1]
 };
 
 cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);

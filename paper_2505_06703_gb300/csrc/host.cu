@@ -392,11 +392,14 @@ struct TypeHost {
   std::vector<int32_t> gather;  // IK views only
   WalkSched ws;                 // chain-walk schedule (mode 0: not walkable)
   bool ws_done = false;
+  float4 *d_mesh = nullptr;     // skinned mesh, 3 float4 per vertex
+  int n_verts = 0;
   float4 *d_wkeys = nullptr;    // schedule-ordered key records
   float4 *d_wbind = nullptr;    // schedule-ordered inverse binds
   TypeDev dev{};
   ~TypeHost() {
-    for (void *p : {(void *)d_tables, (void *)d_inv_bind, (void *)d_keys, (void *)d_wkeys, (void *)d_wbind})
+    for (void *p : {(void *)d_tables, (void *)d_inv_bind, (void *)d_keys, (void *)d_wkeys, (void *)d_wbind,
+                    (void *)d_mesh})
       if (p) cudaFree(p);
   }
   cudaError_t build_tables() {
@@ -479,6 +482,8 @@ struct TypeHost {
     dev.keys = d_keys;
     dev.wk_keys = d_wkeys;
     dev.wk_bind = d_wbind;
+    dev.n_verts = n_verts;
+    dev.mesh = d_mesh;
   }
   // Schedule-ordered key records (when clips are uploaded) and inverse binds
   // of a walkable type; synchronous.
@@ -592,12 +597,19 @@ struct anim_plan {
   // (d_queue[2..3])
   int n_slots_walk = 0;
   int walk_ctas = 0, walk_nbs = 0;
-  size_t walk_smem = 0;  // a type whose adjoint working set does not fit this schedule, else -1
+  size_t walk_smem = 0;
+  // frame with skinning: every type on the segmented CTA kernel (its own
+  // range layout when the frame's layout gives some types to the walk kernel)
+  RangeDev *d_ranges_cta = nullptr;
+  int32_t *d_cap_cta = nullptr;
+  int n_ranges_cta = 0, n_slots_cta = 0;
+  std::vector<int64_t> vert_off;  // [n_chars + 1]
+  int64_t *d_vert_off = nullptr;  // a type whose adjoint working set does not fit this schedule, else -1
   ~anim_plan() {
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
                     (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
                     (void *)d_n_items, (void *)d_queue, (void *)d_used,
-                    (void *)d_cap})
+                    (void *)d_cap, (void *)d_ranges_cta, (void *)d_cap_cta, (void *)d_vert_off})
       if (p) cudaFree(p);
   }
 };
@@ -830,9 +842,35 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->n_ranges = (int)ranges.size();
   P->n_slots = slots;
   CK(upload_vec(&P->d_ranges, ranges));
+  // the all-CTA layout for the frame with skinning
+  std::vector<RangeDev> ranges_cta;
+  int slots_cta = 0;
+  if (P->n_slots_walk > 0) {
+    for (size_t u = 0; u < P->used.size(); ++u) {
+      const int t = P->used[u];
+      const int cnt = (int)P->by_type[u].size(), C = P->C_scan[t], nk = ctx->types[t]->n_keys;
+      for (int k = 0; k < cnt; k += kRangeChars) {
+        RangeDev r;
+        r.type = t;
+        r.start = P->type_chars_start[u] + k;
+        r.count = std::min(kRangeChars, cnt - k);
+        r.region = slots_cta;
+        slots_cta += (r.count + C - 1) / C + std::min(r.count, std::max(nk, 1));
+        ranges_cta.push_back(r);
+      }
+    }
+  }
+  P->n_ranges_cta = (int)ranges_cta.size();
+  P->n_slots_cta = slots_cta;
+  CK(upload_vec(&P->d_ranges_cta, ranges_cta));
+  CK(upload_vec(&P->d_cap_cta, P->C_scan));
+  P->vert_off.assign(P->n_chars + 1, 0);
+  for (int64_t c = 0; c < P->n_chars; ++c)
+    P->vert_off[c + 1] = P->vert_off[c] + ctx->types[P->char_type[c]]->n_verts;
+  CK(upload_vec(&P->d_vert_off, P->vert_off));
   if (P->d_items_frame) cudaFree(P->d_items_frame);
   P->d_items_frame = nullptr;
-  CK(cudaMalloc(&P->d_items_frame, std::max(1, slots) * sizeof(WorkItem)));
+  CK(cudaMalloc(&P->d_items_frame, std::max(1, std::max(slots, slots_cta)) * sizeof(WorkItem)));
   const int grid = ctx->sm_count * ctx->ctas_per_sm;
   P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16),
                  ctx->ctas_per_sm >= 3 ? 3 : 2};
@@ -966,6 +1004,52 @@ int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, f
   T.rate = rate_hz;
   CK(T.build_walk_data());
   CK(upload_types(ctx));
+  return ANIM_OK;
+}
+
+static int check_plan(anim_ctx *ctx, const anim_plan *plan);
+
+int anim_upload_mesh(anim_ctx *ctx, int32_t type_id, int n_verts, const float *rest_pos, const float *rest_nrm,
+                     const int32_t *bones, const float *weights) {
+  if (!ctx) return ANIM_EINVAL;
+  if (type_id < 0 || type_id >= (int)ctx->types.size()) return fail(ctx, ANIM_EINVAL, "type id %d unknown", type_id);
+  if (n_verts < 1 || n_verts > ANIM_MAX_VERTS) return fail(ctx, ANIM_EINVAL, "n_verts must be in [1, %d]", ANIM_MAX_VERTS);
+  if (!rest_pos || !rest_nrm || !bones || !weights) return fail(ctx, ANIM_EINVAL, "NULL mesh array");
+  TypeHost &T = *ctx->types[type_id];
+  std::vector<float4> rec((size_t)n_verts * 3);
+  for (int v = 0; v < n_verts; ++v) {
+    for (int k = 0; k < 4; ++k) {
+      const int b = bones[4 * v + k];
+      const float w = weights[4 * v + k];
+      if (b < 0 || b >= T.n) return fail(ctx, ANIM_EINVAL, "vertex %d: bone %d out of range", v, b);
+      if (!std::isfinite(w)) return fail(ctx, ANIM_EINVAL, "vertex %d: non-finite weight", v);
+    }
+    const float *p = rest_pos + 3 * v, *q = rest_nrm + 3 * v, *w = weights + 4 * v;
+    const int32_t *b = bones + 4 * v;
+    const uint32_t b01 = (uint32_t)b[0] | ((uint32_t)b[1] << 16), b23 = (uint32_t)b[2] | ((uint32_t)b[3] << 16);
+    float f01, f23;
+    memcpy(&f01, &b01, 4);
+    memcpy(&f23, &b23, 4);
+    rec[3 * v] = make_float4(p[0], p[1], p[2], q[0]);
+    rec[3 * v + 1] = make_float4(q[1], q[2], w[0], w[1]);
+    rec[3 * v + 2] = make_float4(w[2], w[3], f01, f23);
+  }
+  CK(cudaSetDevice(ctx->device));
+  if (T.d_mesh) cudaFree(T.d_mesh);
+  T.d_mesh = nullptr;
+  T.n_verts = 0;
+  CK(cudaMalloc(&T.d_mesh, rec.size() * sizeof(float4)));
+  CK(cudaMemcpy(T.d_mesh, rec.data(), rec.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  T.n_verts = n_verts;
+  CK(upload_types(ctx));  // bumps the version: plans rebuild their vertex offsets
+  return ANIM_OK;
+}
+
+int anim_plan_vertex_offsets(anim_ctx *ctx, const anim_plan *plan, int64_t *out) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (!out) return fail(ctx, ANIM_EINVAL, "out is NULL");
+  memcpy(out, plan->vert_off.data(), plan->vert_off.size() * sizeof(int64_t));
   return ANIM_OK;
 }
 
@@ -1163,6 +1247,48 @@ int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_tim
   rc = anim_frame_build_queue(ctx, plan, d_time, stream);
   if (rc) return rc;
   return anim_frame_run_queue(ctx, plan, d_time, d_blend_w, d_skin, stream);
+}
+
+int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
+                                float *d_skin, float *d_verts, void *stream) {
+  int rc = frame_checks(ctx, plan, d_time);
+  if (rc || plan->n_chars == 0) return rc;
+  if (!d_blend_w || !d_verts) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_verts) || (d_skin && !aligned16(d_skin)) || !aligned4(d_blend_w))
+    return fail(ctx, ANIM_EINVAL, "d_verts, d_skin must be 16-byte aligned, d_blend_w 4-byte aligned");
+  const bool own = plan->n_slots_walk > 0;  // the frame's layout gives types to the walk kernel
+  BucketArgs bk{};
+  bk.ranges = own ? plan->d_ranges_cta : plan->d_ranges;
+  bk.n_ranges = own ? plan->n_ranges_cta : plan->n_ranges;
+  bk.n_slots = own ? plan->n_slots_cta : plan->n_slots;
+  bk.type_chars = plan->d_type_chars;
+  bk.time = d_time;
+  bk.types = ctx->d_types;
+  bk.cap = own ? plan->d_cap_cta : plan->d_cap;
+  bk.sorted = plan->d_sorted;
+  bk.items = plan->d_items_frame;
+  bk.queue_head = plan->d_queue;
+  bk.status = ctx->d_status;
+  CK(launch_bucket(bk, (cudaStream_t)stream));
+  ScanArgs a{};
+  a.types = ctx->d_types;
+  a.items = plan->d_items_frame;
+  a.n_items = bk.n_slots;
+  a.item_chars = plan->d_sorted;
+  a.row_off = plan->d_row_off;
+  a.queue_head = plan->d_queue;
+  a.done = plan->d_queue + 1;
+  a.status = ctx->d_status;
+  a.time = d_time;
+  a.blend_w = d_blend_w;
+  a.skin = d_skin;
+  a.verts = d_verts;
+  a.vert_off = plan->d_vert_off;
+  LaunchCfg cfg = plan->cfg_scan;
+  cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
+  cfg.smem = plan->smem_frame;
+  CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
+  return ANIM_OK;
 }
 
 int anim_evaluate_frame_levelsync(anim_ctx *ctx, const anim_plan *plan, const float *d_time,

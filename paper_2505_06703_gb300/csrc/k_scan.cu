@@ -37,6 +37,42 @@ __device__ __forceinline__ Aff sample_local(const KeyRecs &r, float al, float w,
   return aff_from_qt(q, tx, ty, tz);
 }
 
+// Linear blend skinning of the item's characters: vertex v of character c
+// goes to sum_k w_k S_{b_k} [p; 1] with normal normalize(sum_k w_k R_{b_k} n)
+// (rigid skin matrices; zero weights skipped), written as 6 floats at the
+// character's vertex offset.  Consecutive threads take consecutive vertices.
+__device__ __forceinline__ void skin_mesh(const ItemBuf &b, const float4 *P, int cs4, float *verts, int tid) {
+  const int nv = b.T.n_verts;
+  const float4 *mesh = b.T.mesh;
+  for (int c = 0; c < b.C; ++c) {
+    const float4 *Sc = P + c * cs4;
+    float2 *out = reinterpret_cast<float2 *>(verts + b.voff[c] * 6);
+    for (int v = tid; v < nv; v += kComputeThreads) {
+      const float4 r0 = __ldg(mesh + 3 * v), r1 = __ldg(mesh + 3 * v + 1), r2 = __ldg(mesh + 3 * v + 2);
+      const float w[4] = {r1.z, r1.w, r2.x, r2.y};
+      const uint32_t b01 = __float_as_uint(r2.z), b23 = __float_as_uint(r2.w);
+      const int bone[4] = {(int)(b01 & 0xFFFFu), (int)(b01 >> 16), (int)(b23 & 0xFFFFu), (int)(b23 >> 16)};
+      float px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (w[k] == 0.f) continue;
+        const Aff S = lds_aff(Sc + 3 * bone[k]);
+        px = fmaf(w[k], fmaf(S.r0.x, r0.x, fmaf(S.r0.y, r0.y, fmaf(S.r0.z, r0.z, S.r0.w))), px);
+        py = fmaf(w[k], fmaf(S.r1.x, r0.x, fmaf(S.r1.y, r0.y, fmaf(S.r1.z, r0.z, S.r1.w))), py);
+        pz = fmaf(w[k], fmaf(S.r2.x, r0.x, fmaf(S.r2.y, r0.y, fmaf(S.r2.z, r0.z, S.r2.w))), pz);
+        nx = fmaf(w[k], fmaf(S.r0.x, r0.w, fmaf(S.r0.y, r1.x, S.r0.z * r1.y)), nx);
+        ny = fmaf(w[k], fmaf(S.r1.x, r0.w, fmaf(S.r1.y, r1.x, S.r1.z * r1.y)), ny);
+        nz = fmaf(w[k], fmaf(S.r2.x, r0.w, fmaf(S.r2.y, r1.x, S.r2.z * r1.y)), nz);
+      }
+      const float l2 = nx * nx + ny * ny + nz * nz;
+      const float inv = l2 > 0.f ? rsqrtf(l2) : 0.f;
+      out[3 * v] = make_float2(px, py);
+      out[3 * v + 1] = make_float2(pz, nx * inv);
+      out[3 * v + 2] = make_float2(ny * inv, nz * inv);
+    }
+  }
+}
+
 // Persistent kernel.  Work item = C characters of one type (for the frame:
 // characters sharing the key index k0, so they read the same key records).
 // Compute warps run passes 1a/1b/2/3 in shared memory and thread 0 streams
@@ -53,7 +89,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
 
   if (tid >= kComputeThreads) {
     producer_loop<MODE>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time,
-                        a.blend_w, a.status);
+                        a.blend_w, a.status, a.vert_off);
     return;
   }
 
@@ -133,13 +169,16 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     }
     fence_proxy_async_smem();
     compute_sync();
-    if (tid == 0) {
-      float *dst = SKIN ? a.skin : a.model;
+    float *dst = SKIN ? a.skin : a.model;
+    if (tid == 0 && dst) {
       const uint32_t bytes = (uint32_t)n * 48u;
       for (int c = 0; c < C; ++c) bulk_store(dst + b.off[c] * 12, P + c * cs4, bytes);
       bulk_commit();
       pending = true;
     }
+    // ---- pass 4 (frame with skinning): linear blend skinning of the
+    // characters' meshes from the skin matrices still in shared memory
+    if (MODE == 0 && SKIN && a.verts) skin_mesh(b, P, cs4, a.verts, tid);
     cur ^= 1;
     handoff_sync();
   }

@@ -58,6 +58,7 @@ struct ItemBuf {
   int C, k0, type;
   int cgroups, cpt;          // pass 3: character groups and characters per group
   long long off[kCMax];      // first row of each character
+  long long voff[kCMax];     // first skinned vertex of each character (frame with skinning)
   int cid[kCMax];
   float alpha[kCMax];        // frame: fraction between keys k0 and k0+1
   float blend[kCMax];        // frame: clip blend weight
@@ -67,14 +68,15 @@ static_assert(2 * sizeof(ItemBuf) + 2048 <= kStaticSmemAllowance, "item buffers 
 template <int MODE>
 __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &wi, const TypeDev *types,
                                            const int32_t *item_chars, const int64_t *row_off, const float *time,
-                                           const float *blend_w, int *status);
+                                           const float *blend_w, int *status, const int64_t *vert_off = nullptr);
 
 // Producer warp: grab the next item from the queue and stage its data.
 // MODE 0 (frame) also computes each character's key fraction.
 template <int MODE>
 __device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_items, const WorkItem *items,
                                            const TypeDev *types, const int32_t *item_chars, const int64_t *row_off,
-                                           const float *time, const float *blend_w, int *status) {
+                                           const float *time, const float *blend_w, int *status,
+                                           const int64_t *vert_off) {
   const int lane = threadIdx.x & 31;
   int it = 0;
   WorkItem wi;
@@ -89,14 +91,14 @@ __device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_it
     wi = items[it];
     if (wi.count > 0) break;
   }
-  stage_item<MODE>(b, it, wi, types, item_chars, row_off, time, blend_w, status);
+  stage_item<MODE>(b, it, wi, types, item_chars, row_off, time, blend_w, status, vert_off);
 }
 
 // One warp stages work item `it` (descriptor wi) into b.
 template <int MODE>
 __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &wi, const TypeDev *types,
                                            const int32_t *item_chars, const int64_t *row_off, const float *time,
-                                           const float *blend_w, int *status) {
+                                           const float *blend_w, int *status, const int64_t *vert_off) {
   const int lane = threadIdx.x & 31;
   const int *src = reinterpret_cast<const int *>(types + wi.type);
   int *dst = reinterpret_cast<int *>(&b.T);
@@ -106,6 +108,7 @@ __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &w
     const int cid = __ldg(item_chars + wi.start + c);
     b.cid[c] = cid;
     b.off[c] = row_off[cid];
+    if (vert_off) b.voff[c] = vert_off[cid];
     if (MODE == 0) {
       const float tm = __ldg(time + cid);
       float al = 0.f;
@@ -141,14 +144,16 @@ template <int MODE>
 __device__ __forceinline__ void producer_loop(ItemBuf *bufs, int *queue_head, int n_items, const WorkItem *items,
                                               const TypeDev *types, const int32_t *item_chars,
                                               const int64_t *row_off, const float *time, const float *blend_w,
-                                              int *status) {
+                                              int *status, const int64_t *vert_off = nullptr) {
   int cur = 0;
-  fetch_item<MODE>(bufs[0], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status);
+  fetch_item<MODE>(bufs[0], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status,
+                   vert_off);
   __threadfence_block();
   handoff_sync();
   while (bufs[cur].item >= 0) {
     cur ^= 1;
-    fetch_item<MODE>(bufs[cur], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status);
+    fetch_item<MODE>(bufs[cur], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status,
+                     vert_off);
     __threadfence_block();
     handoff_sync();
   }

@@ -21,6 +21,9 @@ def setup(w: dict, device: int = 0, with_clips: bool = True):
         for i, t in zip(ids, types):
             if "keys" in t:
                 ctx.upload_clips(i, t["keys"], t["rate_hz"])
+    for i, t in zip(ids, types):
+        if "mesh" in t:
+            ctx.upload_mesh(i, t["mesh"])
     plan = ctx.plan(np.asarray(ids, np.int32)[w["char_type"]])
     return ctx, plan
 

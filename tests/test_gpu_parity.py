@@ -357,6 +357,43 @@ def test_paper_algorithms_parity(torch, algorithm):
                                  _gpu.cuda(np.zeros((4096, 3))))
 
 
+@pytest.mark.parametrize("walk", [0, 1])
+def test_skinned_frame(torch, walk):
+    """Frame + fused linear blend skinning against the oracle's skinning of
+    the oracle's skin matrices: bipeds and the 1,024-joint chain with
+    1,500-vertex meshes, the five mixed types with 300-vertex meshes and one
+    type left without a mesh; with and without the skin matrices written."""
+    w2 = synth.with_meshes(synth.subset(synth.config2(), list(range(0, 4096, 64)) + [4096]), n_verts=1500, seed=21)
+    w3 = synth.subset(synth.config3(), list(range(0, 10000, 50)))
+    w3 = synth.with_meshes(w3, n_verts=300, seed=22)
+    w3["types"][2] = {k: v for k, v in w3["types"][2].items() if k != "mesh"}
+    for w in (w2, w3):
+        types = w["types"]
+        S_ref = oracle.frame(w)
+        V_ref = oracle.skin_vertices(w, S_ref)
+        ctx, plan = _gpu.setup(w)
+        sched = ctx.get_schedule(plan)
+        ctx.set_schedule(plan, sched[:3] + [walk, sched[4]])
+        voff = ctx.vertex_offsets(plan)
+        assert list(voff) == list(oracle.vertex_offsets(w["char_type"], types))
+        tm, wt = _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])
+        skin = torch.empty((plan.total, 12), device="cuda")
+        v1 = ctx.evaluate_frame_skinned(plan, tm, wt, skin=skin).cpu().numpy()[:int(voff[-1])]
+        v2 = ctx.evaluate_frame_skinned(plan, tm, wt).cpu().numpy()[:int(voff[-1])]
+        _gpu.assert_skin_close(skin.cpu().numpy(), S_ref, w)
+        for v in (v1, v2):
+            for c, ty in enumerate(w["char_type"]):
+                sl = slice(voff[c], voff[c + 1])
+                tol = 2 * _gpu.tol_for_depth(types[ty]["depth"])
+                assert np.abs(v[sl] - V_ref[sl]).max(initial=0.0) <= tol, (c, ty)
+        # the plain frame still works on the same plan afterwards
+        _gpu.assert_skin_close(run_frame_on(ctx, plan, w), S_ref, w)
+
+
+def run_frame_on(ctx, plan, w):
+    return ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])).cpu().numpy()
+
+
 def test_empty_plan_and_errors(torch):
     import paper_2505_06703_gb300 as pk
     rng = np.random.default_rng(5)
