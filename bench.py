@@ -368,6 +368,7 @@ def run_ours(args) -> dict:
         if not args.schedule:  # the extra workloads run the autotuner
             result["frame_mixed"] = run_mixed_frame(local, dev, world, peak)
             result["ik"] = run_ik(local, dev, world, peak)
+            result["frame_skinned"] = run_skinned_frame(local, dev, world, peak)
             cmp_ = time_forward_methods(rank_workload(rank), local, dev, world)
             result["scan_comparison"] = {
                 "workload": "forward from local poses (scan + bind) on the frame's 2,098,176 joints",
@@ -416,6 +417,49 @@ def run_mixed_frame(device, dev, world, peak) -> dict:
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes": alg,
                          "note": "whole frame (work queue + kernels), frames back to back in one CUDA graph"}}
+
+
+def run_skinned_frame(device, dev, world, peak) -> dict:
+    """The frame with linear blend skinning fused in: the frame's characters
+    with a 1,500-vertex mesh per type (about 3,000 faces), positions and
+    normals written, skin matrices kept on chip; frames back to back in one
+    CUDA graph, vertex buffers rotated past the L2 size."""
+    import torch
+    w = synth.with_meshes(synth.config2(), n_verts=1500)
+    ctx, plan = setup_ctx(w, device)
+    for i, t in enumerate(w["types"]):
+        ctx.upload_mesh(i, t["mesh"])
+    ctx.tune(plan, 0)
+    nv = int(ctx.vertex_offsets(plan)[-1])
+    n_out = max(2, math.ceil(2.5 * L2_BYTES / (nv * 24)))
+    outs = [torch.empty((nv, 6), dtype=torch.float32, device=dev) for _ in range(n_out)]
+    tm = torch.as_tensor(w["time"], device=dev)
+    bw = torch.as_tensor(w["weight"], device=dev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for o in outs:
+            ctx.evaluate_frame_skinned(plan, tm, bw, verts=o)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for o in outs:
+            ctx.evaluate_frame_skinned(plan, tm, bw, verts=o)
+    torch.cuda.synchronize()
+    reps = 5
+    ms = aggregate_max(time_events(lambda s: graph.replay(), reps, 2), world)
+    ms_step = ms / (reps * n_out)
+    # vertices out (24 B), mesh records read once per type (48 B per vertex),
+    # the frame's tables and per-character inputs; no skin matrices written
+    alg = nv * 24 + sum(len(t["mesh"]["pos"]) * 48 for t in w["types"]) + \
+        frame_algorithmic_bytes(w) - plan.total * 48
+    achieved = alg / (ms_step / 1e3) / 1e9
+    return {"value": world * nv / (ms_step / 1e3), "unit": "skinned vertices/s", "ms_per_step": ms_step,
+            "joints_per_s": world * plan.total / (ms_step / 1e3), "vertices": nv,
+            "workload": "frame + linear blend skinning: the frame's 4,097 characters, 1,500-vertex mesh per type, "
+                        "4 bones per vertex, positions + normals out, skin matrices not written",
+            "schedule": ctx.get_schedule(plan),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes": alg}}
 
 
 def run_ik(device, dev, world, peak) -> dict:

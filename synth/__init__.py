@@ -199,21 +199,36 @@ def make_type(parents: np.ndarray, rng: np.random.Generator, *, with_clips: bool
     return typ
 
 
-def make_mesh(n_joints: int, n_verts: int, rng: np.random.Generator, max_influences: int = 4) -> dict:
-    """A synthetic skinned mesh in bind space: positions uniform in
-    [-0.5, 0.5]^3, unit normals uniform on the sphere, up to 4 distinct bones
-    per vertex with positive weights summing to 1 (a quarter of the vertices
-    use fewer influences; the unused slots have weight 0)."""
+def make_mesh(parents: np.ndarray, n_verts: int, rng: np.random.Generator, max_influences: int = 4) -> dict:
+    """A synthetic skinned mesh in bind space, laid out the way exporters
+    write one: vertices grouped by a home joint in joint order, each
+    weighted to the home joint and its nearest relatives (parent,
+    grandparent, first child), weights positive, decreasing away from the
+    home joint and summing to 1 (a quarter of the vertices use fewer
+    influences; unused slots have weight 0).  Positions uniform in
+    [-0.5, 0.5]^3, unit normals uniform on the sphere."""
+    parents = np.asarray(parents)
+    n = len(parents)
+    first_child = np.full(n, -1)
+    for j in range(n - 1, 0, -1):
+        if parents[j] >= 0:
+            first_child[parents[j]] = j
     pos = rng.uniform(-0.5, 0.5, size=(n_verts, 3))
     nrm = rng.normal(size=(n_verts, 3))
     nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
-    k = min(max_influences, n_joints)
     bones = np.zeros((n_verts, 4), np.int32)
     wts = np.zeros((n_verts, 4))
     for v in range(n_verts):
+        home = v * n // n_verts
+        cand = [home]
+        p = int(parents[home])
+        for r in (p, int(parents[p]) if p >= 0 else -1, int(first_child[home])):
+            if r >= 0 and r not in cand:
+                cand.append(r)
+        k = min(max_influences, len(cand))
         m = int(rng.integers(1, k + 1)) if rng.uniform() < 0.25 else k
-        bones[v, :m] = rng.choice(n_joints, size=m, replace=False)
-        w = rng.uniform(0.05, 1.0, size=m)
+        bones[v, :m] = cand[:m]
+        w = np.sort(rng.uniform(0.05, 1.0, size=m))[::-1]
         wts[v, :m] = w / w.sum()
     return {"pos": pos.astype(np.float32), "nrm": nrm.astype(np.float32), "bones": bones,
             "weights": wts.astype(np.float32)}
@@ -224,7 +239,7 @@ def with_meshes(w: dict, n_verts: int = 1500, seed: int = 11) -> dict:
     default: about 3,000 faces, the top of the paper's Table 1 range)."""
     rng = np.random.default_rng(seed)
     w = dict(w)
-    w["types"] = [dict(t, mesh=make_mesh(len(t["parents"]), n_verts, rng)) for t in w["types"]]
+    w["types"] = [dict(t, mesh=make_mesh(t["parents"], n_verts, rng)) for t in w["types"]]
     return w
 
 

@@ -24,7 +24,8 @@ import synth
 
 
 def _mesh(rng, n_joints, n_verts, k=4):
-    return synth.make_mesh(n_joints, n_verts, rng, max_influences=k)
+    # bones drawn over a random tree of n_joints (any valid ids will do)
+    return synth.make_mesh(synth.random_tree(n_joints, max(2, n_joints // 2), rng), n_verts, rng, max_influences=k)
 
 
 def _rigid(rng, n):
