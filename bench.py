@@ -537,7 +537,7 @@ def run_ik(device, dev, world, peak) -> dict:
                          "note": "108 B per active joint (q, t, m, v in; q, m, v out) + targets"}}
 
 
-def time_forward_methods(w: dict, device: int, dev: str, world: int, algs=(1, 2, 3, 4)) -> dict:
+def time_forward_methods(w: dict, device: int, dev: str, world: int, algs=(1, 2, 3, 4, 5)) -> dict:
     """Hierarchy-Scan + bind from given local poses on workload w: our
     autotuned forward kernel, the plain level-synchronous kernel and the
     paper's Algorithms 1-4 (one CTA per character, one thread per joint), each
@@ -553,7 +553,8 @@ def time_forward_methods(w: dict, device: int, dev: str, world: int, algs=(1, 2,
     methods = {"ours": lambda o: ctx.forward_local(plan, q, t, skin=True),
                "levelsync": lambda o: ctx.forward_local(plan, q, t, levelsync=True)}
     for a in algs:
-        methods[f"paper_alg{a}"] = (lambda a: lambda o: ctx.forward_local_paper(plan, a, q, t, out=o))(a)
+        name = f"paper_alg{a}" if a <= 4 else "leaf_walk"
+        methods[name] = (lambda a: lambda o: ctx.forward_local_paper(plan, a, q, t, out=o))(a)
     res = {}
     for name, fn in methods.items():
         stream = torch.cuda.Stream()

@@ -201,7 +201,9 @@ ANIM_API int anim_forward_local_levelsync(anim_ctx *ctx, const anim_plan *plan, 
  * 6 in-block doubling rounds, then a walk over the nearest out-of-block
  * ancestors' partial products (Sec. 3.2.1, Alg. 3); 4: a joint and up to 7
  * in-block ancestors serially, up to 7 jumps of stride 8, then the
- * out-of-block walk (Sec. 3.2.2, Alg. 4).  Same inputs and outputs as
+ * out-of-block walk (Sec. 3.2.2, Alg. 4); 5: threads for the leaf joints
+ * only, each composing down its root path and writing every joint on it
+ * (the scheme Sec. 2 attributes to KIYA).  Same inputs and outputs as
  * anim_forward_local.  ANIM_EUNSUPPORTED if a type of the plan has more than
  * 1,024 joints; ANIM_EINVAL for another algorithm number. */
 ANIM_API int anim_forward_local_paper(anim_ctx *ctx, const anim_plan *plan, int algorithm, const float *d_q,

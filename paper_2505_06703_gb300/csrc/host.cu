@@ -1371,7 +1371,7 @@ int anim_forward_local_paper(anim_ctx *ctx, const anim_plan *plan, int algorithm
                              const float *d_t, float *d_skin, void *stream) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
-  if (algorithm < 1 || algorithm > 4) return fail(ctx, ANIM_EINVAL, "algorithm must be 1, 2, 3 or 4");
+  if (algorithm < 1 || algorithm > 5) return fail(ctx, ANIM_EINVAL, "algorithm must be in 1..5");
   if (plan->n_chars == 0) return ANIM_OK;
   if (!d_q || !d_t || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
   if (!aligned16(d_q) || !aligned16(d_skin) || !aligned4(d_t))

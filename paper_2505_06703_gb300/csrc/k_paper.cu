@@ -15,6 +15,11 @@
 //   Alg. 4 (Sec. 3.2.2): a joint and up to 7 in-block ancestors serially,
 //     barrier, up to 7 jumps of stride 8 over those partials, barrier, then
 //     the out-of-block walk of Alg. 3.
+//   KIYA's scheme (Sec. 2, described in words only; numbered 5 here): threads
+//     for the leaf joints only; each leaf's thread records its root path,
+//     then composes down it, writing the model pose of every joint on the
+//     path (ancestors shared by several leaves are written with equal
+//     values by each of them).
 // Then the Bind MeshPose product S_j = M_j B_j, stored from registers.
 #include <cuda_runtime.h>
 
@@ -55,7 +60,28 @@ __global__ void k_paper(const PaperArgs a) {
   __syncthreads();
 
   const float4 *R = M0;  // the buffer holding the model poses at the end
-  if (a.algo == 1) {
+  if (a.algo == 5) {
+    // leaves: joints no other joint names as parent (flags in p0)
+    for (int j = tid; j < n; j += nt) p0[j] = 0;
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      const int p = __ldg(par + j);
+      if (p >= 0) p0[p] = 1;
+    }
+    __syncthreads();
+    int16_t path[kPaperMaxJoints];  // root path of the leaf (local memory)
+    for (int j = tid; j < n; j += nt) {
+      if (p0[j]) continue;
+      int d = 0;
+      for (int u = j; u >= 0; u = __ldg(par + u)) path[d++] = (int16_t)u;
+      Aff m = lds_aff(Lm + 3 * path[d - 1]);
+      sts_aff(M0 + 3 * path[d - 1], m);
+      for (int k = d - 2; k >= 0; --k) {
+        m = aff_mul(m, lds_aff(Lm + 3 * path[k]));
+        sts_aff(M0 + 3 * path[k], m);
+      }
+    }
+  } else if (a.algo == 1) {
     for (int j = tid; j < n; j += nt) {
       Aff m = lds_aff(Lm + 3 * j);
       for (int p = __ldg(par + j); p >= 0; p = __ldg(par + p)) m = aff_mul(lds_aff(Lm + 3 * p), m);

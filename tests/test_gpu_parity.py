@@ -327,9 +327,10 @@ def test_edge_types_frame_and_local(torch):
     assert (np.abs(gt.cpu().numpy() - dt_ref).max(axis=1) <= tol).all()
 
 
-@pytest.mark.parametrize("algorithm", [1, 2, 3, 4])
+@pytest.mark.parametrize("algorithm", [1, 2, 3, 4, 5])
 def test_paper_algorithms_parity(torch, algorithm):
-    """The paper's Algorithms 1-4 as GPU kernels give the oracle's skin
+    """The paper's Algorithms 1-4 and the leaf walk it describes (5) as GPU
+    kernels give the oracle's skin
     matrices: the 64-joint trees of the plain forward workload, the biped
     (depth 70), the 256-joint depth-96 tree, a 1,000-joint tree numbered in
     random topological order (blocks of 64 indices span many subtrees) and a
