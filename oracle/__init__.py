@@ -81,6 +81,10 @@ def _load():
                                    c_double, c_double, c_double, d, d]
         _lib.oracle_ik.restype = c_int
         _lib.oracle_lbs.argtypes = [c_int, f, f, i32, f, d, d]
+        _lib.oracle_sample_layers.argtypes = [c_int, c_int, c_int, c_float, f, c_void_p, c_float, f, c_float, d, d]
+        _lib.oracle_frame_layers.argtypes = [c_int, i32, i32, d, f, i64, i32, i32, f, f, i64, c_int64, i32, f, f, f,
+                                             i64, d]
+        _lib.oracle_frame_layers.restype = c_int
     return _lib
 
 
@@ -310,3 +314,49 @@ def skin_vertices(w: dict, skin) -> np.ndarray:
         if voff[c + 1] > voff[c]:
             out[voff[c]:voff[c + 1]] = lbs(types[int(ty)]["mesh"], skin[off[c]:off[c + 1]])
     return out
+
+
+def sample_layers(keys: np.ndarray, rate: float, time: float, weights, add_keys=None, add_w: float = 0.0):
+    """Layered blend of one character's joints: (q [n][4], t [n][3]) fp64.
+    keys [n_clips][n_keys][n][8] (n_clips <= 4), weights [n_clips], optional
+    additive layer add_keys [n_keys][n][8] applied with weight add_w."""
+    lib = _load()
+    k = _f32(keys)
+    nc, nk, n = k.shape[:3]
+    wts = _f32(np.resize(np.asarray(weights, np.float32), 4))
+    ak = _f32(add_keys) if add_keys is not None else None
+    q, t = np.empty((n, 4)), np.empty((n, 3))
+    lib.oracle_sample_layers(n, nc, nk, float(rate), _p(k, c_float),
+                             ak.ctypes.data_as(c_void_p) if ak is not None else None, float(time), _p(wts, c_float),
+                             float(add_w), _p(q, c_double), _p(t, c_double))
+    return q, t
+
+
+def frame_layers(w: dict):
+    """Skin matrices [sum][3][4] of a workload with per-character clip
+    weights w["weights"] [n_chars][4] and additive weights w["add_w"];
+    types may carry "add_keys" [n_keys][n][8]."""
+    lib = _load()
+    types = w["types"]
+    T = _Types(types)
+    B = inverse_binds(types)
+    keys = [_f32(t["keys"]).ravel() for t in types]
+    key_off = _i64(np.concatenate([[0], np.cumsum([k.size for k in keys])[:-1]]))
+    keys_cat = _f32(np.concatenate(keys))
+    adds = [_f32(t["add_keys"]).ravel() if "add_keys" in t else np.zeros(0, np.float32) for t in types]
+    add_cat = _f32(np.concatenate(adds)) if sum(a.size for a in adds) else _f32(np.zeros(1))
+    pos = np.concatenate([[0], np.cumsum([a.size for a in adds])[:-1]])
+    add_off = _i64([pos[i] if "add_keys" in t else -1 for i, t in enumerate(types)])
+    n_clips = _i32([t["keys"].shape[0] for t in types])
+    n_keys = _i32([t["keys"].shape[1] for t in types])
+    rate = _f32([t["rate_hz"] for t in types])
+    ct, tm = _i32(w["char_type"]), _f32(w["time"])
+    wts, aw = _f32(w["weights"]).reshape(-1, 4), _f32(w["add_w"])
+    off = offsets(ct, types)
+    skin = np.empty((int(off[-1]), 12))
+    _check(lib.oracle_frame_layers(T.n, _p(T.counts, c_int32), _p(T.parents, c_int32), _p(B, c_double),
+                                   _p(keys_cat, c_float), _p(key_off, c_int64), _p(n_clips, c_int32),
+                                   _p(n_keys, c_int32), _p(rate, c_float), _p(add_cat, c_float), _p(add_off, c_int64),
+                                   len(ct), _p(ct, c_int32), _p(tm, c_float), _p(wts, c_float), _p(aw, c_float),
+                                   _p(off, c_int64), _p(skin, c_double)), "frame_layers")
+    return skin.reshape(-1, 3, 4)

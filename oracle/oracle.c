@@ -599,3 +599,99 @@ void oracle_lbs(int n_verts, const float *pos, const float *nrm, const int32_t *
     }
   }
 }
+
+/* Hamilton product a b of quaternions stored (x, y, z, w). */
+static void quat_mul(const double *a, const double *b, double *r) {
+  r[0] = a[3] * b[0] + a[0] * b[3] + a[1] * b[2] - a[2] * b[1];
+  r[1] = a[3] * b[1] - a[0] * b[2] + a[1] * b[3] + a[2] * b[0];
+  r[2] = a[3] * b[2] + a[0] * b[1] - a[1] * b[0] + a[2] * b[3];
+  r[3] = a[3] * b[3] - a[0] * b[0] - a[1] * b[1] - a[2] * b[2];
+}
+
+/*
+ * Layered blend (the paper asks the method to keep the state-machine
+ * blending of clips, Sec. 2, without giving one; this is the reading used):
+ * up to 4 clips sampled at the character's time as in oracle_sample_local,
+ * rotations blended by incremental slerp -- q = q_0, W = w_0, then for each
+ * further clip i: W += w_i and, if W > 0, q = slerp(q, q_i, w_i / W) -- and
+ * translations by their weighted mean (t_0 when every weight is 0); two
+ * clips with weights (1 - w, w) give the two-clip blend.  An optional
+ * additive layer (add_keys [key][joint][8], same key count and rate) sampled
+ * at the same time is applied on top with weight a:
+ *     q <- q * slerp(identity, q_a, a),   t <- t + a t_a.
+ */
+void oracle_sample_layers(int n, int n_clips, int n_keys, float rate, const float *keys, const float *add_keys,
+                          float time, const float *weights, float add_w, double *q_out, double *t_out) {
+  int k0, k1;
+  double alpha;
+  key_pos(time, rate, n_keys, &k0, &k1, &alpha);
+  for (int j = 0; j < n; ++j) {
+    double q[4], t[3] = {0.0, 0.0, 0.0}, W = 0.0;
+    for (int c = 0; c < n_clips; ++c) {
+      const float *r0 = keys + (((size_t)c * n_keys + k0) * n + j) * 8;
+      const float *r1 = keys + (((size_t)c * n_keys + k1) * n + j) * 8;
+      double a[4] = {r0[0], r0[1], r0[2], r0[3]}, b[4] = {r1[0], r1[1], r1[2], r1[3]}, qc[4];
+      oracle_slerp(a, b, alpha, qc);
+      const double w = weights[c];
+      if (c == 0) {
+        for (int k = 0; k < 4; ++k) q[k] = qc[k];
+      } else if (W + w > 0.0) {
+        double r[4];
+        oracle_slerp(q, qc, w / (W + w), r);
+        for (int k = 0; k < 4; ++k) q[k] = r[k];
+      }
+      W += w;
+      for (int k = 0; k < 3; ++k) t[k] += w * ((1.0 - alpha) * (double)r0[4 + k] + alpha * (double)r1[4 + k]);
+      if (c == 0 && W == 0.0)
+        for (int k = 0; k < 3; ++k) t[k] = 0.0;
+    }
+    if (W > 0.0) {
+      for (int k = 0; k < 3; ++k) t[k] /= W;
+    } else {
+      const float *r0 = keys + ((size_t)k0 * n + j) * 8, *r1 = keys + ((size_t)k1 * n + j) * 8;
+      for (int k = 0; k < 3; ++k) t[k] = (1.0 - alpha) * (double)r0[4 + k] + alpha * (double)r1[4 + k];
+    }
+    if (add_keys) {
+      const float *r0 = add_keys + ((size_t)k0 * n + j) * 8, *r1 = add_keys + ((size_t)k1 * n + j) * 8;
+      double a[4] = {r0[0], r0[1], r0[2], r0[3]}, b[4] = {r1[0], r1[1], r1[2], r1[3]}, qa[4], qs[4], r[4];
+      const double id[4] = {0.0, 0.0, 0.0, 1.0};
+      oracle_slerp(a, b, alpha, qa);
+      oracle_slerp(id, qa, add_w, qs);
+      quat_mul(q, qs, r);
+      for (int k = 0; k < 4; ++k) q[k] = r[k];
+      for (int k = 0; k < 3; ++k) t[k] += add_w * ((1.0 - alpha) * (double)r0[4 + k] + alpha * (double)r1[4 + k]);
+    }
+    for (int k = 0; k < 4; ++k) q_out[4 * (size_t)j + k] = q[k];
+    for (int k = 0; k < 3; ++k) t_out[3 * (size_t)j + k] = t[k];
+  }
+}
+
+/* The frame with layered blending: per character its clip weights
+ * weights[c][4] and additive weight add_w[c]; add_off[type] < 0: no
+ * additive layer. */
+int oracle_frame_layers(int n_types, const int32_t *counts, const int32_t *parents_cat, const double *invbind_cat,
+                        const float *keys_cat, const int64_t *key_off, const int32_t *n_clips,
+                        const int32_t *n_keys, const float *rate, const float *add_cat, const int64_t *add_off,
+                        int64_t n_chars, const int32_t *char_type, const float *time, const float *weights,
+                        const float *add_w, const int64_t *out_off, double *skin) {
+  int64_t *toff = type_offsets(n_types, counts);
+  int maxn = 0;
+  for (int t = 0; t < n_types; ++t) maxn = counts[t] > maxn ? counts[t] : maxn;
+  double *q = (double *)malloc(sizeof(double) * 4 * (size_t)maxn);
+  double *tr = (double *)malloc(sizeof(double) * 3 * (size_t)maxn);
+  double *L = (double *)malloc(sizeof(double) * 12 * (size_t)maxn);
+  double *M = (double *)malloc(sizeof(double) * 12 * (size_t)maxn);
+  if (!toff || !q || !tr || !L || !M) { free(toff); free(q); free(tr); free(L); free(M); return -2; }
+  for (int64_t c = 0; c < n_chars; ++c) {
+    int ty = char_type[c];
+    int n = counts[ty];
+    const int32_t *par = parents_cat + toff[ty];
+    oracle_sample_layers(n, n_clips[ty], n_keys[ty], rate[ty], keys_cat + key_off[ty],
+                         add_off[ty] >= 0 ? add_cat + add_off[ty] : NULL, time[c], weights + 4 * c, add_w[c], q, tr);
+    for (int j = 0; j < n; ++j) local_matrix(q + 4 * (size_t)j, tr + 3 * (size_t)j, L + 12 * (size_t)j);
+    oracle_forward(n, par, L, M);
+    oracle_bind(n, M, invbind_cat + 12 * toff[ty], skin + 12 * out_off[c]);
+  }
+  free(toff); free(q); free(tr); free(L); free(M);
+  return 0;
+}

@@ -243,6 +243,46 @@ def with_meshes(w: dict, n_verts: int = 1500, seed: int = 11) -> dict:
     return w
 
 
+def with_layers(w: dict, n_clips: int = 4, additive: bool = True, seed: int = 31) -> dict:
+    """The workload with up to 4 clips per type (extra clips drawn like the
+    first ones: rotations within 30 degrees of identity, translations those
+    of clip 0 plus noise of 1 % of the bone scale), an optional additive
+    layer per type (rotations within 15 degrees of identity, translations
+    within 5 % of clip 0's), per-character clip weights [n_chars][4]
+    (uniform, a third of them zeroed, never all) and additive weights
+    uniform in [0, 1]."""
+    rng = np.random.default_rng(seed)
+    w = dict(w)
+    types = []
+    for t in w["types"]:
+        t = dict(t)
+        k = t["keys"]
+        nc, nk, n = k.shape[:3]
+        if n_clips > nc:
+            extra = np.zeros((n_clips - nc, nk, n, 8), np.float32)
+            for c in range(n_clips - nc):
+                for kk in range(nk):
+                    extra[c, kk, :, 0:4] = random_unit_quats(rng, n, 30.0)
+                    extra[c, kk, :, 4:7] = k[0, kk, :, 4:7] + rng.uniform(-0.01, 0.01, (n, 3)) * t["scale"]
+            t["keys"] = np.concatenate([k, extra]).astype(np.float32)
+        if additive:
+            add = np.zeros((nk, n, 8), np.float32)
+            for kk in range(nk):
+                add[kk, :, 0:4] = random_unit_quats(rng, n, 15.0)
+                add[kk, :, 4:7] = 0.05 * k[0, kk, :, 4:7] * rng.uniform(-1, 1, (n, 1))
+            t["add_keys"] = add
+        types.append(t)
+    w["types"] = types
+    m = len(w["char_type"])
+    wts = rng.uniform(0.0, 1.0, size=(m, 4))
+    wts[rng.uniform(size=(m, 4)) < 1 / 3] = 0.0
+    wts[np.arange(m), rng.integers(0, n_clips, size=m)] += 0.1
+    wts[:, n_clips:] = 0.0
+    w["weights"] = wts.astype(np.float32)
+    w["add_w"] = rng.uniform(0.0, 1.0, size=m).astype(np.float32)
+    return w
+
+
 def char_offsets(char_type: np.ndarray, types: list) -> np.ndarray:
     """Exclusive prefix of joint counts in character order (row offsets of
     each character's joints in the [sum n][...] arrays)."""
