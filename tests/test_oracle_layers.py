@@ -74,7 +74,9 @@ def test_weight_scale_does_not_matter():
     k = w["types"][0]["keys"]
     q1, t1 = oracle.sample_layers(k, 30.0, 0.77, [0.2, 0.3, 0.1, 0.4])
     q2, t2 = oracle.sample_layers(k, 30.0, 0.77, [2.0, 3.0, 1.0, 4.0])
-    np.testing.assert_allclose(q1, q2, atol=1e-12)
+    # exact in real arithmetic; the weights reach the oracle as float32, whose
+    # rounding of 0.2 and 2.0 differ by ~1e-8 relative
+    np.testing.assert_allclose(q1, q2, atol=1e-7)
     np.testing.assert_allclose(t1, t2, atol=1e-6)
 
 
