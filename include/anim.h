@@ -80,6 +80,7 @@ enum {
 /* Limits.  A skeleton type has at most ANIM_MAX_JOINTS joints. */
 #define ANIM_MAX_JOINTS 2048
 #define ANIM_MAX_KEYS 1024
+#define ANIM_MAX_CLIPS 4
 #define ANIM_MAX_VERTS (1 << 20)
 
 typedef struct anim_ctx anim_ctx;
@@ -113,11 +114,19 @@ ANIM_API int anim_create_skeletons(anim_ctx *ctx, int n_types, const int32_t *jo
 
 /* Upload the clips sampled by the Simulation stage (Sec. 1 step 1) for a
  * type: keys is host [n_clips][n_keys][n][8] = qx qy qz qw tx ty tz pad,
- * n_clips in {1, 2} (with 2 clips the frame blends clip 0 -> clip 1 by the
- * per-character weight), 2 <= n_keys <= ANIM_MAX_KEYS, keys looping with
- * period n_keys / rate_hz seconds.  Replaces earlier clips of the type.
- * Synchronous. */
+ * 1 <= n_clips <= ANIM_MAX_CLIPS (anim_evaluate_frame blends clip 0 -> clip
+ * 1 by the per-character weight; anim_evaluate_frame_layers blends all of
+ * them), 2 <= n_keys <= ANIM_MAX_KEYS, keys looping with period n_keys /
+ * rate_hz seconds.  Replaces earlier clips of the type (and drops an
+ * additive layer whose key count or rate no longer matches).  Synchronous. */
 ANIM_API int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, float rate_hz, const float *keys);
+
+/* An additive layer for a type (the paper asks for the clip blending of an
+ * animation state machine to be kept, Sec. 2, without defining layers):
+ * host keys [n_keys][n][8] in the clip format, with the clips' n_keys and
+ * rate_hz (clips first: ANIM_ESTATE otherwise); applied by
+ * anim_evaluate_frame_layers.  Synchronous. */
+ANIM_API int anim_upload_additive(anim_ctx *ctx, int32_t type_id, int n_keys, float rate_hz, const float *keys);
 
 /* A plan fixes the characters of a batch: char_type[c] (host, n_chars
  * entries) is each character's type.  The plan holds the row offsets, the
@@ -165,6 +174,20 @@ ANIM_API int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const flo
  * kernel here (the chain-walk kernel has no skinning pass). */
 ANIM_API int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const float *d_time,
                                          const float *d_blend_w, float *d_skin, float *d_verts, void *stream);
+
+/* The fused frame with layered blending: every clip of a character's type
+ * is sampled at d_time[c] (slerp between keys, lerp for translations), the
+ * rotations are blended by incremental slerp -- q = q_0, W = w_0, then for
+ * each further clip i: W += w_i and, while W > 0, q = slerp(q, q_i, w_i / W)
+ * -- and the translations by their weighted mean (clip 0's when all weights
+ * are 0); two clips with weights (1 - w, w) give anim_evaluate_frame's
+ * blend.  A type with an additive layer then takes q * slerp(1, q_a, a) and
+ * t + a t_a with a = d_add_w[c] (d_add_w NULL: a = 0).  d_weights: device
+ * [n_chars][4] float (weights of clips beyond the type's count are
+ * ignored), non-negative; d_skin as in anim_evaluate_frame.  Every type
+ * runs on the segmented kernel here. */
+ANIM_API int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float *d_time,
+                                        const float *d_weights, const float *d_add_w, float *d_skin, void *stream);
 
 /* The two launches of anim_evaluate_frame, for callers that schedule them
  * apart (e.g. to time the persistent kernel alone): build_queue buckets the

@@ -34,6 +34,8 @@ SIGNATURES = {
     "anim_upload_mesh": (c_int, [_P, c_int32, c_int, _P, _P, _P, _P]),
     "anim_plan_vertex_offsets": (c_int, [_P, _P, _P]),
     "anim_evaluate_frame_skinned": (c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "anim_upload_additive": (c_int, [_P, c_int32, c_int, c_float, _P]),
+    "anim_evaluate_frame_layers": (c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame_levelsync": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_frame_build_queue": (c_int, [_P, _P, _P, _P]),
@@ -167,6 +169,19 @@ class Context:
         nc, nk, n, eight = k.shape
         assert eight == 8
         self._ck(self.lib.anim_upload_clips(self.h, int(type_id), nc, nk, float(rate_hz), _np_ptr(k)))
+
+    def upload_additive(self, type_id: int, keys, rate_hz: float):
+        k = np.ascontiguousarray(keys, dtype=np.float32)
+        nk, n, eight = k.shape
+        assert eight == 8
+        self._ck(self.lib.anim_upload_additive(self.h, int(type_id), nk, float(rate_hz), _np_ptr(k)))
+
+    def evaluate_frame_layers(self, plan, time, weights, add_w=None, out=None, stream=None):
+        """Frame with layered blending: clip weights [n_chars, 4], additive weights [n_chars] or None."""
+        out = self._out(plan, 12, out)
+        self._ck(self.lib.anim_evaluate_frame_layers(self.h, plan.h, _dptr(time), _dptr(weights), _dptr(add_w),
+                                                     _dptr(out), _stream(stream)))
+        return out
 
     def upload_mesh(self, type_id: int, mesh: dict):
         """mesh: pos [nv,3], nrm [nv,3], bones [nv,4] int, weights [nv,4]."""

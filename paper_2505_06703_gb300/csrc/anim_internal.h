@@ -32,6 +32,7 @@ struct TypeDev {
   const uint32_t *jinfo;     // [n] segment of the joint (bits 0-15) | kJStart | kJLink
   const float4 *inv_bind;    // [n][3] rows of B_i
   const float4 *keys;        // [n_clips][n_keys][n][2]: (qx qy qz qw), (tx ty tz theta)
+  const float4 *add_keys;    // additive layer [n_keys][n][2] in the same format, or nullptr
   // adjoint: depth-first pre-order of the joints (subtrees are contiguous)
   const int32_t *dfs;        // [n] joint at pre-order slot i
   const int32_t *dfs_slot;   // [n] slot of joint j
@@ -93,7 +94,7 @@ struct WorkItem {
 constexpr int kPersistentThreads = 288;
 // One-item adjoint kernel: 4 warps, no producer; its static shared memory.
 constexpr int kAdjSmallThreads = 128;
-constexpr int kAdjSmallStatic = 3 * 1024;
+constexpr int kAdjSmallStatic = 4 * 1024;
 
 struct LaunchCfg {
   int threads;       // CTA size
@@ -128,6 +129,10 @@ struct ScanArgs {
   // normal) at the characters' vertex offsets; skin may then be nullptr
   float *verts;
   const int64_t *vert_off;  // [n_chars + 1]
+  // frame with layered blending: clip weights [n_chars][4] and additive
+  // weights [n_chars] (nullable); blend_w is unused then
+  const float *layer_w;
+  const float *add_w;
 };
 
 cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);

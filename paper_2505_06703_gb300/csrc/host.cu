@@ -392,6 +392,7 @@ struct TypeHost {
   std::vector<int32_t> gather;  // IK views only
   WalkSched ws;                 // chain-walk schedule (mode 0: not walkable)
   bool ws_done = false;
+  float4 *d_add = nullptr;      // additive layer keys [n_keys][n][2]
   float4 *d_mesh = nullptr;     // skinned mesh, 3 float4 per vertex
   int n_verts = 0;
   float4 *d_wkeys = nullptr;    // schedule-ordered key records
@@ -399,7 +400,7 @@ struct TypeHost {
   TypeDev dev{};
   ~TypeHost() {
     for (void *p : {(void *)d_tables, (void *)d_inv_bind, (void *)d_keys, (void *)d_wkeys, (void *)d_wbind,
-                    (void *)d_mesh})
+                    (void *)d_mesh, (void *)d_add})
       if (p) cudaFree(p);
   }
   cudaError_t build_tables() {
@@ -480,6 +481,7 @@ struct TypeHost {
     dev.rate = rate;
     dev.inv_bind = d_inv_bind;
     dev.keys = d_keys;
+    dev.add_keys = d_add;
     dev.wk_keys = d_wkeys;
     dev.wk_bind = d_wbind;
     dev.n_verts = n_verts;
@@ -986,7 +988,7 @@ int anim_create_skeletons(anim_ctx *ctx, int n_types, const int32_t *joint_count
 int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, float rate_hz, const float *keys) {
   if (!ctx) return ANIM_EINVAL;
   if (type_id < 0 || type_id >= (int)ctx->types.size()) return fail(ctx, ANIM_EINVAL, "type id %d unknown", type_id);
-  if (n_clips < 1 || n_clips > 2) return fail(ctx, ANIM_EINVAL, "n_clips must be 1 or 2");
+  if (n_clips < 1 || n_clips > ANIM_MAX_CLIPS) return fail(ctx, ANIM_EINVAL, "n_clips must be in [1, %d]", ANIM_MAX_CLIPS);
   if (n_keys < 2 || n_keys > ANIM_MAX_KEYS) return fail(ctx, ANIM_EINVAL, "n_keys must be in [2, %d]", ANIM_MAX_KEYS);
   if (!(rate_hz > 0.f) || !std::isfinite(rate_hz)) return fail(ctx, ANIM_EINVAL, "rate_hz must be finite and > 0");
   if (!keys) return fail(ctx, ANIM_EINVAL, "keys is NULL");
@@ -999,10 +1001,34 @@ int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, f
   CK(cudaMemcpy(T.d_keys, keys, bytes, cudaMemcpyHostToDevice));
   CK(launch_prepare_keys(T.d_keys, n_clips, n_keys, T.n, 0));
   CK(cudaDeviceSynchronize());
+  if (T.d_add && (T.n_keys != n_keys || T.rate != rate_hz)) {  // the additive layer no longer matches
+    cudaFree(T.d_add);
+    T.d_add = nullptr;
+  }
   T.n_clips = n_clips;
   T.n_keys = n_keys;
   T.rate = rate_hz;
   CK(T.build_walk_data());
+  CK(upload_types(ctx));
+  return ANIM_OK;
+}
+
+int anim_upload_additive(anim_ctx *ctx, int32_t type_id, int n_keys, float rate_hz, const float *keys) {
+  if (!ctx) return ANIM_EINVAL;
+  if (type_id < 0 || type_id >= (int)ctx->types.size()) return fail(ctx, ANIM_EINVAL, "type id %d unknown", type_id);
+  TypeHost &T = *ctx->types[type_id];
+  if (T.n_clips == 0) return fail(ctx, ANIM_ESTATE, "type %d has no clips: upload them first", type_id);
+  if (n_keys != T.n_keys || !(rate_hz == T.rate))
+    return fail(ctx, ANIM_EINVAL, "the additive layer must have the clips' key count (%d) and rate", T.n_keys);
+  if (!keys) return fail(ctx, ANIM_EINVAL, "keys is NULL");
+  CK(cudaSetDevice(ctx->device));
+  const size_t bytes = (size_t)n_keys * T.n * 32;
+  if (T.d_add) cudaFree(T.d_add);
+  T.d_add = nullptr;
+  CK(cudaMalloc(&T.d_add, bytes));
+  CK(cudaMemcpy(T.d_add, keys, bytes, cudaMemcpyHostToDevice));
+  CK(launch_prepare_keys(T.d_add, 1, n_keys, T.n, 0));
+  CK(cudaDeviceSynchronize());
   CK(upload_types(ctx));
   return ANIM_OK;
 }
@@ -1284,6 +1310,47 @@ int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const floa
   a.skin = d_skin;
   a.verts = d_verts;
   a.vert_off = plan->d_vert_off;
+  LaunchCfg cfg = plan->cfg_scan;
+  cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
+  cfg.smem = plan->smem_frame;
+  CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
+  return ANIM_OK;
+}
+
+int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_weights,
+                               const float *d_add_w, float *d_skin, void *stream) {
+  int rc = frame_checks(ctx, plan, d_time);
+  if (rc || plan->n_chars == 0) return rc;
+  if (!d_weights || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!aligned16(d_skin) || !aligned4(d_weights) || (d_add_w && !aligned4(d_add_w)))
+    return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned, d_weights and d_add_w 4-byte aligned");
+  const bool own = plan->n_slots_walk > 0;  // the frame's layout gives types to the walk kernel
+  BucketArgs bk{};
+  bk.ranges = own ? plan->d_ranges_cta : plan->d_ranges;
+  bk.n_ranges = own ? plan->n_ranges_cta : plan->n_ranges;
+  bk.n_slots = own ? plan->n_slots_cta : plan->n_slots;
+  bk.type_chars = plan->d_type_chars;
+  bk.time = d_time;
+  bk.types = ctx->d_types;
+  bk.cap = own ? plan->d_cap_cta : plan->d_cap;
+  bk.sorted = plan->d_sorted;
+  bk.items = plan->d_items_frame;
+  bk.queue_head = plan->d_queue;
+  bk.status = ctx->d_status;
+  CK(launch_bucket(bk, (cudaStream_t)stream));
+  ScanArgs a{};
+  a.types = ctx->d_types;
+  a.items = plan->d_items_frame;
+  a.n_items = bk.n_slots;
+  a.item_chars = plan->d_sorted;
+  a.row_off = plan->d_row_off;
+  a.queue_head = plan->d_queue;
+  a.done = plan->d_queue + 1;
+  a.status = ctx->d_status;
+  a.time = d_time;
+  a.skin = d_skin;
+  a.layer_w = d_weights;
+  a.add_w = d_add_w;
   LaunchCfg cfg = plan->cfg_scan;
   cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
   cfg.smem = plan->smem_frame;

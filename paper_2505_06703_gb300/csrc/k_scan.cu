@@ -37,6 +37,67 @@ __device__ __forceinline__ Aff sample_local(const KeyRecs &r, float al, float w,
   return aff_from_qt(q, tx, ty, tz);
 }
 
+// Pass 1a of the frame with layered blending: every clip of the type is
+// sampled at the character's key fraction (slerp / lerp between keys k0 and
+// k0 + 1); rotations are blended by incremental slerp (q = q_0, W = w_0, then
+// for each further clip W += w_i and q = slerp(q, q_i, w_i / W) while W > 0),
+// translations by their weighted mean (clip 0's when every weight is 0);
+// an additive layer sampled the same way multiplies on the right,
+// q * slerp(1, q_a, a), and adds a t_a.
+__device__ __forceinline__ void sample_layers_pass(const ItemBuf &b, float4 *P, int cs4, int tid) {
+  const int n = b.T.n, nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1, nc = b.T.n_clips;
+  const int CN = b.C * n;
+  const float4 *add = b.T.add_keys;
+  for (int idx = tid; idx < CN; idx += kComputeThreads) {
+    const int j = (int)b.divC.div(idx), c = idx - j * b.C;
+    const float al = b.alpha[c];
+    float4 q = make_float4(0.f, 0.f, 0.f, 1.f);
+    float tx = 0.f, ty = 0.f, tz = 0.f, t0x = 0.f, t0y = 0.f, t0z = 0.f, W = 0.f;
+    for (int i = 0; i < nc; ++i) {
+      const float4 *A0 = b.T.keys + (((size_t)i * nk + k0) * n + j) * 2;
+      const float4 *A1 = b.T.keys + (((size_t)i * nk + k1) * n + j) * 2;
+      const float4 qa0 = __ldg(A0), ta0 = __ldg(A0 + 1), qa1 = __ldg(A1), ta1 = __ldg(A1 + 1);
+      const float4 qi = slerp_pre(qa0, qa1, ta0.w, al);
+      const float ix = fmaf(al, ta1.x - ta0.x, ta0.x), iy = fmaf(al, ta1.y - ta0.y, ta0.y),
+                  iz = fmaf(al, ta1.z - ta0.z, ta0.z);
+      const float w = b.lw[c][i];
+      if (i == 0) {
+        q = qi;
+        t0x = ix;
+        t0y = iy;
+        t0z = iz;
+      } else if (W + w > 0.f) {
+        q = slerp_unit(q, qi, w / (W + w));
+      }
+      W += w;
+      tx = fmaf(w, ix, tx);
+      ty = fmaf(w, iy, ty);
+      tz = fmaf(w, iz, tz);
+    }
+    if (W > 0.f) {
+      const float inv = 1.f / W;
+      tx *= inv;
+      ty *= inv;
+      tz *= inv;
+    } else {
+      tx = t0x;
+      ty = t0y;
+      tz = t0z;
+    }
+    if (add) {
+      const float aw = b.law[c];
+      const float4 *A0 = add + ((size_t)k0 * n + j) * 2, *A1 = add + ((size_t)k1 * n + j) * 2;
+      const float4 qa0 = __ldg(A0), ta0 = __ldg(A0 + 1), qa1 = __ldg(A1), ta1 = __ldg(A1 + 1);
+      const float4 qa = slerp_pre(qa0, qa1, ta0.w, al);
+      q = qmul(q, slerp_unit(make_float4(0.f, 0.f, 0.f, 1.f), qa, aw));
+      tx = fmaf(aw, fmaf(al, ta1.x - ta0.x, ta0.x), tx);
+      ty = fmaf(aw, fmaf(al, ta1.y - ta0.y, ta0.y), ty);
+      tz = fmaf(aw, fmaf(al, ta1.z - ta0.z, ta0.z), tz);
+    }
+    sts_aff(P + c * cs4 + 3 * j, aff_from_qt(q, tx, ty, tz));
+  }
+}
+
 // Linear blend skinning of the item's characters: vertex v of character c
 // goes to sum_k w_k S_{b_k} [p; 1] with normal normalize(sum_k w_k R_{b_k} n)
 // (rigid skin matrices; zero weights skipped), written as 6 floats at the
@@ -80,7 +141,9 @@ __device__ __forceinline__ void skin_mesh(const ItemBuf &b, const float4 *P, int
 // stages the next item meanwhile.
 //   MODE 0: local poses sampled from the type's clips at each character's time;
 //   MODE 1: local poses read from q [total][4] (normalized here), t [total][3].
-template <int MODE, bool SKIN, bool MODEL, int MINB>
+// FEAT (frame only): 0 plain, 1 with the skinning pass, 2 with layered
+// blending -- separate instantiations so the plain frame carries neither.
+template <int MODE, bool SKIN, bool MODEL, int MINB, int FEAT>
 __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
@@ -89,7 +152,8 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
 
   if (tid >= kComputeThreads) {
     producer_loop<MODE>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time,
-                        a.blend_w, a.status, a.vert_off);
+                        a.blend_w, a.status, FEAT == 1 ? a.vert_off : nullptr,
+                        FEAT == 2 ? LayerIn{a.layer_w, a.add_w} : LayerIn{nullptr, nullptr});
     return;
   }
 
@@ -112,7 +176,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     // ---- pass 1a: local matrices of every (joint, character); the type's
     // tables are staged into shared memory alongside
     stage_tables(b, Lt, tid);
-    if (MODE == 0) {
+    if (MODE == 0 && FEAT == 2) {
+      sample_layers_pass(b, P, cs4, tid);
+    } else if (MODE == 0) {
       const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
       const float4 *KA0 = b.T.keys + (size_t)k0 * n * 2;
       const float4 *KA1 = b.T.keys + (size_t)k1 * n * 2;
@@ -178,7 +244,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     }
     // ---- pass 4 (frame with skinning): linear blend skinning of the
     // characters' meshes from the skin matrices still in shared memory
-    if (MODE == 0 && SKIN && a.verts) skin_mesh(b, P, cs4, a.verts, tid);
+    if (MODE == 0 && SKIN && FEAT == 1) skin_mesh(b, P, cs4, a.verts, tid);
     cur ^= 1;
     handoff_sync();
   }
@@ -186,9 +252,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   if (tid == 0 && a.done) last_cta_reset(a.queue_head, a.done);
 }
 
-template <int MODE, bool SKIN, bool MODEL, int MINB>
+template <int MODE, bool SKIN, bool MODEL, int MINB, int FEAT>
 static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  auto k = k_scan<MODE, SKIN, MODEL, MINB>;
+  auto k = k_scan<MODE, SKIN, MODEL, MINB, FEAT>;
   static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
   if (cfg.smem > set_smem) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
@@ -202,10 +268,14 @@ static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaSt
 template <int MINB>
 static cudaError_t launch_scan_m(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   const bool skin = a.skin != nullptr, model = a.model != nullptr;
-  if (mode == 0) return launch_scan_t<0, true, false, MINB>(a, cfg, st);
-  if (skin && model) return launch_scan_t<1, true, true, MINB>(a, cfg, st);
-  if (skin) return launch_scan_t<1, true, false, MINB>(a, cfg, st);
-  return launch_scan_t<1, false, true, MINB>(a, cfg, st);
+  if (mode == 0) {
+    if (a.verts) return launch_scan_t<0, true, false, MINB, 1>(a, cfg, st);
+    if (a.layer_w) return launch_scan_t<0, true, false, MINB, 2>(a, cfg, st);
+    return launch_scan_t<0, true, false, MINB, 0>(a, cfg, st);
+  }
+  if (skin && model) return launch_scan_t<1, true, true, MINB, 0>(a, cfg, st);
+  if (skin) return launch_scan_t<1, true, false, MINB, 0>(a, cfg, st);
+  return launch_scan_t<1, false, true, MINB, 0>(a, cfg, st);
 }
 
 cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {

@@ -62,13 +62,21 @@ struct ItemBuf {
   int cid[kCMax];
   float alpha[kCMax];        // frame: fraction between keys k0 and k0+1
   float blend[kCMax];        // frame: clip blend weight
+  float lw[kCMax][4];        // frame with layers: clip weights
+  float law[kCMax];          // frame with layers: additive weight
 };
 static_assert(2 * sizeof(ItemBuf) + 2048 <= kStaticSmemAllowance, "item buffers exceed the static allowance");
+
+struct LayerIn {
+  const float *w;    // [n_chars][4]
+  const float *add;  // [n_chars] or nullptr
+};
 
 template <int MODE>
 __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &wi, const TypeDev *types,
                                            const int32_t *item_chars, const int64_t *row_off, const float *time,
-                                           const float *blend_w, int *status, const int64_t *vert_off = nullptr);
+                                           const float *blend_w, int *status, const int64_t *vert_off = nullptr,
+                                           LayerIn layers = LayerIn{nullptr, nullptr});
 
 // Producer warp: grab the next item from the queue and stage its data.
 // MODE 0 (frame) also computes each character's key fraction.
@@ -76,7 +84,7 @@ template <int MODE>
 __device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_items, const WorkItem *items,
                                            const TypeDev *types, const int32_t *item_chars, const int64_t *row_off,
                                            const float *time, const float *blend_w, int *status,
-                                           const int64_t *vert_off) {
+                                           const int64_t *vert_off, LayerIn layers) {
   const int lane = threadIdx.x & 31;
   int it = 0;
   WorkItem wi;
@@ -91,14 +99,15 @@ __device__ __forceinline__ void fetch_item(ItemBuf &b, int *queue_head, int n_it
     wi = items[it];
     if (wi.count > 0) break;
   }
-  stage_item<MODE>(b, it, wi, types, item_chars, row_off, time, blend_w, status, vert_off);
+  stage_item<MODE>(b, it, wi, types, item_chars, row_off, time, blend_w, status, vert_off, layers);
 }
 
 // One warp stages work item `it` (descriptor wi) into b.
 template <int MODE>
 __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &wi, const TypeDev *types,
                                            const int32_t *item_chars, const int64_t *row_off, const float *time,
-                                           const float *blend_w, int *status, const int64_t *vert_off) {
+                                           const float *blend_w, int *status, const int64_t *vert_off,
+                                           LayerIn layers) {
   const int lane = threadIdx.x & 31;
   const int *src = reinterpret_cast<const int *>(types + wi.type);
   int *dst = reinterpret_cast<int *>(&b.T);
@@ -119,7 +128,12 @@ __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &w
         atomicOr(status, 1);
       }
       b.alpha[c] = al;
-      b.blend[c] = __ldg(blend_w + cid);
+      if (layers.w) {
+        for (int i = 0; i < 4; ++i) b.lw[c][i] = __ldg(layers.w + 4 * (size_t)cid + i);
+        b.law[c] = layers.add ? __ldg(layers.add + cid) : 0.f;
+      } else {
+        b.blend[c] = __ldg(blend_w + cid);
+      }
     }
   }
   if (lane == 0) {
@@ -144,16 +158,17 @@ template <int MODE>
 __device__ __forceinline__ void producer_loop(ItemBuf *bufs, int *queue_head, int n_items, const WorkItem *items,
                                               const TypeDev *types, const int32_t *item_chars,
                                               const int64_t *row_off, const float *time, const float *blend_w,
-                                              int *status, const int64_t *vert_off = nullptr) {
+                                              int *status, const int64_t *vert_off = nullptr,
+                                              LayerIn layers = LayerIn{nullptr, nullptr}) {
   int cur = 0;
   fetch_item<MODE>(bufs[0], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status,
-                   vert_off);
+                   vert_off, layers);
   __threadfence_block();
   handoff_sync();
   while (bufs[cur].item >= 0) {
     cur ^= 1;
     fetch_item<MODE>(bufs[cur], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status,
-                     vert_off);
+                     vert_off, layers);
     __threadfence_block();
     handoff_sync();
   }

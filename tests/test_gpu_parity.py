@@ -395,6 +395,33 @@ def run_frame_on(ctx, plan, w):
     return ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])).cpu().numpy()
 
 
+@pytest.mark.parametrize("walk", [0, 1])
+def test_layered_frame(torch, walk):
+    """Frame with up to 4 clips blended by incremental slerp and an additive
+    layer, against the oracle: the config-2 and config-3 types with 4 and 3
+    clips, one type without the additive layer; the two-clip case equals the
+    plain frame."""
+    w2 = synth.with_layers(synth.subset(synth.config2(), list(range(0, 4096, 64)) + [4096]), n_clips=4, seed=41)
+    w3 = synth.with_layers(synth.subset(synth.config3(), list(range(0, 10000, 50))), n_clips=3, seed=42)
+    w3["types"][1] = {k: v for k, v in w3["types"][1].items() if k != "add_keys"}
+    for w in (w2, w3):
+        ref = oracle.frame_layers(w)
+        ctx, plan = _gpu.setup(w)
+        sched = ctx.get_schedule(plan)
+        ctx.set_schedule(plan, sched[:3] + [walk, sched[4]])
+        got = ctx.evaluate_frame_layers(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weights"]), _gpu.cuda(w["add_w"]))
+        _gpu.assert_skin_close(got.cpu().numpy(), ref, w)
+        # the plain two-clip frame on the same plan afterwards
+        _gpu.assert_skin_close(run_frame_on(ctx, plan, w), oracle.frame(w), w)
+    # weights (1 - w, w, 0, 0) without additive weight: the two-clip frame
+    w = synth.subset(synth.config2(), list(range(0, 4096, 128)) + [4096])
+    m = len(w["char_type"])
+    wl = np.stack([1 - w["weight"], w["weight"], np.zeros(m), np.zeros(m)], 1).astype(np.float32)
+    ctx, plan = _gpu.setup(w)
+    got = ctx.evaluate_frame_layers(plan, _gpu.cuda(w["time"]), _gpu.cuda(wl))
+    _gpu.assert_skin_close(got.cpu().numpy(), oracle.frame(w), w)
+
+
 def test_empty_plan_and_errors(torch):
     import paper_2505_06703_gb300 as pk
     rng = np.random.default_rng(5)
