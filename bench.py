@@ -369,6 +369,7 @@ def run_ours(args) -> dict:
             result["frame_mixed"] = run_mixed_frame(local, dev, world, peak)
             result["ik"] = run_ik(local, dev, world, peak)
             result["frame_skinned"] = run_skinned_frame(local, dev, world, peak)
+            result["frame_layers"] = run_layered_frame(local, dev, world, peak)
             cmp_ = time_forward_methods(rank_workload(rank), local, dev, world)
             result["scan_comparison"] = {
                 "workload": "forward from local poses (scan + bind) on the frame's 2,098,176 joints",
@@ -457,6 +458,47 @@ def run_skinned_frame(device, dev, world, peak) -> dict:
             "joints_per_s": world * plan.total / (ms_step / 1e3), "vertices": nv,
             "workload": "frame + linear blend skinning: the frame's 4,097 characters, 1,500-vertex mesh per type, "
                         "4 bones per vertex, positions + normals out, skin matrices not written",
+            "schedule": ctx.get_schedule(plan),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes": alg}}
+
+
+def run_layered_frame(device, dev, world, peak) -> dict:
+    """The frame with layered blending: the frame's characters with 4 clips
+    per type blended by per-character weights plus an additive layer;
+    frames back to back in one CUDA graph, outputs rotated past L2."""
+    import torch
+    w = synth.with_layers(synth.config2(), n_clips=4)
+    ctx, plan = setup_ctx(w, device)
+    for i, t in enumerate(w["types"]):
+        ctx.upload_additive(i, t["add_keys"], t["rate_hz"])
+    ctx.tune(plan, 0)
+    joints = plan.total
+    n_out = max(2, math.ceil(2.5 * L2_BYTES / (joints * 48)))
+    outs = [torch.empty((joints, 12), dtype=torch.float32, device=dev) for _ in range(n_out)]
+    tm = torch.as_tensor(w["time"], device=dev)
+    wts = torch.as_tensor(w["weights"], device=dev)
+    aw = torch.as_tensor(w["add_w"], device=dev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for o in outs:
+            ctx.evaluate_frame_layers(plan, tm, wts, aw, out=o)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for o in outs:
+            ctx.evaluate_frame_layers(plan, tm, wts, aw, out=o)
+    torch.cuda.synchronize()
+    reps = 5
+    ms = aggregate_max(time_events(lambda s: graph.replay(), reps, 2), world)
+    ms_step = ms / (reps * n_out)
+    # skin out, 4 clips + the additive layer of keys once, 28 B per character
+    alg = frame_algorithmic_bytes(w) + sum(len(t["parents"]) * t["add_keys"].shape[0] * 28 for t in w["types"]) + \
+        len(w["char_type"]) * 16
+    achieved = alg / (ms_step / 1e3) / 1e9
+    return {"value": world * joints / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step,
+            "workload": "frame with 4 clips per type blended by per-character weights (incremental slerp) "
+                        "+ an additive layer; the frame's 4,097 characters",
             "schedule": ctx.get_schedule(plan),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes": alg}}
