@@ -85,6 +85,8 @@ def _load():
         _lib.oracle_frame_layers.argtypes = [c_int, i32, i32, d, f, i64, i32, i32, f, f, i64, c_int64, i32, f, f, f,
                                              i64, d]
         _lib.oracle_frame_layers.restype = c_int
+        _lib.oracle_raster.argtypes = [c_int, i32, POINTER(POINTER(c_int32)), i64, d, c_int, c_double, c_double,
+                                       c_double, c_double, c_int, c_int, POINTER(ctypes.c_uint32), c_void_p]
     return _lib
 
 
@@ -360,3 +362,27 @@ def frame_layers(w: dict):
                                    len(ct), _p(ct, c_int32), _p(tm, c_float), _p(wts, c_float), _p(aw, c_float),
                                    _p(off, c_int64), _p(skin, c_double)), "frame_layers")
     return skin.reshape(-1, 3, 4)
+
+
+RASTER_EMPTY = 0xFFFFFFFF
+
+
+def raster(faces_per_char, verts, vert_off, cols: int, spacing: float, ox: float, oy: float, scale: float,
+           width: int, height: int, with_cover: bool = False):
+    """Software rasterization of skinned characters (fixed rules, see
+    oracle_raster): faces_per_char[c] [n_faces][3] vertex indices of
+    character c, verts [sum][6] positions + normals, vert_off [n_chars + 1].
+    Returns ids [height][width] uint32 (and per-pixel coverage counts)."""
+    lib = _load()
+    n = len(faces_per_char)
+    fs = [np.ascontiguousarray(f, dtype=np.int32).reshape(-1) for f in faces_per_char]
+    nf = _i32([len(f) // 3 for f in fs])
+    arr = (POINTER(c_int32) * max(n, 1))(*[f.ctypes.data_as(POINTER(c_int32)) for f in fs])
+    v = _f64(verts)
+    vo = _i64(vert_off)
+    ids = np.empty((height, width), np.uint32)
+    cover = np.empty((height, width), np.int32) if with_cover else None
+    lib.oracle_raster(n, _p(nf, c_int32), arr, _p(vo, c_int64), _p(v, c_double), int(cols), float(spacing), float(ox),
+                      float(oy), float(scale), int(width), int(height), ids.ctypes.data_as(POINTER(ctypes.c_uint32)),
+                      cover.ctypes.data_as(c_void_p) if cover is not None else None)
+    return (ids, cover) if with_cover else ids

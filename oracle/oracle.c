@@ -695,3 +695,92 @@ int oracle_frame_layers(int n_types, const int32_t *counts, const int32_t *paren
   free(toff); free(q); free(tr); free(L); free(M);
   return 0;
 }
+
+/*
+ * Headless rasterization of the skinned crowd (the paper renders its crowd,
+ * Sec. 4 and Fig. 6, through a graphics API; this is the same picture as a
+ * plain software rasterizer with fixed rules).  Character c stands at world
+ * offset (col * spacing, -row * spacing, 0), col = c % cols, row = c / cols;
+ * orthographic camera looking down -Z: a world point (X, Y, Z) lands at
+ * screen (ox + scale X, oy - scale Y), depth d = (2 - Z) / 4 (smaller is
+ * nearer).  Screen positions are snapped to 1/256 pixel (round to nearest,
+ * halves away from zero); coverage of pixel (x, y) -- centre (x + 0.5,
+ * y + 0.5) -- uses 64-bit integer edge functions of the snapped positions
+ * with the triangle oriented to positive area and the tie rule: a centre on
+ * an edge a->b belongs to the triangle if b - a points down (dy > 0), or
+ * horizontally left (dy == 0, dx < 0), so two triangles sharing an edge never
+ * both take (or both miss) a centre on it; zero-area triangles cover
+ * nothing.  Visibility: the smallest (depth, id) with depth interpolated
+ * barycentrically at the centre; id = c * 4096 + face index.
+ *   ids [height][width] receives the winning id or 0xFFFFFFFF; cover
+ *   (nullable) the number of triangles covering each pixel.
+ */
+static int64_t snap256(double v) { return (int64_t)llround(v * 256.0); }
+
+void oracle_raster(int n_chars, const int32_t *n_faces, const int32_t *const *faces, const int64_t *vert_off,
+                   const double *verts, int cols, double spacing, double ox, double oy, double scale, int width,
+                   int height, uint32_t *ids, int32_t *cover) {
+  double *depth = (double *)malloc(sizeof(double) * (size_t)width * height);
+  for (size_t i = 0; i < (size_t)width * height; ++i) {
+    ids[i] = 0xFFFFFFFFu;
+    depth[i] = INFINITY;
+    if (cover) cover[i] = 0;
+  }
+  for (int c = 0; c < n_chars; ++c) {
+    const double wx = (c % cols) * spacing, wy = -(c / cols) * spacing;
+    for (int f = 0; f < n_faces[c]; ++f) {
+      int64_t X[3], Y[3];
+      double D[3];
+      for (int k = 0; k < 3; ++k) {
+        const double *v = verts + 6 * (vert_off[c] + faces[c][3 * f + k]);
+        X[k] = snap256(ox + scale * (v[0] + wx));
+        Y[k] = snap256(oy - scale * (v[1] + wy));
+        D[k] = (2.0 - v[2]) / 4.0;
+      }
+      int64_t area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+      if (area == 0) continue;
+      if (area < 0) {  // orient to positive area
+        int64_t tx = X[1], ty = Y[1];
+        double td = D[1];
+        X[1] = X[2]; Y[1] = Y[2]; D[1] = D[2];
+        X[2] = tx; Y[2] = ty; D[2] = td;
+        area = -area;
+      }
+      int64_t xmin = X[0], xmax = X[0], ymin = Y[0], ymax = Y[0];
+      for (int k = 1; k < 3; ++k) {
+        xmin = X[k] < xmin ? X[k] : xmin; xmax = X[k] > xmax ? X[k] : xmax;
+        ymin = Y[k] < ymin ? Y[k] : ymin; ymax = Y[k] > ymax ? Y[k] : ymax;
+      }
+      /* pixels whose centre x*256+128 lies in [xmin, xmax] */
+      int px0 = (int)((xmin - 128 + 255) >> 8), px1 = (int)((xmax - 128) >> 8);
+      int py0 = (int)((ymin - 128 + 255) >> 8), py1 = (int)((ymax - 128) >> 8);
+      if (px0 < 0) px0 = 0;
+      if (py0 < 0) py0 = 0;
+      if (px1 > width - 1) px1 = width - 1;
+      if (py1 > height - 1) py1 = height - 1;
+      for (int py = py0; py <= py1; ++py) {
+        for (int px = px0; px <= px1; ++px) {
+          const int64_t cx = (int64_t)px * 256 + 128, cy = (int64_t)py * 256 + 128;
+          int64_t e[3];
+          int inside = 1;
+          for (int k = 0; k < 3 && inside; ++k) {
+            const int a = (k + 1) % 3, b = (k + 2) % 3;  /* edge opposite vertex k */
+            const int64_t dx = X[b] - X[a], dy = Y[b] - Y[a];
+            e[k] = dx * (cy - Y[a]) - dy * (cx - X[a]);
+            if (e[k] < 0 || (e[k] == 0 && !(dy > 0 || (dy == 0 && dx < 0)))) inside = 0;
+          }
+          if (!inside) continue;
+          if (cover) ++cover[(size_t)py * width + px];
+          const double d = ((double)e[0] * D[0] + (double)e[1] * D[1] + (double)e[2] * D[2]) / (double)area;
+          const uint32_t id = (uint32_t)c * 4096u + (uint32_t)f;
+          const size_t pi = (size_t)py * width + px;
+          if (d < depth[pi] || (d == depth[pi] && id < ids[pi])) {
+            depth[pi] = d;
+            ids[pi] = id;
+          }
+        }
+      }
+    }
+  }
+  free(depth);
+}

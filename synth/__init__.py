@@ -205,15 +205,20 @@ def make_mesh(parents: np.ndarray, n_verts: int, rng: np.random.Generator, max_i
     weighted to the home joint and its nearest relatives (parent,
     grandparent, first child), weights positive, decreasing away from the
     home joint and summing to 1 (a quarter of the vertices use fewer
-    influences; unused slots have weight 0).  Positions uniform in
-    [-0.5, 0.5]^3, unit normals uniform on the sphere."""
+    influences; unused slots have weight 0).  Positions: a random centre in
+    [-0.5, 0.5]^3 per home joint plus uniform offsets of +-0.03, so a
+    joint's vertices form a small patch; unit normals uniform on the sphere.
+    Faces: a triangle strip over the vertex sequence (n_verts - 2 faces,
+    alternating orientation), i.e. small triangles within a patch."""
     parents = np.asarray(parents)
     n = len(parents)
     first_child = np.full(n, -1)
     for j in range(n - 1, 0, -1):
         if parents[j] >= 0:
             first_child[parents[j]] = j
-    pos = rng.uniform(-0.5, 0.5, size=(n_verts, 3))
+    centre = rng.uniform(-0.5, 0.5, size=(n, 3))
+    home_of = np.arange(n_verts) * n // n_verts
+    pos = centre[home_of] + rng.uniform(-0.03, 0.03, size=(n_verts, 3))
     nrm = rng.normal(size=(n_verts, 3))
     nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
     bones = np.zeros((n_verts, 4), np.int32)
@@ -230,8 +235,10 @@ def make_mesh(parents: np.ndarray, n_verts: int, rng: np.random.Generator, max_i
         bones[v, :m] = cand[:m]
         w = np.sort(rng.uniform(0.05, 1.0, size=m))[::-1]
         wts[v, :m] = w / w.sum()
+    faces = np.array([(v, v + 1, v + 2) if v % 2 == 0 else (v, v + 2, v + 1) for v in range(max(0, n_verts - 2))],
+                     np.int32).reshape(-1, 3)
     return {"pos": pos.astype(np.float32), "nrm": nrm.astype(np.float32), "bones": bones,
-            "weights": wts.astype(np.float32)}
+            "weights": wts.astype(np.float32), "faces": faces}
 
 
 def with_meshes(w: dict, n_verts: int = 1500, seed: int = 11) -> dict:
