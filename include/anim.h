@@ -151,6 +151,11 @@ ANIM_API int anim_plan_row_offsets(const anim_plan *plan, int64_t *out);
 ANIM_API int anim_upload_mesh(anim_ctx *ctx, int32_t type_id, int n_verts, const float *rest_pos,
                               const float *rest_nrm, const int32_t *bones, const float *weights);
 
+/* Triangles of a type's mesh for anim_raster: host faces [n_faces][3]
+ * vertex indices in [0, n_verts) of the mesh uploaded before (ANIM_ESTATE
+ * without one), 1 <= n_faces <= 4,096.  Replaces earlier faces. */
+ANIM_API int anim_upload_faces(anim_ctx *ctx, int32_t type_id, int n_faces, const int32_t *faces);
+
 /* Host copy of the plan's vertex offsets: out[0..n_chars], the exclusive
  * prefix of the characters' vertex counts (0 for a type without a mesh). */
 ANIM_API int anim_plan_vertex_offsets(anim_ctx *ctx, const anim_plan *plan, int64_t *out);
@@ -188,6 +193,30 @@ ANIM_API int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, c
  * runs on the segmented kernel here. */
 ANIM_API int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float *d_time,
                                         const float *d_weights, const float *d_add_w, float *d_skin, void *stream);
+
+/* Camera and crowd layout of anim_raster. */
+typedef struct anim_raster_params {
+  int32_t width, height;  /* image size in pixels */
+  int32_t cols;           /* characters per grid row */
+  float spacing;          /* world distance between grid cells */
+  float ox, oy, scale;    /* screen = (ox + scale X, oy - scale Y) */
+} anim_raster_params;
+
+/* Headless rasterization of the skinned crowd (the paper renders its crowd,
+ * Sec. 4 and Fig. 6, through a graphics API; no graphics stack here):
+ * character c stands at world offset (col * spacing, -row * spacing, 0),
+ * col = c % cols, row = c / cols; an orthographic camera looking down -Z
+ * maps (X, Y, Z) to screen (ox + scale X, oy - scale Y), depth (2 - Z) / 4.
+ * Positions snapped to 1/256 pixel; a pixel is covered when its centre is
+ * inside a triangle by integer edge functions, ties on an edge a->b going to
+ * the triangle when b - a points down or horizontally left; the nearest
+ * depth wins, then the smaller id c * 4096 + face.  d_verts: the skinned
+ * vertices of anim_evaluate_frame_skinned; d_vis: device scratch
+ * [height][width] uint64; d_ids (nullable): [height][width] winning ids,
+ * 0xFFFFFFFF where empty; d_rgba (nullable): [height][width] flat-shaded
+ * RGBA8.  At most 1,048,575 characters.  Three launches on `stream`. */
+ANIM_API int anim_raster(anim_ctx *ctx, const anim_plan *plan, const float *d_verts, const anim_raster_params *params,
+                         uint64_t *d_vis, uint32_t *d_ids, uint32_t *d_rgba, void *stream);
 
 /* The two launches of anim_evaluate_frame, for callers that schedule them
  * apart (e.g. to time the persistent kernel alone): build_queue buckets the

@@ -35,6 +35,8 @@ SIGNATURES = {
     "anim_plan_vertex_offsets": (c_int, [_P, _P, _P]),
     "anim_evaluate_frame_skinned": (c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "anim_upload_additive": (c_int, [_P, c_int32, c_int, c_float, _P]),
+    "anim_upload_faces": (c_int, [_P, c_int32, c_int, _P]),
+    "anim_raster": (c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame_layers": (c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame_levelsync": (c_int, [_P, _P, _P, _P, _P, _P]),
@@ -183,6 +185,24 @@ class Context:
                                                      _dptr(out), _stream(stream)))
         return out
 
+    def upload_faces(self, type_id: int, faces):
+        f = np.ascontiguousarray(faces, dtype=np.int32)
+        self._ck(self.lib.anim_upload_faces(self.h, int(type_id), len(f), _np_ptr(f)))
+
+    def raster(self, plan, verts, width, height, cols, spacing, ox, oy, scale, ids=True, rgba=False, vis=None,
+               stream=None):
+        """Headless rasterization of the skinned characters: (ids [h, w] int32
+        view of uint32 or None, rgba [h, w] int32 view or None)."""
+        import torch
+        dev = f"cuda:{self.device}"
+        vis = vis if vis is not None else torch.empty((height, width), dtype=torch.int64, device=dev)
+        out_ids = torch.empty((height, width), dtype=torch.int32, device=dev) if ids else None
+        out_rgba = torch.empty((height, width), dtype=torch.int32, device=dev) if rgba else None
+        p = _RasterParams(int(width), int(height), int(cols), float(spacing), float(ox), float(oy), float(scale))
+        self._ck(self.lib.anim_raster(self.h, plan.h, _dptr(verts), ctypes.byref(p), _dptr(vis), _dptr(out_ids),
+                                      _dptr(out_rgba), _stream(stream)))
+        return out_ids, out_rgba
+
     def upload_mesh(self, type_id: int, mesh: dict):
         """mesh: pos [nv,3], nrm [nv,3], bones [nv,4] int, weights [nv,4]."""
         pos = np.ascontiguousarray(mesh["pos"], dtype=np.float32)
@@ -297,6 +317,11 @@ class Context:
             raise ValueError("a schedule has 5 values")
         a = np.ascontiguousarray(sched, dtype=np.int32)
         self._ck(self.lib.anim_set_schedule(self.h, plan.h, _np_ptr(a)))
+
+
+class _RasterParams(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("cols", c_int32), ("spacing", c_float), ("ox", c_float),
+                ("oy", c_float), ("scale", c_float)]
 
 
 class Plan:

@@ -47,8 +47,9 @@ struct TypeDev {
   // per vertex: (px py pz nx), (ny nz w0 w1), (w2 w3 bones01 bones23) with
   // the bone ids as 16-bit pairs in the last two words' bits.
   int n_verts;
-  int pad3;
+  int n_faces;
   const float4 *mesh;
+  const int32_t *faces;      // [n_faces][3] vertex indices (raster)
   // Chain-walk frame kernel (k_walk): a static lane schedule of wk_S steps
   // for wk_P lanes per character; entry [s][slot] names the joint lane `slot`
   // composes at step s (kWInvalid: idle).  wk_mode 1: natural chains walked
@@ -242,6 +243,22 @@ struct PaperArgs {
 };
 size_t paper_smem_bytes(int n);
 cudaError_t launch_paper(const PaperArgs &a, int n_chars, int threads, size_t smem, cudaStream_t s);
+
+// Headless rasterization of skinned characters (comparator picture of the
+// paper's rendering): clear, one CTA per character rasterizing its faces
+// into the 64-bit visibility buffer, resolve to ids / RGBA.
+struct RasterArgs {
+  const TypeDev *types;
+  const int32_t *char_type;
+  const int64_t *vert_off;
+  const float *verts;             // [total vertices][6]
+  unsigned long long *vis;        // [height][width]
+  uint32_t *ids;                  // nullable
+  uint32_t *rgba;                 // nullable
+  int width, height, cols;
+  float spacing, ox, oy, scale;
+};
+cudaError_t launch_raster(const RasterArgs &a, int n_chars, cudaStream_t s);
 
 // Setup kernels.
 cudaError_t launch_prepare_keys(float4 *keys, int n_clips, int n_keys, int n, cudaStream_t s);

@@ -395,12 +395,14 @@ struct TypeHost {
   float4 *d_add = nullptr;      // additive layer keys [n_keys][n][2]
   float4 *d_mesh = nullptr;     // skinned mesh, 3 float4 per vertex
   int n_verts = 0;
+  int32_t *d_faces = nullptr;   // [n_faces][3]
+  int n_faces = 0;
   float4 *d_wkeys = nullptr;    // schedule-ordered key records
   float4 *d_wbind = nullptr;    // schedule-ordered inverse binds
   TypeDev dev{};
   ~TypeHost() {
     for (void *p : {(void *)d_tables, (void *)d_inv_bind, (void *)d_keys, (void *)d_wkeys, (void *)d_wbind,
-                    (void *)d_mesh, (void *)d_add})
+                    (void *)d_mesh, (void *)d_add, (void *)d_faces})
       if (p) cudaFree(p);
   }
   cudaError_t build_tables() {
@@ -486,6 +488,8 @@ struct TypeHost {
     dev.wk_bind = d_wbind;
     dev.n_verts = n_verts;
     dev.mesh = d_mesh;
+    dev.n_faces = n_faces;
+    dev.faces = d_faces;
   }
   // Schedule-ordered key records (when clips are uploaded) and inverse binds
   // of a walkable type; synchronous.
@@ -1067,7 +1071,64 @@ int anim_upload_mesh(anim_ctx *ctx, int32_t type_id, int n_verts, const float *r
   CK(cudaMalloc(&T.d_mesh, rec.size() * sizeof(float4)));
   CK(cudaMemcpy(T.d_mesh, rec.data(), rec.size() * sizeof(float4), cudaMemcpyHostToDevice));
   T.n_verts = n_verts;
+  if (T.d_faces) {  // faces index the mesh they were uploaded for
+    cudaFree(T.d_faces);
+    T.d_faces = nullptr;
+    T.n_faces = 0;
+  }
   CK(upload_types(ctx));  // bumps the version: plans rebuild their vertex offsets
+  return ANIM_OK;
+}
+
+int anim_upload_faces(anim_ctx *ctx, int32_t type_id, int n_faces, const int32_t *faces) {
+  if (!ctx) return ANIM_EINVAL;
+  if (type_id < 0 || type_id >= (int)ctx->types.size()) return fail(ctx, ANIM_EINVAL, "type id %d unknown", type_id);
+  TypeHost &T = *ctx->types[type_id];
+  if (T.n_verts == 0) return fail(ctx, ANIM_ESTATE, "type %d has no mesh: upload it first", type_id);
+  if (n_faces < 1 || n_faces > 4096) return fail(ctx, ANIM_EINVAL, "n_faces must be in [1, 4096]");
+  if (!faces) return fail(ctx, ANIM_EINVAL, "faces is NULL");
+  for (int i = 0; i < 3 * n_faces; ++i)
+    if (faces[i] < 0 || faces[i] >= T.n_verts)
+      return fail(ctx, ANIM_EINVAL, "face %d: vertex %d out of range", i / 3, faces[i]);
+  CK(cudaSetDevice(ctx->device));
+  if (T.d_faces) cudaFree(T.d_faces);
+  T.d_faces = nullptr;
+  T.n_faces = 0;
+  CK(cudaMalloc(&T.d_faces, (size_t)n_faces * 12));
+  CK(cudaMemcpy(T.d_faces, faces, (size_t)n_faces * 12, cudaMemcpyHostToDevice));
+  T.n_faces = n_faces;
+  CK(upload_types(ctx));
+  return ANIM_OK;
+}
+
+int anim_raster(anim_ctx *ctx, const anim_plan *plan, const float *d_verts, const anim_raster_params *params,
+                uint64_t *d_vis, uint32_t *d_ids, uint32_t *d_rgba, void *stream) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (!params || params->width < 1 || params->height < 1 || params->cols < 1 ||
+      (int64_t)params->width * params->height > (1ll << 28) || !std::isfinite(params->spacing) ||
+      !std::isfinite(params->ox) || !std::isfinite(params->oy) || !std::isfinite(params->scale))
+    return fail(ctx, ANIM_EINVAL, "bad raster parameters");
+  if (plan->n_chars >= (1 << 20)) return fail(ctx, ANIM_EUNSUPPORTED, "at most 1,048,575 characters");
+  if (!d_vis || ((uintptr_t)d_vis & 7u)) return fail(ctx, ANIM_EINVAL, "d_vis must be an 8-byte aligned device pointer");
+  if (plan->n_chars > 0 && (!d_verts || !aligned4(d_verts)))
+    return fail(ctx, ANIM_EINVAL, "d_verts must be a 4-byte aligned device pointer");
+  RasterArgs a{};
+  a.types = ctx->d_types;
+  a.char_type = plan->d_char_type;
+  a.vert_off = plan->d_vert_off;
+  a.verts = d_verts;
+  a.vis = reinterpret_cast<unsigned long long *>(d_vis);
+  a.ids = d_ids;
+  a.rgba = d_rgba;
+  a.width = params->width;
+  a.height = params->height;
+  a.cols = params->cols;
+  a.spacing = params->spacing;
+  a.ox = params->ox;
+  a.oy = params->oy;
+  a.scale = params->scale;
+  CK(launch_raster(a, (int)plan->n_chars, (cudaStream_t)stream));
   return ANIM_OK;
 }
 

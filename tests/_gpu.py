@@ -24,6 +24,8 @@ def setup(w: dict, device: int = 0, with_clips: bool = True):
     for i, t in zip(ids, types):
         if "mesh" in t:
             ctx.upload_mesh(i, t["mesh"])
+            if "faces" in t["mesh"] and len(t["mesh"]["faces"]):
+                ctx.upload_faces(i, t["mesh"]["faces"])
         if with_clips and "add_keys" in t:
             ctx.upload_additive(i, t["add_keys"], t["rate_hz"])
     plan = ctx.plan(np.asarray(ids, np.int32)[w["char_type"]])

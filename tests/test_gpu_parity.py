@@ -422,6 +422,68 @@ def test_layered_frame(torch, walk):
     _gpu.assert_skin_close(got.cpu().numpy(), oracle.frame(w), w)
 
 
+def _raster_tri(V, voff, faces, ct, ident, cols, spacing, ox, oy, scale):
+    """Screen-space vertices (pixels, FP64) and depths of triangle `ident`."""
+    c, f = int(ident) >> 12, int(ident) & 4095
+    tri = faces[int(ct[c])][f]
+    wx, wy = (c % cols) * spacing, -(c // cols) * spacing
+    v = V[voff[c] + tri]
+    xy = np.stack([ox + scale * (v[:, 0] + wx), oy - scale * (v[:, 1] + wy)], 1)
+    return xy, (2.0 - v[:, 2]) / 4.0
+
+
+def _edge_distance(xy, p):
+    """Distance in pixels from point p to the closest edge of triangle xy."""
+    best = np.inf
+    for k in range(3):
+        a, b = xy[k], xy[(k + 1) % 3]
+        d = b - a
+        t = np.clip(np.dot(p - a, d) / max(np.dot(d, d), 1e-30), 0.0, 1.0)
+        best = min(best, np.linalg.norm(a + t * d - p))
+    return best
+
+
+def _depth_at(xy, dz, p):
+    m = np.array([[xy[0, 0], xy[1, 0], xy[2, 0]], [xy[0, 1], xy[1, 1], xy[2, 1]], [1.0, 1.0, 1.0]])
+    lam = np.linalg.solve(m, [p[0], p[1], 1.0])
+    return float(lam @ dz)
+
+
+def test_crowd_raster(torch):
+    """The headless raster of the skinned crowd (65 characters, 1,500-vertex
+    meshes) against the oracle's rasterizer run on the oracle's skinned
+    vertices: the id images agree except where both answers are valid -- a
+    pixel centre within 1/32 pixel of an edge of one of the two triangles
+    (FP32 and FP64 vertices snap apart there), or two triangles whose depths
+    at the centre agree to 1e-4."""
+    EMPTY = 0xFFFFFFFF
+    w = synth.with_meshes(synth.subset(synth.config2(), list(range(0, 4096, 64)) + [4096]), n_verts=1500, seed=51)
+    types, ct = w["types"], w["char_type"]
+    V_ref = oracle.skin_vertices(w, oracle.frame(w))
+    voff = oracle.vertex_offsets(ct, types)
+    ctx, plan = _gpu.setup(w)
+    verts = ctx.evaluate_frame_skinned(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"]))
+    W, H, cols, spacing, ox, oy, scale = 640, 520, 9, 2.5, 60.0, 60.0, 24.0
+    ids_gpu, rgba = ctx.raster(plan, verts, W, H, cols, spacing, ox, oy, scale, rgba=True)
+    g = ids_gpu.cpu().numpy().view(np.uint32)
+    faces = [t["mesh"]["faces"] for t in types]
+    ref = oracle.raster([faces[int(t)] for t in ct], V_ref, voff, cols, spacing, ox, oy, scale, W, H)
+    covered = (g != EMPTY) | (ref != EMPTY)
+    assert covered.sum() > 0.1 * W * H
+    bad = np.argwhere((g != ref) & covered)
+    assert len(bad) <= 0.002 * covered.sum(), (len(bad), int(covered.sum()))
+    for py, px in bad:
+        p = np.array([px + 0.5, py + 0.5])
+        tris = [_raster_tri(V_ref, voff, faces, ct, i, cols, spacing, ox, oy, scale)
+                for i in (g[py, px], ref[py, px]) if i != EMPTY]
+        near_edge = any(_edge_distance(xy, p) < 1 / 32 for xy, _ in tris)
+        same_depth = len(tris) == 2 and abs(_depth_at(*tris[0], p) - _depth_at(*tris[1], p)) < 1e-4
+        assert near_edge or same_depth, (py, px, g[py, px], ref[py, px])
+    # every covered pixel is shaded, the background is not
+    img = rgba.cpu().numpy().view(np.uint32)
+    assert ((img != 0xFF201810) == (g != EMPTY)).all()
+
+
 def test_empty_plan_and_errors(torch):
     import paper_2505_06703_gb300 as pk
     rng = np.random.default_rng(5)
