@@ -192,12 +192,14 @@ class Context:
     def raster(self, plan, verts, width, height, cols, spacing, ox, oy, scale, ids=True, rgba=False, vis=None,
                stream=None):
         """Headless rasterization of the skinned characters: (ids [h, w] int32
-        view of uint32 or None, rgba [h, w] int32 view or None)."""
+        view of uint32 or None, rgba [h, w] int32 view or None); ids / rgba
+        may be given as tensors to write into, or True / False."""
         import torch
         dev = f"cuda:{self.device}"
         vis = vis if vis is not None else torch.empty((height, width), dtype=torch.int64, device=dev)
-        out_ids = torch.empty((height, width), dtype=torch.int32, device=dev) if ids else None
-        out_rgba = torch.empty((height, width), dtype=torch.int32, device=dev) if rgba else None
+        pick = lambda x: x if isinstance(x, torch.Tensor) else (
+            torch.empty((height, width), dtype=torch.int32, device=dev) if x else None)
+        out_ids, out_rgba = pick(ids), pick(rgba)
         p = _RasterParams(int(width), int(height), int(cols), float(spacing), float(ox), float(oy), float(scale))
         self._ck(self.lib.anim_raster(self.h, plan.h, _dptr(verts), ctypes.byref(p), _dptr(vis), _dptr(out_ids),
                                       _dptr(out_rgba), _stream(stream)))
