@@ -50,7 +50,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes per launch of the persistent frame kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources it was taken on; reported as null once the sources change.
-# dram read + write bytes of one k_scan launch from one ncu capture, per kernel-source hash
+# dram read + write bytes of one frame-kernel launch from one ncu capture, per kernel-source hash
 NCU_TRAFFIC = {"7700f5e04a11ee1d": 1835776 + 41493248}
 
 
@@ -315,7 +315,7 @@ def run_ours(args) -> dict:
     achieved = alg / (k_ms / 1e3) / 1e9
     tr = NCU_TRAFFIC.get(kernel_source_hash())
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": tr, "kernel": "k_scan<0> (persistent frame)",
+                "frac": round(achieved / peak, 4), "traffic": tr, "kernel": "k_frame_qt (persistent frame)",
                 "kernel_ms": round(k_ms, 5), "algorithmic_bytes": alg, "peak_source": peak_src}
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,

@@ -268,5 +268,10 @@ cudaError_t launch_bind_from_rest(const int32_t *parent, const float *rest_q, co
 // Shared-memory footprint of one work item of C characters (bytes).
 size_t scan_smem_bytes(int n, int nseg, int C);
 size_t adjoint_smem_bytes(int n, int nseg, int C);
+size_t frame_qt_smem_bytes(int n, int nseg, int C);
+
+// The plain frame with (quaternion, translation) items (MODE 0, skin
+// matrices out, no skinning or layers).
+cudaError_t launch_frame_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 }  // namespace anim

@@ -579,6 +579,7 @@ struct anim_plan {
   std::vector<int> used;                      // type ids, most costly first
   std::vector<std::vector<int32_t>> by_type;  // characters of each used type (indexed like used)
   std::vector<int> C_scan, C_adj;             // per ctx type id
+  std::vector<int> C_frame;                   // plain frame: characters per (q, t) item
   int64_t total = 0;
   int version = -1;  // schedule version the items were built for
   // device
@@ -596,7 +597,8 @@ struct anim_plan {
   int *d_queue = nullptr;  // [0] work-queue head, [1] finished-CTA counter (both back to 0 after each launch)
   int32_t *d_used = nullptr, *d_cap = nullptr;
   LaunchCfg cfg_scan{}, cfg_adj{};
-  size_t smem_frame = 0;
+  size_t smem_frame = 0;     // plain frame, (q, t) items
+  size_t smem_frame_mat = 0; // frame with skinning or layers, matrix items
   int adj_unfit = -1;
   // frame: item slots [0, n_slots_walk) belong to the chain-walk kernel
   // (queue counters d_queue[0..1]), the rest to the segmented CTA kernel
@@ -729,11 +731,15 @@ size_t adj_budget(const anim_ctx *ctx) {
   return ctx->smem_per_sm / (size_t)ctx->adj_ctas - 1024 - kAdjSmallStatic;
 }
 
-int choose_C(const anim_ctx *ctx, const TypeHost &T, bool adjoint) {
+// Characters per work item: kind 0 the matrix scan, 1 the adjoint, 2 the
+// plain frame's (q, t) items.
+int choose_C(const anim_ctx *ctx, const TypeHost &T, int kind) {
+  const bool adjoint = kind == 1;
   const size_t budget = adjoint ? adj_budget(ctx) : smem_budget(ctx);
   int C = std::max(1, std::min(kCMax, ctx->joints_per_item / std::max(1, T.n)));
   auto bytes = [&](int c) {
-    return adjoint ? adjoint_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
+    return kind == 1 ? adjoint_smem_bytes(T.n, T.seg.nseg, c)
+                     : kind == 2 ? frame_qt_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
   };
   while (C > 1 && bytes(C) > budget) --C;
   if (bytes(C) > ctx->smem_optin - kStaticSmemAllowance) return 0;
@@ -775,16 +781,18 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   const int nt = (int)ctx->types.size();
   P->C_scan.assign(nt, 1);
   P->C_adj.assign(nt, 1);
+  P->C_frame.assign(nt, 1);
   P->adj_unfit = -1;
   size_t smem_s = 0, smem_a = 0;
   for (int t : P->used) {
     const TypeHost &T = *ctx->types[t];
-    const int cs = choose_C(ctx, T, false), ca = choose_C(ctx, *T.adj, true);
+    const int cs = choose_C(ctx, T, 0), ca = choose_C(ctx, *T.adj, 1);
     if (cs == 0)
       return fail(ctx, ANIM_EUNSUPPORTED,
                   "type %d (%d joints, %d segments) does not fit in shared memory with one character", t, T.n,
                   T.seg.nseg);
     P->C_scan[t] = cs;
+    P->C_frame[t] = std::max(cs, choose_C(ctx, T, 2));  // (q, t) items are smaller
     smem_s = std::max(smem_s, scan_smem_bytes(T.n, T.seg.nseg, cs));
     // the adjoint keeps two more vectors per joint: a schedule may fit the
     // forward kernels and not the adjoint, which then refuses to run
@@ -800,15 +808,19 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->n_items_adj = (int)ia.size();
   CK(upload_vec(&P->d_items_scan, is));
   CK(upload_vec(&P->d_items_adj, ia));
-  // frame: walkable types (chain-walk kernel, 32 / P characters per item)
-  // take the first item regions, the others follow
-  std::vector<int32_t> cap(P->C_scan);
+  // plain frame: walkable types (chain-walk kernel, 32 / P characters per
+  // item) take the first item regions, the others ((q, t) items) follow
+  std::vector<int32_t> cap(P->C_frame);
   std::vector<char> walk_t(nt, 0);
   int wcmax = 0;
+  size_t smem_f = 0;
   P->walk_nbs = 0;
   for (int t : P->used) {
     const TypeHost &T = *ctx->types[t];
-    if (!ctx->use_walk || T.ws.mode == 0) continue;
+    if (!ctx->use_walk || T.ws.mode == 0) {
+      smem_f = std::max(smem_f, frame_qt_smem_bytes(T.n, T.seg.nseg, P->C_frame[t]));
+      continue;
+    }
     walk_t[t] = 1;
     cap[t] = 32 / T.ws.P;
     wcmax = std::max(wcmax, cap[t]);
@@ -848,10 +860,10 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->n_ranges = (int)ranges.size();
   P->n_slots = slots;
   CK(upload_vec(&P->d_ranges, ranges));
-  // the all-CTA layout for the frame with skinning
+  // the matrix-item layout of every type for the frame with skinning or layers
   std::vector<RangeDev> ranges_cta;
   int slots_cta = 0;
-  if (P->n_slots_walk > 0) {
+  {
     for (size_t u = 0; u < P->used.size(); ++u) {
       const int t = P->used[u];
       const int cnt = (int)P->by_type[u].size(), C = P->C_scan[t], nk = ctx->types[t]->n_keys;
@@ -884,7 +896,8 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
     P->cfg_adj = {kAdjSmallThreads, std::max(1, P->n_items_adj), std::max<size_t>(smem_a, 16)};
   else
     P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
-  P->smem_frame = std::max<size_t>(smem_s, 16);
+  P->smem_frame = std::max<size_t>(smem_f, 16);
+  P->smem_frame_mat = std::max<size_t>(smem_s, 16);
   P->version = ctx->version;
   return ANIM_OK;
 }
@@ -1299,7 +1312,7 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
     LaunchCfg cfg = plan->cfg_scan;
     cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
     cfg.smem = plan->smem_frame;
-    CK(launch_scan(0, a, cfg, cta_st));
+    CK(launch_frame_qt(a, cfg, cta_st));
   }
   if (has_walk) {
     WalkArgs w{};
@@ -1343,15 +1356,14 @@ int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const floa
   if (!d_blend_w || !d_verts) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
   if (!aligned16(d_verts) || (d_skin && !aligned16(d_skin)) || !aligned4(d_blend_w))
     return fail(ctx, ANIM_EINVAL, "d_verts, d_skin must be 16-byte aligned, d_blend_w 4-byte aligned");
-  const bool own = plan->n_slots_walk > 0;  // the frame's layout gives types to the walk kernel
-  BucketArgs bk{};
-  bk.ranges = own ? plan->d_ranges_cta : plan->d_ranges;
-  bk.n_ranges = own ? plan->n_ranges_cta : plan->n_ranges;
-  bk.n_slots = own ? plan->n_slots_cta : plan->n_slots;
+  BucketArgs bk{};  // matrix items of every type (the plain frame's layout differs)
+  bk.ranges = plan->d_ranges_cta;
+  bk.n_ranges = plan->n_ranges_cta;
+  bk.n_slots = plan->n_slots_cta;
   bk.type_chars = plan->d_type_chars;
   bk.time = d_time;
   bk.types = ctx->d_types;
-  bk.cap = own ? plan->d_cap_cta : plan->d_cap;
+  bk.cap = plan->d_cap_cta;
   bk.sorted = plan->d_sorted;
   bk.items = plan->d_items_frame;
   bk.queue_head = plan->d_queue;
@@ -1373,7 +1385,7 @@ int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const floa
   a.vert_off = plan->d_vert_off;
   LaunchCfg cfg = plan->cfg_scan;
   cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
-  cfg.smem = plan->smem_frame;
+  cfg.smem = plan->smem_frame_mat;
   CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
   return ANIM_OK;
 }
@@ -1385,15 +1397,14 @@ int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float
   if (!d_weights || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
   if (!aligned16(d_skin) || !aligned4(d_weights) || (d_add_w && !aligned4(d_add_w)))
     return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned, d_weights and d_add_w 4-byte aligned");
-  const bool own = plan->n_slots_walk > 0;  // the frame's layout gives types to the walk kernel
-  BucketArgs bk{};
-  bk.ranges = own ? plan->d_ranges_cta : plan->d_ranges;
-  bk.n_ranges = own ? plan->n_ranges_cta : plan->n_ranges;
-  bk.n_slots = own ? plan->n_slots_cta : plan->n_slots;
+  BucketArgs bk{};  // matrix items of every type (the plain frame's layout differs)
+  bk.ranges = plan->d_ranges_cta;
+  bk.n_ranges = plan->n_ranges_cta;
+  bk.n_slots = plan->n_slots_cta;
   bk.type_chars = plan->d_type_chars;
   bk.time = d_time;
   bk.types = ctx->d_types;
-  bk.cap = own ? plan->d_cap_cta : plan->d_cap;
+  bk.cap = plan->d_cap_cta;
   bk.sorted = plan->d_sorted;
   bk.items = plan->d_items_frame;
   bk.queue_head = plan->d_queue;
@@ -1414,7 +1425,7 @@ int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float
   a.add_w = d_add_w;
   LaunchCfg cfg = plan->cfg_scan;
   cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
-  cfg.smem = plan->smem_frame;
+  cfg.smem = plan->smem_frame_mat;
   CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
   return ANIM_OK;
 }
@@ -1596,7 +1607,7 @@ int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_
     CK(ev);
     for (int e = 0; e < n_eff; ++e) eff_slot[(size_t)t * n_eff + e] = vid[effectors[(size_t)t * n_eff + e]];
     vdev[t] = V->dev;
-    const int C = choose_C(ctx, *V, true);
+    const int C = choose_C(ctx, *V, 1);
     if (C == 0) return fail(ctx, ANIM_EUNSUPPORTED, "IK view of type %d does not fit in shared memory", t);
     Cv[t] = C;
     smem = std::max(smem, adjoint_smem_bytes(V->n, V->seg.nseg, C));

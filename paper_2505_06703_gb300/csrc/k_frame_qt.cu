@@ -1,0 +1,222 @@
+// The plain fused frame (Simulation -> Hierarchy-Scan -> Bind MeshPose,
+// Sec. 1 steps 1-3, Eq. 1) with rigid transforms kept as (quaternion,
+// translation) pairs -- 32 bytes per joint instead of a 48-byte 3x4 matrix
+// -- while the segmented scan runs in shared memory.  The local poses are
+// rigid (unit scale), so the pair is an exact representation:
+//   (qa, ta) o (qb, tb) = (qa qb, ta + R(qa) tb).
+// The smaller item footprint lets more characters be in flight per SM, which
+// is what bounds the latency-limited scan passes.  The bind pass normalizes
+// the composed quaternion once (removing the norm drift of long products),
+// forms M = [R(q) | t] and writes S = M B straight to global memory.
+// Same item pipeline as k_scan (producer warp, 8 compute warps, work queue);
+// the skinning and layered-blend variants of the frame keep the matrix form.
+#include <cuda_runtime.h>
+
+#include "anim_internal.h"
+#include "dev_math.cuh"
+#include "scan_core.cuh"
+
+namespace anim {
+
+namespace {
+
+struct QT {
+  float4 q;  // x y z w
+  float4 t;  // x y z (w unused)
+};
+
+__device__ __forceinline__ QT lds_qt(const float4 *p) { return QT{p[0], p[1]}; }
+__device__ __forceinline__ void sts_qt(float4 *p, const QT &a) {
+  p[0] = a.q;
+  p[1] = a.t;
+}
+
+// R(q) v for a unit quaternion q: v + 2 w (u x v) + 2 u x (u x v), u = q.xyz.
+__device__ __forceinline__ float3 qrot(const float4 q, const float4 v) {
+  const float cx = 2.f * (q.y * v.z - q.z * v.y), cy = 2.f * (q.z * v.x - q.x * v.z), cz = 2.f * (q.x * v.y - q.y * v.x);
+  return make_float3(fmaf(q.w, cx, v.x) + (q.y * cz - q.z * cy), fmaf(q.w, cy, v.y) + (q.z * cx - q.x * cz),
+                     fmaf(q.w, cz, v.z) + (q.x * cy - q.y * cx));
+}
+
+__device__ __forceinline__ QT qt_mul(const QT &a, const QT &b) {
+  const float3 r = qrot(a.q, b.t);
+  return QT{qmul(a.q, b.q), make_float4(a.t.x + r.x, a.t.y + r.y, a.t.z + r.z, 0.f)};
+}
+
+// Item layout: P [C][2n + 1] float4, Y0 / Y1 [C][nseg][2] float4, then the
+// type's segment tables as in the matrix layout.
+__device__ __forceinline__ ItemLayout item_layout_qt(float4 *sm, int C, int n, int nseg) {
+  ItemLayout L;
+  L.P = sm;
+  L.Y0 = L.P + C * (2 * n + 1);
+  L.Y1 = L.Y0 + 2 * C * nseg;
+  char *t = reinterpret_cast<char *>(L.Y1 + 2 * C * nseg);
+  L.ptr0 = reinterpret_cast<int16_t *>(t);
+  L.ptr1 = L.ptr0 + nseg;
+  L.seg_start = reinterpret_cast<int32_t *>(t + 4 * nseg);
+  L.seg_link = L.seg_start + nseg + 1;
+  L.jinfo = reinterpret_cast<uint16_t *>(L.seg_link + nseg);
+  L.end = reinterpret_cast<float4 *>(t + item_table_bytes(n, nseg));
+  return L;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a) {
+  extern __shared__ __align__(128) float4 sm[];
+  __shared__ ItemBuf bufs[2];
+  const int tid = threadIdx.x;
+  const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
+
+  if (tid >= kComputeThreads) {
+    producer_loop<0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time, a.blend_w,
+                     a.status);
+    return;
+  }
+
+  int cur = 0;
+  handoff_sync();
+  for (;;) {
+    const ItemBuf &b = bufs[cur];
+    if (b.item < 0) break;
+    const int C = b.C, n = b.T.n, nseg = b.T.nseg;
+    const int cs2 = 2 * n + 1;  // float4 stride between characters (16 B skew)
+    const ItemLayout Lt = item_layout_qt(sm, C, n, nseg);
+    float4 *P = Lt.P;
+    compute_sync();
+
+    // ---- pass 1a: local poses (q, t) from the clips; tables staged alongside
+    stage_tables(b, Lt, tid);
+    {
+      const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
+      const float4 *KA0 = b.T.keys + (size_t)k0 * n * 2;
+      const float4 *KA1 = b.T.keys + (size_t)k1 * n * 2;
+      const float4 *KB0 = b.T.keys + (size_t)(nk + k0) * n * 2;
+      const float4 *KB1 = b.T.keys + (size_t)(nk + k1) * n * 2;
+      const bool two = b.T.n_clips >= 2;
+      const int CN = C * n;
+#pragma unroll 2
+      for (int idx = tid; idx < CN; idx += kComputeThreads) {
+        const int j = (int)b.divC.div(idx), c = idx - j * C;  // character-minor: lanes share key records
+        const float al = b.alpha[c];
+        float4 q = slerp_pre(__ldg(KA0 + 2 * j), __ldg(KA1 + 2 * j), __ldg(KA0 + 2 * j + 1).w, al);
+        const float4 ta0 = __ldg(KA0 + 2 * j + 1), ta1 = __ldg(KA1 + 2 * j + 1);
+        float tx = fmaf(al, ta1.x - ta0.x, ta0.x), ty = fmaf(al, ta1.y - ta0.y, ta0.y),
+              tz = fmaf(al, ta1.z - ta0.z, ta0.z);
+        if (two) {
+          const float4 tb0 = __ldg(KB0 + 2 * j + 1), tb1 = __ldg(KB1 + 2 * j + 1);
+          const float4 qb = slerp_pre(__ldg(KB0 + 2 * j), __ldg(KB1 + 2 * j), tb0.w, al);
+          const float w = b.blend[c];
+          q = slerp_unit(q, qb, w);
+          tx = fmaf(w, fmaf(al, tb1.x - tb0.x, tb0.x) - tx, tx);
+          ty = fmaf(w, fmaf(al, tb1.y - tb0.y, tb0.y) - ty, ty);
+          tz = fmaf(w, fmaf(al, tb1.z - tb0.z, tb0.z) - tz, tz);
+        }
+        sts_qt(P + c * cs2 + 2 * j, QT{q, make_float4(tx, ty, tz, 0.f)});
+      }
+    }
+    compute_sync();
+
+    // ---- pass 1b: running products along segments
+    {
+      const int NS = nseg * C;
+      for (int idx = tid; idx < NS; idx += kComputeThreads) {
+        const int g = (int)b.divC.div(idx), c = idx - g * C;
+        const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1];
+        float4 *Pc = P + c * cs2;
+        QT acc = lds_qt(Pc + 2 * a0);
+        if (a0 + 1 >= a1) continue;
+        QT nxt = lds_qt(Pc + 2 * (a0 + 1));
+        for (int j = a0 + 1; j < a1; ++j) {
+          const QT L = nxt;
+          if (j + 1 < a1) nxt = lds_qt(Pc + 2 * (j + 1));
+          acc = qt_mul(acc, L);
+          sts_qt(Pc + 2 * j, acc);
+        }
+      }
+    }
+    compute_sync();
+
+    // ---- pass 2: pointer jumping over segments (Y double-buffered)
+    const float4 *Y;
+    {
+      const int CS = C * nseg;
+      float4 *Y0 = Lt.Y0, *Y1 = Lt.Y1;
+      int16_t *ptr0 = Lt.ptr0, *ptr1 = Lt.ptr1;
+      for (int idx = tid; idx < CS; idx += kComputeThreads) {
+        const int c = (int)b.divS.div(idx), g = idx - c * nseg;
+        const int lk = Lt.seg_link[g];
+        const QT y = lk < 0 ? QT{make_float4(0.f, 0.f, 0.f, 1.f), make_float4(0.f, 0.f, 0.f, 0.f)}
+                            : lds_qt(P + c * cs2 + 2 * lk);
+        sts_qt(Y0 + 2 * idx, y);
+        if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(Lt.jinfo[lk] & kJ16Seg));
+      }
+      compute_sync();
+      float4 *yc = Y0, *yn = Y1;
+      int16_t *pc = ptr0, *pn = ptr1;
+      for (int r = 0; r < b.T.rounds; ++r) {
+        for (int idx = tid; idx < CS; idx += kComputeThreads) {
+          const int c = (int)b.divS.div(idx), g = idx - c * nseg;
+          const int p = pc[g];
+          QT y = lds_qt(yc + 2 * idx);
+          if (p >= 0) y = qt_mul(lds_qt(yc + 2 * (c * nseg + p)), y);
+          sts_qt(yn + 2 * idx, y);
+          if (c == 0) pn[g] = (int16_t)(p >= 0 ? pc[p] : -1);
+        }
+        compute_sync();
+        float4 *tf = yc;
+        yc = yn;
+        yn = tf;
+        int16_t *tp = pc;
+        pc = pn;
+        pn = tp;
+      }
+      Y = yc;
+    }
+
+    // ---- pass 3: model pose, normalize, matrix, bind, store
+    {
+      const int W = n * b.cgroups, cpt = b.cpt;
+      float4 *skin4 = reinterpret_cast<float4 *>(a.skin);
+      for (int idx = tid; idx < W; idx += kComputeThreads) {
+        const int grp = (int)b.divN.div(idx), j = idx - grp * n;
+        const uint32_t info = Lt.jinfo[j];
+        const int g = (int)(info & kJ16Seg);
+        const Aff B = ldg_aff(b.T.inv_bind + 3 * j);
+        const int c1 = min(C, (grp + 1) * cpt);
+        for (int c = grp * cpt; c < c1; ++c) {
+          QT m = lds_qt(P + c * cs2 + 2 * j);
+          if (info & kJ16Link) m = qt_mul(lds_qt(Y + 2 * (c * nseg + g)), m);
+          const Aff M = aff_from_qt(normalize4(m.q), m.t.x, m.t.y, m.t.z);
+          stg_aff(skin4 + (b.off[c] + j) * 3, aff_mul(M, B));
+        }
+      }
+    }
+    cur ^= 1;
+    handoff_sync();
+  }
+  if (tid == 0 && a.done) last_cta_reset(a.queue_head, a.done);
+}
+
+template <int MINB>
+static cudaError_t launch_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
+  static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
+  if (cfg.smem > set_smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_frame_qt<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    set_smem = cfg.smem;
+  }
+  k_frame_qt<MINB><<<cfg.ctas, cfg.threads, cfg.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t frame_qt_smem_bytes(int n, int nseg, int C) {
+  return 16ull * ((size_t)C * (2 * (size_t)n + 1) + 4ull * C * nseg) + item_table_bytes(n, nseg);
+}
+
+cudaError_t launch_frame_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
+  return cfg.min_blocks >= 3 ? launch_qt<3>(a, cfg, st) : launch_qt<2>(a, cfg, st);
+}
+
+}  // namespace anim
