@@ -93,25 +93,36 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
       const float4 *KB0 = b.T.keys + (size_t)(nk + k0) * n * 2;
       const float4 *KB1 = b.T.keys + (size_t)(nk + k1) * n * 2;
       const bool two = b.T.n_clips >= 2;
-      const int CN = C * n;
-#pragma unroll 2
-      for (int idx = tid; idx < CN; idx += kComputeThreads) {
-        const int j = (int)b.divC.div(idx), c = idx - j * C;  // character-minor: lanes share key records
-        const float al = b.alpha[c];
-        float4 q = slerp_pre(__ldg(KA0 + 2 * j), __ldg(KA1 + 2 * j), __ldg(KA0 + 2 * j + 1).w, al);
-        const float4 ta0 = __ldg(KA0 + 2 * j + 1), ta1 = __ldg(KA1 + 2 * j + 1);
-        float tx = fmaf(al, ta1.x - ta0.x, ta0.x), ty = fmaf(al, ta1.y - ta0.y, ta0.y),
-              tz = fmaf(al, ta1.z - ta0.z, ta0.z);
+      // joint-major: a thread loads joint j's key records once and samples
+      // them for its group of characters (the pass-3 grouping)
+      const int W = n * b.cgroups, cpt = b.cpt;
+      for (int idx = tid; idx < W; idx += kComputeThreads) {
+        const int grp = (int)b.divN.div(idx), j = idx - grp * n;
+        const float4 qa0 = __ldg(KA0 + 2 * j), ta0 = __ldg(KA0 + 2 * j + 1);
+        const float4 qa1 = __ldg(KA1 + 2 * j), ta1 = __ldg(KA1 + 2 * j + 1);
+        float4 qb0 = qa0, tb0 = ta0, qb1 = qa1, tb1 = ta1;
         if (two) {
-          const float4 tb0 = __ldg(KB0 + 2 * j + 1), tb1 = __ldg(KB1 + 2 * j + 1);
-          const float4 qb = slerp_pre(__ldg(KB0 + 2 * j), __ldg(KB1 + 2 * j), tb0.w, al);
-          const float w = b.blend[c];
-          q = slerp_unit(q, qb, w);
-          tx = fmaf(w, fmaf(al, tb1.x - tb0.x, tb0.x) - tx, tx);
-          ty = fmaf(w, fmaf(al, tb1.y - tb0.y, tb0.y) - ty, ty);
-          tz = fmaf(w, fmaf(al, tb1.z - tb0.z, tb0.z) - tz, tz);
+          qb0 = __ldg(KB0 + 2 * j);
+          tb0 = __ldg(KB0 + 2 * j + 1);
+          qb1 = __ldg(KB1 + 2 * j);
+          tb1 = __ldg(KB1 + 2 * j + 1);
         }
-        sts_qt(P + c * cs2 + 2 * j, QT{q, make_float4(tx, ty, tz, 0.f)});
+        const int c1 = min(C, (grp + 1) * cpt);
+        for (int c = grp * cpt; c < c1; ++c) {
+          const float al = b.alpha[c];
+          float4 q = slerp_pre(qa0, qa1, ta0.w, al);
+          float tx = fmaf(al, ta1.x - ta0.x, ta0.x), ty = fmaf(al, ta1.y - ta0.y, ta0.y),
+                tz = fmaf(al, ta1.z - ta0.z, ta0.z);
+          if (two) {
+            const float4 qb = slerp_pre(qb0, qb1, tb0.w, al);
+            const float w = b.blend[c];
+            q = slerp_unit(q, qb, w);
+            tx = fmaf(w, fmaf(al, tb1.x - tb0.x, tb0.x) - tx, tx);
+            ty = fmaf(w, fmaf(al, tb1.y - tb0.y, tb0.y) - ty, ty);
+            tz = fmaf(w, fmaf(al, tb1.z - tb0.z, tb0.z) - tz, tz);
+          }
+          sts_qt(P + c * cs2 + 2 * j, QT{q, make_float4(tx, ty, tz, 0.f)});
+        }
       }
     }
     compute_sync();
