@@ -65,6 +65,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
   const int tid = threadIdx.x;
+  // launched with programmatic stream serialization after the work-queue
+  // kernel: wait for its grid to complete before reading anything it wrote
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
 
   if (tid >= kComputeThreads) {
@@ -82,7 +85,6 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
     const int cs2 = 2 * n + 1;  // float4 stride between characters (16 B skew)
     const ItemLayout Lt = item_layout_qt(sm, C, n, nseg);
     float4 *P = Lt.P;
-    compute_sync();
 
     // ---- pass 1a: local poses (q, t) from the clips; tables staged alongside
     stage_tables(b, Lt, tid);
@@ -216,8 +218,19 @@ static cudaError_t launch_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream
     if (e != cudaSuccess) return e;
     set_smem = cfg.smem;
   }
-  k_frame_qt<MINB><<<cfg.ctas, cfg.threads, cfg.smem, st>>>(a);
-  return cudaGetLastError();
+  // programmatic stream serialization: the CTAs become resident while the
+  // preceding work-queue kernel runs and wait in griddepcontrol.wait
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)cfg.ctas);
+  lc.blockDim = dim3((unsigned)cfg.threads);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, k_frame_qt<MINB>, a);
 }
 
 }  // namespace

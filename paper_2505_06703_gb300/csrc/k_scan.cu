@@ -334,6 +334,10 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
   __shared__ int s_warp[32];
   __shared__ int s_total, s_itotal;
   const int tid = threadIdx.x, nth = blockDim.x;
+  // a frame kernel launched after this one with programmatic stream
+  // serialization may start now; it waits for this grid's completion (and
+  // its memory) in griddepcontrol.wait before reading the queue
+  asm volatile("griddepcontrol.launch_dependents;");
   if (blockIdx.x == 0 && tid == 0) *a.queue_head = 0;  // consumed by the next launch in stream order
   const RangeDev R = a.ranges[blockIdx.x];
   const int nk = a.types[R.type].n_keys;
