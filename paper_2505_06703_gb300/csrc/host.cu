@@ -1793,7 +1793,7 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   };
   anim_ctx::TuneChoice best{0, 0, 0, 0, 0, 1e30f};
   const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {256, 512, 1024, 2048, 4096};
-  const int adjs[] = {0, 4, 6, 8};
+  const int adjs[] = {0, 4, 6, 7, 8};
   // the chain-walk kernel serves the frame only, the adjoint kernel choice
   // the adjoint only: other searches keep the context's settings
   const int walk_lo = which == 0 ? 0 : ctx->use_walk, walk_hi = which == 0 ? 1 : ctx->use_walk;

@@ -22,7 +22,7 @@ namespace anim {
 // float4 each (+1 spare), then the view's subtree ends, parents and gather
 // map as int16 [n] each.
 size_t adjoint_smem_bytes(int n, int nseg, int C) {
-  return scan_item_bytes(n, nseg, C) + 16ull * 2ull * ((size_t)C * (n + 1) + 1) + (6ull * n + 15) / 16 * 16;
+  return qt_item_bytes(n, nseg, C) + 16ull * 2ull * ((size_t)C * (n + 1) + 1) + (6ull * n + 15) / 16 * 16;
 }
 
 __device__ __forceinline__ float3 cross3(const float3 a, const float3 b) {
@@ -112,8 +112,8 @@ template <int MODE, int NT>
 __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf &b, float4 *sm, float4 *wsF,
                                              float4 *wsT, int tid, int step) {
   const int C = b.C, n = b.T.n, nseg = b.T.nseg;
-  const int cs4 = 3 * n + 1;
-  const ItemLayout Lt = item_layout(sm, C, n, nseg);
+  const int cs2 = 2 * n + 1;  // the forward scan keeps (q, t) pairs
+  const ItemLayout Lt = item_layout_qt(sm, C, n, nseg);
   float4 *P = Lt.P;
   float4 *PF = Lt.end;                // [C][n+1]
   float4 *PT = PF + C * (n + 1) + 1;  // [C][n+1] (+1: the scan's total)
@@ -130,7 +130,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     gat16[j] = (int16_t)(gath ? __ldg(gat + j) : j);
   }
 
-  // ---- pass 1a: local matrices from (q, t); the joint's loss input
+  // ---- pass 1a: local poses (q normalized, t); the joint's loss input
   // (dLoss/dp or target) is fetched alongside into its depth-first slot
   stage_tables<NT>(b, Lt, tid);
   {
@@ -141,7 +141,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       const long long row = b.off[c] + (gath ? __ldg(gat + j) : j);
       const float4 q = normalize4(__ldg(q4 + row));
       const float *tp = a.t + 3 * row;
-      sts_aff(P + c * cs4 + 3 * j, aff_from_qt(q, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2)));
+      sts_qt(P + c * cs2 + 2 * j, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
       if (MODE != 2) {
         const float *src = (MODE == 0 ? a.grad_pos : a.target) + 3 * row;
         PF[c * (n + 1) + j] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), 0.f);
@@ -149,23 +149,24 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     }
   }
   pass_sync<NT>();
-  pass1b<NT>(b, Lt, P, cs4, tid);
+  pass1b_qt<NT>(b, Lt, P, cs2, tid);
   pass_sync<NT>();
-  const float4 *Y = pass2<NT>(b, Lt, P, cs4, tid);
+  const float4 *Y = pass2_qt<NT>(b, Lt, P, cs2, tid);
 
   // ---- model poses in place and the per-slot terms (g, p x g) in the same
   // pass; loss terms in F.w; slot n of each character is zero
   for (int idx = tid; idx < CN; idx += NT) {
     const int c = (int)b.divN.div(idx), j = idx - c * n;
     const uint32_t info = Lt.jinfo[j];
-    float4 *slot = P + c * cs4 + 3 * j;
+    float4 *slot = P + c * cs2 + 2 * j;
     float3 p;
     if (info & kJ16Link) {
-      const Aff m = aff_mul(lds_aff(Y + 3 * (c * nseg + (int)(info & kJ16Seg))), lds_aff(slot));
-      sts_aff(slot, m);
-      p = make_float3(m.r0.w, m.r1.w, m.r2.w);
+      const QT m = qt_mul(lds_qt(Y + 2 * (c * nseg + (int)(info & kJ16Seg))), lds_qt(slot));
+      sts_qt(slot, m);
+      p = make_float3(m.t.x, m.t.y, m.t.z);
     } else {
-      p = make_float3(slot[0].w, slot[1].w, slot[2].w);
+      const float4 t = slot[1];
+      p = make_float3(t.x, t.y, t.z);
     }
     const int i = j;
     float3 g = make_float3(0.f, 0.f, 0.f);
@@ -194,7 +195,8 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       const int c = idx / a.n_eff, e = idx - c * a.n_eff;
       const int j = __ldg(a.eff_slot + b.type * a.n_eff + e);
       const int i = j;
-      const float3 p = make_float3(P[c * cs4 + 3 * j].w, P[c * cs4 + 3 * j + 1].w, P[c * cs4 + 3 * j + 2].w);
+      const float4 pt = P[c * cs2 + 2 * j + 1];
+      const float3 p = make_float3(pt.x, pt.y, pt.z);
       const float *tg = a.target + ((size_t)b.cid[c] * a.n_eff + e) * 3;
       const float dx = p.x - __ldg(tg), dy = p.y - __ldg(tg + 1), dz = p.z - __ldg(tg + 2);
       const float3 g = make_float3(2.f * dx, 2.f * dy, 2.f * dz);
@@ -222,17 +224,17 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     const float4 t0 = PT[c * (n + 1) + i], t1 = PT[c * (n + 1) + e];
     const float3 F = make_float3(f1.x - f0.x, f1.y - f0.y, f1.z - f0.z);
     const float3 Tq = make_float3(t1.x - t0.x, t1.y - t0.y, t1.z - t0.z);
-    const float3 p = make_float3(P[c * cs4 + 3 * j].w, P[c * cs4 + 3 * j + 1].w, P[c * cs4 + 3 * j + 2].w);
+    const float4 pt = P[c * cs2 + 2 * j + 1];
+    const float3 p = make_float3(pt.x, pt.y, pt.z);
     const float3 pf = cross3(p, F);
     const float3 tw = make_float3(Tq.x - pf.x, Tq.y - pf.y, Tq.z - pf.z);
     const int par = par16[j];
     float3 tau = tw, dt = F;
-    if (par >= 0) {
-      const float4 r0 = P[c * cs4 + 3 * par], r1 = P[c * cs4 + 3 * par + 1], r2 = P[c * cs4 + 3 * par + 2];
-      tau = make_float3(r0.x * tw.x + r1.x * tw.y + r2.x * tw.z, r0.y * tw.x + r1.y * tw.y + r2.y * tw.z,
-                        r0.z * tw.x + r1.z * tw.y + r2.z * tw.z);
-      dt = make_float3(r0.x * F.x + r1.x * F.y + r2.x * F.z, r0.y * F.x + r1.y * F.y + r2.y * F.z,
-                       r0.z * F.x + r1.z * F.y + r2.z * F.z);
+    if (par >= 0) {  // into the parent's frame: R_par^T = R(conj(q_par))
+      const float4 qp = normalize4(P[c * cs2 + 2 * par]);
+      const float4 qc = make_float4(-qp.x, -qp.y, -qp.z, qp.w);
+      tau = qrot(qc, tw);
+      dt = qrot(qc, F);
     }
     const long long row = b.off[c] + gat16[j];
     const float4 q = __ldg(reinterpret_cast<const float4 *>(a.q) + row);
@@ -311,7 +313,7 @@ static_assert(sizeof(ItemBuf) + 2 * (kAdjSmallThreads / 32) * 16 <= kAdjSmallSta
 // hardware schedules the items in waves.  Suits many small items, where the
 // persistent kernel would run each CTA's items one after another.
 template <int MODE>
-__global__ void __launch_bounds__(kAdjSmallThreads, 4) k_adjoint_small(const AdjointArgs a) {
+__global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const AdjointArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf b;
   __shared__ float4 wsF[kAdjSmallThreads / 32], wsT[kAdjSmallThreads / 32];

@@ -1,9 +1,7 @@
 // The plain fused frame (Simulation -> Hierarchy-Scan -> Bind MeshPose,
 // Sec. 1 steps 1-3, Eq. 1) with rigid transforms kept as (quaternion,
 // translation) pairs -- 32 bytes per joint instead of a 48-byte 3x4 matrix
-// -- while the segmented scan runs in shared memory.  The local poses are
-// rigid (unit scale), so the pair is an exact representation:
-//   (qa, ta) o (qb, tb) = (qa qb, ta + R(qa) tb).
+// -- while the segmented scan runs in shared memory (scan_core.cuh).
 // The smaller item footprint lets more characters be in flight per SM, which
 // is what bounds the latency-limited scan passes.  The bind pass normalizes
 // the composed quaternion once (removing the norm drift of long products),
@@ -19,46 +17,6 @@
 namespace anim {
 
 namespace {
-
-struct QT {
-  float4 q;  // x y z w
-  float4 t;  // x y z (w unused)
-};
-
-__device__ __forceinline__ QT lds_qt(const float4 *p) { return QT{p[0], p[1]}; }
-__device__ __forceinline__ void sts_qt(float4 *p, const QT &a) {
-  p[0] = a.q;
-  p[1] = a.t;
-}
-
-// R(q) v for a unit quaternion q: v + 2 w (u x v) + 2 u x (u x v), u = q.xyz.
-__device__ __forceinline__ float3 qrot(const float4 q, const float4 v) {
-  const float cx = 2.f * (q.y * v.z - q.z * v.y), cy = 2.f * (q.z * v.x - q.x * v.z), cz = 2.f * (q.x * v.y - q.y * v.x);
-  return make_float3(fmaf(q.w, cx, v.x) + (q.y * cz - q.z * cy), fmaf(q.w, cy, v.y) + (q.z * cx - q.x * cz),
-                     fmaf(q.w, cz, v.z) + (q.x * cy - q.y * cx));
-}
-
-__device__ __forceinline__ QT qt_mul(const QT &a, const QT &b) {
-  const float3 r = qrot(a.q, b.t);
-  return QT{qmul(a.q, b.q), make_float4(a.t.x + r.x, a.t.y + r.y, a.t.z + r.z, 0.f)};
-}
-
-// Item layout: P [C][2n + 1] float4, Y0 / Y1 [C][nseg][2] float4, then the
-// type's segment tables as in the matrix layout.
-__device__ __forceinline__ ItemLayout item_layout_qt(float4 *sm, int C, int n, int nseg) {
-  ItemLayout L;
-  L.P = sm;
-  L.Y0 = L.P + C * (2 * n + 1);
-  L.Y1 = L.Y0 + 2 * C * nseg;
-  char *t = reinterpret_cast<char *>(L.Y1 + 2 * C * nseg);
-  L.ptr0 = reinterpret_cast<int16_t *>(t);
-  L.ptr1 = L.ptr0 + nseg;
-  L.seg_start = reinterpret_cast<int32_t *>(t + 4 * nseg);
-  L.seg_link = L.seg_start + nseg + 1;
-  L.jinfo = reinterpret_cast<uint16_t *>(L.seg_link + nseg);
-  L.end = reinterpret_cast<float4 *>(t + item_table_bytes(n, nseg));
-  return L;
-}
 
 template <int MINB>
 __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a) {
@@ -130,61 +88,10 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
     compute_sync();
 
     // ---- pass 1b: running products along segments
-    {
-      const int NS = nseg * C;
-      for (int idx = tid; idx < NS; idx += kComputeThreads) {
-        const int g = (int)b.divC.div(idx), c = idx - g * C;
-        const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1];
-        float4 *Pc = P + c * cs2;
-        QT acc = lds_qt(Pc + 2 * a0);
-        if (a0 + 1 >= a1) continue;
-        QT nxt = lds_qt(Pc + 2 * (a0 + 1));
-        for (int j = a0 + 1; j < a1; ++j) {
-          const QT L = nxt;
-          if (j + 1 < a1) nxt = lds_qt(Pc + 2 * (j + 1));
-          acc = qt_mul(acc, L);
-          sts_qt(Pc + 2 * j, acc);
-        }
-      }
-    }
+    pass1b_qt(b, Lt, P, cs2, tid);
     compute_sync();
-
-    // ---- pass 2: pointer jumping over segments (Y double-buffered)
-    const float4 *Y;
-    {
-      const int CS = C * nseg;
-      float4 *Y0 = Lt.Y0, *Y1 = Lt.Y1;
-      int16_t *ptr0 = Lt.ptr0, *ptr1 = Lt.ptr1;
-      for (int idx = tid; idx < CS; idx += kComputeThreads) {
-        const int c = (int)b.divS.div(idx), g = idx - c * nseg;
-        const int lk = Lt.seg_link[g];
-        const QT y = lk < 0 ? QT{make_float4(0.f, 0.f, 0.f, 1.f), make_float4(0.f, 0.f, 0.f, 0.f)}
-                            : lds_qt(P + c * cs2 + 2 * lk);
-        sts_qt(Y0 + 2 * idx, y);
-        if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(Lt.jinfo[lk] & kJ16Seg));
-      }
-      compute_sync();
-      float4 *yc = Y0, *yn = Y1;
-      int16_t *pc = ptr0, *pn = ptr1;
-      for (int r = 0; r < b.T.rounds; ++r) {
-        for (int idx = tid; idx < CS; idx += kComputeThreads) {
-          const int c = (int)b.divS.div(idx), g = idx - c * nseg;
-          const int p = pc[g];
-          QT y = lds_qt(yc + 2 * idx);
-          if (p >= 0) y = qt_mul(lds_qt(yc + 2 * (c * nseg + p)), y);
-          sts_qt(yn + 2 * idx, y);
-          if (c == 0) pn[g] = (int16_t)(p >= 0 ? pc[p] : -1);
-        }
-        compute_sync();
-        float4 *tf = yc;
-        yc = yn;
-        yn = tf;
-        int16_t *tp = pc;
-        pc = pn;
-        pn = tp;
-      }
-      Y = yc;
-    }
+    // ---- pass 2: pointer jumping over segments
+    const float4 *Y = pass2_qt(b, Lt, P, cs2, tid);
 
     // ---- pass 3: model pose, normalize, matrix, bind, store
     {
@@ -235,9 +142,7 @@ static cudaError_t launch_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream
 
 }  // namespace
 
-size_t frame_qt_smem_bytes(int n, int nseg, int C) {
-  return 16ull * ((size_t)C * (2 * (size_t)n + 1) + 4ull * C * nseg) + item_table_bytes(n, nseg);
-}
+size_t frame_qt_smem_bytes(int n, int nseg, int C) { return qt_item_bytes(n, nseg, C); }
 
 cudaError_t launch_frame_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   return cfg.min_blocks >= 3 ? launch_qt<3>(a, cfg, st) : launch_qt<2>(a, cfg, st);

@@ -314,4 +314,110 @@ __host__ __device__ inline size_t scan_item_bytes(int n, int nseg, int C) {
   return 16ull * ((size_t)C * (3 * (size_t)n + 1) + 6ull * C * nseg) + item_table_bytes(n, nseg);
 }
 
+// ---- the same scan on rigid transforms kept as (quaternion, translation)
+// pairs.  The local poses are rigid (unit scale), so the pair is an exact
+// representation: (qa, ta) o (qb, tb) = (qa qb, ta + R(qa) tb), 32 bytes per
+// joint in shared memory instead of a 48-byte 3x4 matrix.
+struct QT {
+  float4 q;  // x y z w
+  float4 t;  // x y z (w unused)
+};
+__device__ __forceinline__ QT lds_qt(const float4 *p) { return QT{p[0], p[1]}; }
+__device__ __forceinline__ void sts_qt(float4 *p, const QT &a) {
+  p[0] = a.q;
+  p[1] = a.t;
+}
+// R(q) v for a unit quaternion q: v + 2 w (u x v) + 2 u x (u x v), u = q.xyz.
+__device__ __forceinline__ float3 qrot(const float4 q, const float3 v) {
+  const float cx = 2.f * (q.y * v.z - q.z * v.y), cy = 2.f * (q.z * v.x - q.x * v.z),
+              cz = 2.f * (q.x * v.y - q.y * v.x);
+  return make_float3(fmaf(q.w, cx, v.x) + (q.y * cz - q.z * cy), fmaf(q.w, cy, v.y) + (q.z * cx - q.x * cz),
+                     fmaf(q.w, cz, v.z) + (q.x * cy - q.y * cx));
+}
+__device__ __forceinline__ QT qt_mul(const QT &a, const QT &b) {
+  const float3 r = qrot(a.q, make_float3(b.t.x, b.t.y, b.t.z));
+  return QT{qmul(a.q, b.q), make_float4(a.t.x + r.x, a.t.y + r.y, a.t.z + r.z, 0.f)};
+}
+__device__ __forceinline__ QT qt_identity() {
+  return QT{make_float4(0.f, 0.f, 0.f, 1.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+}
+
+// Item layout: P [C][2n + 1] float4, Y0 / Y1 [C][nseg][2] float4, then the
+// type's segment tables as in the matrix layout.
+__device__ __forceinline__ ItemLayout item_layout_qt(float4 *sm, int C, int n, int nseg) {
+  ItemLayout L;
+  L.P = sm;
+  L.Y0 = L.P + C * (2 * n + 1);
+  L.Y1 = L.Y0 + 2 * C * nseg;
+  char *t = reinterpret_cast<char *>(L.Y1 + 2 * C * nseg);
+  L.ptr0 = reinterpret_cast<int16_t *>(t);
+  L.ptr1 = L.ptr0 + nseg;
+  L.seg_start = reinterpret_cast<int32_t *>(t + 4 * nseg);
+  L.seg_link = L.seg_start + nseg + 1;
+  L.jinfo = reinterpret_cast<uint16_t *>(L.seg_link + nseg);
+  L.end = reinterpret_cast<float4 *>(t + item_table_bytes(n, nseg));
+  return L;
+}
+__host__ __device__ inline size_t qt_item_bytes(int n, int nseg, int C) {
+  return 16ull * ((size_t)C * (2 * (size_t)n + 1) + 4ull * C * nseg) + item_table_bytes(n, nseg);
+}
+
+// Pass 1b on (q, t) pairs: running products along each segment, in place
+// (P's character stride cs2 in float4).
+template <int NT = kComputeThreads>
+__device__ __forceinline__ void pass1b_qt(const ItemBuf &b, const ItemLayout &Lt, float4 *P, int cs2, int tid) {
+  const int C = b.C, NS = b.T.nseg * C;
+  for (int idx = tid; idx < NS; idx += NT) {
+    const int g = (int)b.divC.div(idx), c = idx - g * C;
+    const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1];
+    float4 *Pc = P + c * cs2;
+    QT acc = lds_qt(Pc + 2 * a0);
+    if (a0 + 1 >= a1) continue;
+    QT nxt = lds_qt(Pc + 2 * (a0 + 1));
+    for (int j = a0 + 1; j < a1; ++j) {
+      const QT L = nxt;
+      if (j + 1 < a1) nxt = lds_qt(Pc + 2 * (j + 1));
+      acc = qt_mul(acc, L);
+      sts_qt(Pc + 2 * j, acc);
+    }
+  }
+}
+
+// Pass 2 on (q, t) pairs + its barriers; returns the buffer holding Y.
+template <int NT = kComputeThreads>
+__device__ __forceinline__ float4 *pass2_qt(const ItemBuf &b, const ItemLayout &Lt, const float4 *P, int cs2,
+                                            int tid) {
+  const int nseg = b.T.nseg;
+  const int CS = b.C * nseg;
+  float4 *Y0 = Lt.Y0, *Y1 = Lt.Y1;
+  int16_t *ptr0 = Lt.ptr0, *ptr1 = Lt.ptr1;
+  for (int idx = tid; idx < CS; idx += NT) {
+    const int c = (int)b.divS.div(idx), g = idx - c * nseg;
+    const int lk = Lt.seg_link[g];
+    sts_qt(Y0 + 2 * idx, lk < 0 ? qt_identity() : lds_qt(P + c * cs2 + 2 * lk));
+    if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(Lt.jinfo[lk] & kJ16Seg));
+  }
+  pass_sync<NT>();
+  float4 *cur = Y0, *nxt = Y1;
+  int16_t *pc = ptr0, *pn = ptr1;
+  for (int r = 0; r < b.T.rounds; ++r) {
+    for (int idx = tid; idx < CS; idx += NT) {
+      const int c = (int)b.divS.div(idx), g = idx - c * nseg;
+      const int p = pc[g];
+      QT y = lds_qt(cur + 2 * idx);
+      if (p >= 0) y = qt_mul(lds_qt(cur + 2 * (c * nseg + p)), y);
+      sts_qt(nxt + 2 * idx, y);
+      if (c == 0) pn[g] = (int16_t)(p >= 0 ? pc[p] : -1);
+    }
+    pass_sync<NT>();
+    float4 *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    int16_t *tp = pc;
+    pc = pn;
+    pn = tp;
+  }
+  return cur;
+}
+
 }  // namespace anim
