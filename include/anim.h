@@ -169,6 +169,19 @@ ANIM_API int anim_plan_vertex_offsets(anim_ctx *ctx, const anim_plan *plan, int6
 ANIM_API int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
                         float *d_skin, void *stream);
 
+/* The fused frame from and to host memory, for callers whose inputs and
+ * outputs live on the host: h_time and h_blend_w (host [n_chars] float) are
+ * copied in, the frame runs as in anim_evaluate_frame, and the skin matrices
+ * are copied back into h_skin (host [total][12] float), all in order on
+ * `stream`; the output is complete once `stream` has synchronized.
+ * Page-locked buffers (cudaMallocHost, cudaHostRegister) make the copies
+ * asynchronous; pageable ones work through the driver's staging.  The device
+ * staging buffers (n_chars x 8 B + total x 48 B) belong to the plan and are
+ * allocated by the first call, which is therefore not capturable in a CUDA
+ * graph; later calls are. */
+ANIM_API int anim_evaluate_frame_host(anim_ctx *ctx, anim_plan *plan, const float *h_time, const float *h_blend_w,
+                             float *h_skin, void *stream);
+
 /* The fused frame followed by linear blend skinning of every character's
  * mesh, fused into the same kernel: vertex v of character c goes to
  * sum_k w_k S_{b_k} [p; 1] with normal normalize(sum_k w_k R_{b_k} n), where

@@ -39,6 +39,7 @@ SIGNATURES = {
     "anim_raster": (c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame_layers": (c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame": (c_int, [_P, _P, _P, _P, _P, _P]),
+    "anim_evaluate_frame_host": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_evaluate_frame_levelsync": (c_int, [_P, _P, _P, _P, _P, _P]),
     "anim_frame_build_queue": (c_int, [_P, _P, _P, _P]),
     "anim_frame_run_queue": (c_int, [_P, _P, _P, _P, _P, _P]),
@@ -250,6 +251,24 @@ class Context:
         out = self._out(plan, 12, out)
         fn = self.lib.anim_evaluate_frame_levelsync if levelsync else self.lib.anim_evaluate_frame
         self._ck(fn(self.h, plan.h, _dptr(time), _dptr(blend_w), _dptr(out), _stream(stream)))
+        return out
+
+    def evaluate_frame_host(self, plan, time, blend_w, out=None, stream=None):
+        """The frame from and to host memory: time, blend_w are CPU float32
+        tensors [n_chars] (page-locked for asynchronous copies); returns the
+        CPU tensor [total, 12] the skin matrices are copied into (page-locked
+        when allocated here).  Complete once `stream` has synchronized."""
+        import torch
+        for x in (time, blend_w):
+            if x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous() or x.numel() != plan.n_chars:
+                raise ValueError("time and blend_w must be contiguous CPU float32 tensors [n_chars]")
+        if out is None:
+            out = torch.empty((plan.total, 12), dtype=torch.float32, pin_memory=True)
+        if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != plan.total * 12:
+            raise ValueError("out must be a contiguous CPU float32 tensor [total, 12]")
+        self._ck(self.lib.anim_evaluate_frame_host(self.h, plan.h, c_void_p(time.data_ptr()),
+                                                   c_void_p(blend_w.data_ptr()), c_void_p(out.data_ptr()),
+                                                   _stream(stream)))
         return out
 
     def frame_build_queue(self, plan, time, stream=None):

@@ -612,12 +612,14 @@ struct anim_plan {
   int32_t *d_cap_cta = nullptr;
   int n_ranges_cta = 0, n_slots_cta = 0;
   std::vector<int64_t> vert_off;  // [n_chars + 1]
-  int64_t *d_vert_off = nullptr;  // a type whose adjoint working set does not fit this schedule, else -1
+  int64_t *d_vert_off = nullptr;
+  float *d_host_in = nullptr, *d_host_skin = nullptr;  // staging of the host-buffer frame
   ~anim_plan() {
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
                     (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
                     (void *)d_n_items, (void *)d_queue, (void *)d_used,
-                    (void *)d_cap, (void *)d_ranges_cta, (void *)d_cap_cta, (void *)d_vert_off})
+                    (void *)d_cap, (void *)d_ranges_cta, (void *)d_cap_cta, (void *)d_vert_off,
+                    (void *)d_host_in, (void *)d_host_skin})
       if (p) cudaFree(p);
   }
 };
@@ -1347,6 +1349,33 @@ int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_tim
   rc = anim_frame_build_queue(ctx, plan, d_time, stream);
   if (rc) return rc;
   return anim_frame_run_queue(ctx, plan, d_time, d_blend_w, d_skin, stream);
+}
+
+int anim_evaluate_frame_host(anim_ctx *ctx, anim_plan *plan, const float *h_time, const float *h_blend_w,
+                             float *h_skin, void *stream) {
+  int rc = check_plan(ctx, plan);
+  if (rc || plan->n_chars == 0) return rc;
+  if (!h_time || !h_blend_w || !h_skin) return fail(ctx, ANIM_EINVAL, "NULL host pointer");
+  CK(cudaSetDevice(ctx->device));
+  const size_t n = (size_t)plan->n_chars, n_pad = (n + 3) / 4 * 4;
+  if (!plan->d_host_in) {
+    CK(cudaMalloc(&plan->d_host_in, 2 * n_pad * sizeof(float)));
+    cudaError_t e = cudaMalloc(&plan->d_host_skin, (size_t)plan->total * 48);
+    if (e != cudaSuccess) {
+      cudaFree(plan->d_host_in);
+      plan->d_host_in = nullptr;
+      plan->d_host_skin = nullptr;
+      return fail(ctx, ANIM_ECUDA, "%s", cudaGetErrorString(e));
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  float *d_time = plan->d_host_in, *d_blend = plan->d_host_in + n_pad;
+  CK(cudaMemcpyAsync(d_time, h_time, n * sizeof(float), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_blend, h_blend_w, n * sizeof(float), cudaMemcpyHostToDevice, st));
+  rc = anim_evaluate_frame(ctx, plan, d_time, d_blend, plan->d_host_skin, stream);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h_skin, plan->d_host_skin, (size_t)plan->total * 48, cudaMemcpyDeviceToHost, st));
+  return ANIM_OK;
 }
 
 int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,

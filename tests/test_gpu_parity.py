@@ -93,6 +93,26 @@ def test_frame_repeatable_and_graph_capturable(torch):
     assert torch.equal(out, a)
 
 
+def test_frame_from_host_buffers(torch):
+    """The host-buffer entry point (inputs copied in, skin matrices copied
+    back inside the call) gives the device entry point's frame bit for bit,
+    for page-locked and pageable buffers, and the oracle's within tolerance."""
+    w = synth.subset(synth.config3(), list(range(0, 10000, 7)))
+    ctx, plan = _gpu.setup(w)
+    ref = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])).cpu()
+    h_t = torch.as_tensor(w["time"]).pin_memory()
+    h_w = torch.as_tensor(w["weight"]).pin_memory()
+    out = ctx.evaluate_frame_host(plan, h_t, h_w)
+    torch.cuda.synchronize()
+    assert out.is_pinned() and torch.equal(out, ref)
+    pageable = torch.zeros((plan.total, 12), dtype=torch.float32)
+    ctx.evaluate_frame_host(plan, torch.as_tensor(w["time"]).clone(), torch.as_tensor(w["weight"]).clone(),
+                            out=pageable)
+    torch.cuda.synchronize()
+    assert torch.equal(pageable, ref)
+    _gpu.assert_skin_close(out.numpy(), oracle.frame(w), w)
+
+
 def test_autotuned_frame_parity(torch):
     """anim_tune picks a schedule by timing candidates; the tuned frame still
     matches the oracle and a second tune of the same mix hits the cache."""
