@@ -141,7 +141,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       const long long row = b.off[c] + (gath ? __ldg(gat + j) : j);
       const float4 q = normalize4(__ldg(q4 + row));
       const float *tp = a.t + 3 * row;
-      sts_qt(P + c * cs2 + 2 * j, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
+      sts_qt(P + c * cs2, j, n, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
       if (MODE != 2) {
         const float *src = (MODE == 0 ? a.grad_pos : a.target) + 3 * row;
         PF[c * (n + 1) + j] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), 0.f);
@@ -158,14 +158,14 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
   for (int idx = tid; idx < CN; idx += NT) {
     const int c = (int)b.divN.div(idx), j = idx - c * n;
     const uint32_t info = Lt.jinfo[j];
-    float4 *slot = P + c * cs2 + 2 * j;
+    float4 *Pc = P + c * cs2;
     float3 p;
     if (info & kJ16Link) {
-      const QT m = qt_mul(lds_qt(Y + 2 * (c * nseg + (int)(info & kJ16Seg))), lds_qt(slot));
-      sts_qt(slot, m);
+      const QT m = qt_mul(lds_qt(Y, c * nseg + (int)(info & kJ16Seg), C * nseg), lds_qt(Pc, j, n));
+      sts_qt(Pc, j, n, m);
       p = make_float3(m.t.x, m.t.y, m.t.z);
     } else {
-      const float4 t = slot[1];
+      const float4 t = Pc[n + j];
       p = make_float3(t.x, t.y, t.z);
     }
     const int i = j;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       const int c = idx / a.n_eff, e = idx - c * a.n_eff;
       const int j = __ldg(a.eff_slot + b.type * a.n_eff + e);
       const int i = j;
-      const float4 pt = P[c * cs2 + 2 * j + 1];
+      const float4 pt = P[c * cs2 + n + j];
       const float3 p = make_float3(pt.x, pt.y, pt.z);
       const float *tg = a.target + ((size_t)b.cid[c] * a.n_eff + e) * 3;
       const float dx = p.x - __ldg(tg), dy = p.y - __ldg(tg + 1), dz = p.z - __ldg(tg + 2);
@@ -224,14 +224,14 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     const float4 t0 = PT[c * (n + 1) + i], t1 = PT[c * (n + 1) + e];
     const float3 F = make_float3(f1.x - f0.x, f1.y - f0.y, f1.z - f0.z);
     const float3 Tq = make_float3(t1.x - t0.x, t1.y - t0.y, t1.z - t0.z);
-    const float4 pt = P[c * cs2 + 2 * j + 1];
+    const float4 pt = P[c * cs2 + n + j];
     const float3 p = make_float3(pt.x, pt.y, pt.z);
     const float3 pf = cross3(p, F);
     const float3 tw = make_float3(Tq.x - pf.x, Tq.y - pf.y, Tq.z - pf.z);
     const int par = par16[j];
     float3 tau = tw, dt = F;
     if (par >= 0) {  // into the parent's frame: R_par^T = R(conj(q_par))
-      const float4 qp = normalize4(P[c * cs2 + 2 * par]);
+      const float4 qp = normalize4(P[c * cs2 + par]);
       const float4 qc = make_float4(-qp.x, -qp.y, -qp.z, qp.w);
       tau = qrot(qc, tw);
       dt = qrot(qc, F);

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
             ty = fmaf(w, fmaf(al, tb1.y - tb0.y, tb0.y) - ty, ty);
             tz = fmaf(w, fmaf(al, tb1.z - tb0.z, tb0.z) - tz, tz);
           }
-          sts_qt(P + c * cs2 + 2 * j, QT{q, make_float4(tx, ty, tz, 0.f)});
+          sts_qt(P + c * cs2, j, n, QT{q, make_float4(tx, ty, tz, 0.f)});
         }
       }
     }
@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
         const Aff B = ldg_aff(b.T.inv_bind + 3 * j);
         const int c1 = min(C, (grp + 1) * cpt);
         for (int c = grp * cpt; c < c1; ++c) {
-          QT m = lds_qt(P + c * cs2 + 2 * j);
-          if (info & kJ16Link) m = qt_mul(lds_qt(Y + 2 * (c * nseg + g)), m);
+          QT m = lds_qt(P + c * cs2, j, n);
+          if (info & kJ16Link) m = qt_mul(lds_qt(Y, c * nseg + g, C * nseg), m);
           const Aff M = aff_from_qt(normalize4(m.q), m.t.x, m.t.y, m.t.z);
           stg_aff(skin4 + (b.off[c] + j) * 3, aff_mul(M, B));
         }

@@ -322,10 +322,12 @@ struct QT {
   float4 q;  // x y z w
   float4 t;  // x y z (w unused)
 };
-__device__ __forceinline__ QT lds_qt(const float4 *p) { return QT{p[0], p[1]}; }
-__device__ __forceinline__ void sts_qt(float4 *p, const QT &a) {
-  p[0] = a.q;
-  p[1] = a.t;
+// Pairs are stored as two planes, q at base[j] and t at base[half + j], so
+// lanes on consecutive j touch consecutive 16-byte slots.
+__device__ __forceinline__ QT lds_qt(const float4 *base, int j, int half) { return QT{base[j], base[half + j]}; }
+__device__ __forceinline__ void sts_qt(float4 *base, int j, int half, const QT &a) {
+  base[j] = a.q;
+  base[half + j] = a.t;
 }
 // R(q) v for a unit quaternion q: v + 2 w (u x v) + 2 u x (u x v), u = q.xyz.
 __device__ __forceinline__ float3 qrot(const float4 q, const float3 v) {
@@ -342,7 +344,8 @@ __device__ __forceinline__ QT qt_identity() {
   return QT{make_float4(0.f, 0.f, 0.f, 1.f), make_float4(0.f, 0.f, 0.f, 0.f)};
 }
 
-// Item layout: P [C][2n + 1] float4, Y0 / Y1 [C][nseg][2] float4, then the
+// Item layout: P [C][2n + 1] float4 (per character a q plane of n, a t plane
+// of n, one pad), Y0 / Y1 [2][C * nseg] float4 (q plane, t plane), then the
 // type's segment tables as in the matrix layout.
 __device__ __forceinline__ ItemLayout item_layout_qt(float4 *sm, int C, int n, int nseg) {
   ItemLayout L;
@@ -369,16 +372,16 @@ __device__ __forceinline__ void pass1b_qt(const ItemBuf &b, const ItemLayout &Lt
   const int C = b.C, NS = b.T.nseg * C;
   for (int idx = tid; idx < NS; idx += NT) {
     const int g = (int)b.divC.div(idx), c = idx - g * C;
-    const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1];
+    const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1], n = b.T.n;
     float4 *Pc = P + c * cs2;
-    QT acc = lds_qt(Pc + 2 * a0);
+    QT acc = lds_qt(Pc, a0, n);
     if (a0 + 1 >= a1) continue;
-    QT nxt = lds_qt(Pc + 2 * (a0 + 1));
+    QT nxt = lds_qt(Pc, a0 + 1, n);
     for (int j = a0 + 1; j < a1; ++j) {
       const QT L = nxt;
-      if (j + 1 < a1) nxt = lds_qt(Pc + 2 * (j + 1));
+      if (j + 1 < a1) nxt = lds_qt(Pc, j + 1, n);
       acc = qt_mul(acc, L);
-      sts_qt(Pc + 2 * j, acc);
+      sts_qt(Pc, j, n, acc);
     }
   }
 }
@@ -387,14 +390,14 @@ __device__ __forceinline__ void pass1b_qt(const ItemBuf &b, const ItemLayout &Lt
 template <int NT = kComputeThreads>
 __device__ __forceinline__ float4 *pass2_qt(const ItemBuf &b, const ItemLayout &Lt, const float4 *P, int cs2,
                                             int tid) {
-  const int nseg = b.T.nseg;
+  const int nseg = b.T.nseg, n = b.T.n;
   const int CS = b.C * nseg;
   float4 *Y0 = Lt.Y0, *Y1 = Lt.Y1;
   int16_t *ptr0 = Lt.ptr0, *ptr1 = Lt.ptr1;
   for (int idx = tid; idx < CS; idx += NT) {
     const int c = (int)b.divS.div(idx), g = idx - c * nseg;
     const int lk = Lt.seg_link[g];
-    sts_qt(Y0 + 2 * idx, lk < 0 ? qt_identity() : lds_qt(P + c * cs2 + 2 * lk));
+    sts_qt(Y0, idx, CS, lk < 0 ? qt_identity() : lds_qt(P + c * cs2, lk, n));
     if (c == 0) ptr0[g] = (int16_t)(lk < 0 ? -1 : (int)(Lt.jinfo[lk] & kJ16Seg));
   }
   pass_sync<NT>();
@@ -404,9 +407,9 @@ __device__ __forceinline__ float4 *pass2_qt(const ItemBuf &b, const ItemLayout &
     for (int idx = tid; idx < CS; idx += NT) {
       const int c = (int)b.divS.div(idx), g = idx - c * nseg;
       const int p = pc[g];
-      QT y = lds_qt(cur + 2 * idx);
-      if (p >= 0) y = qt_mul(lds_qt(cur + 2 * (c * nseg + p)), y);
-      sts_qt(nxt + 2 * idx, y);
+      QT y = lds_qt(cur, idx, CS);
+      if (p >= 0) y = qt_mul(lds_qt(cur, c * nseg + p, CS), y);
+      sts_qt(nxt, idx, CS, y);
       if (c == 0) pn[g] = (int16_t)(p >= 0 ? pc[p] : -1);
     }
     pass_sync<NT>();
