@@ -318,12 +318,19 @@ __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const Adj
   __shared__ ItemBuf b;
   __shared__ float4 wsF[kAdjSmallThreads / 32], wsT[kAdjSmallThreads / 32];
   const int tid = threadIdx.x;
-  const int step = (MODE == 2) ? *a.step + 1 : 0;
+  // Launched with programmatic stream serialization: the next launch's CTAs
+  // may become resident now and stage their items (plan data only: item
+  // descriptor, type table, character rows) while this grid finishes.
+  asm volatile("griddepcontrol.launch_dependents;");
   if (tid < 32) {
     const WorkItem wi = a.items[blockIdx.x];
     stage_item<1>(b, (int)blockIdx.x, wi, a.types, a.item_chars, a.row_off, nullptr, nullptr, a.status);
   }
+  // poses, targets, the IK step counter and the outputs may belong to the
+  // preceding kernel in the stream: wait for it to complete
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
+  const int step = (MODE == 2) ? *a.step + 1 : 0;
   adjoint_item<MODE, kAdjSmallThreads>(a, b, sm, wsF, wsT, tid, step);
   if (MODE == 2 && tid == 0) {  // the last CTA advances the IK step
     __threadfence();
@@ -345,8 +352,17 @@ static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cuda
       if (e != cudaSuccess) return e;
       set_small = cfg.smem;
     }
-    k_adjoint_small<MODE><<<a.n_items, kAdjSmallThreads, cfg.smem, st>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)a.n_items);
+    lc.blockDim = dim3((unsigned)kAdjSmallThreads);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k_adjoint_small<MODE>, a);
   }
   static size_t set_smem = 0;
   if (cfg.smem > set_smem) {
