@@ -314,7 +314,7 @@ def run_ours(args) -> dict:
     achieved = alg / (k_ms / 1e3) / 1e9
     tr = NCU_TRAFFIC.get(kernel_source_hash())
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": tr, "kernel": "k_frame_qt (persistent frame)",
+                "frac": round(achieved / peak, 4), "traffic": tr, "kernel": "k_scan_qt<0> (persistent frame)",
                 "kernel_ms": round(k_ms, 5), "algorithmic_bytes": alg, "peak_source": peak_src}
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,

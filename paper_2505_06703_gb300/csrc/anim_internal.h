@@ -136,7 +136,8 @@ struct ScanArgs {
   const float *add_w;
 };
 
-cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+// The matrix frame kernel: with the skinning pass (a.verts) or layered blending (a.layer_w).
+cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 // Frame work queue.  The plan cuts the characters of each type (types in
 // cost order) into ranges of at most kRangeChars, each owning a region of
@@ -268,10 +269,11 @@ cudaError_t launch_bind_from_rest(const int32_t *parent, const float *rest_q, co
 // Shared-memory footprint of one work item of C characters (bytes).
 size_t scan_smem_bytes(int n, int nseg, int C);
 size_t adjoint_smem_bytes(int n, int nseg, int C);
-size_t frame_qt_smem_bytes(int n, int nseg, int C);
+size_t scan_qt_smem_bytes(int n, int nseg, int C);
 
-// The plain frame with (quaternion, translation) items (MODE 0, skin
-// matrices out, no skinning or layers).
-cudaError_t launch_frame_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+// The scan on (quaternion, translation) items: mode 0 the plain frame (skin
+// matrices out, no skinning or layers), mode 1 the forward from local poses
+// (skin and / or model matrices out).
+cudaError_t launch_scan_qt(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 }  // namespace anim

@@ -741,7 +741,7 @@ int choose_C(const anim_ctx *ctx, const TypeHost &T, int kind) {
   int C = std::max(1, std::min(kCMax, ctx->joints_per_item / std::max(1, T.n)));
   auto bytes = [&](int c) {
     return kind == 1 ? adjoint_smem_bytes(T.n, T.seg.nseg, c)
-                     : kind == 2 ? frame_qt_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
+                     : kind == 2 ? scan_qt_smem_bytes(T.n, T.seg.nseg, c) : scan_smem_bytes(T.n, T.seg.nseg, c);
   };
   while (C > 1 && bytes(C) > budget) --C;
   if (bytes(C) > ctx->smem_optin - kStaticSmemAllowance) return 0;
@@ -785,7 +785,7 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->C_adj.assign(nt, 1);
   P->C_frame.assign(nt, 1);
   P->adj_unfit = -1;
-  size_t smem_s = 0, smem_a = 0;
+  size_t smem_s = 0, smem_a = 0, smem_q = 0;
   for (int t : P->used) {
     const TypeHost &T = *ctx->types[t];
     const int cs = choose_C(ctx, T, 0), ca = choose_C(ctx, *T.adj, 1);
@@ -796,6 +796,7 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
     P->C_scan[t] = cs;
     P->C_frame[t] = std::max(cs, choose_C(ctx, T, 2));  // (q, t) items are smaller
     smem_s = std::max(smem_s, scan_smem_bytes(T.n, T.seg.nseg, cs));
+    smem_q = std::max(smem_q, scan_qt_smem_bytes(T.n, T.seg.nseg, P->C_frame[t]));
     // the adjoint keeps two more vectors per joint: a schedule may fit the
     // forward kernels and not the adjoint, which then refuses to run
     if (ca == 0) {
@@ -805,7 +806,8 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
     P->C_adj[t] = ca;
     smem_a = std::max(smem_a, adjoint_smem_bytes(T.adj->n, T.adj->seg.nseg, ca));
   }
-  auto is = make_items(P, P->C_scan), ia = make_items(P, P->C_adj);
+  // static items: (q, t) items for the forward from local poses, adjoint items
+  auto is = make_items(P, P->C_frame), ia = make_items(P, P->C_adj);
   P->n_items_scan = (int)is.size();
   P->n_items_adj = (int)ia.size();
   CK(upload_vec(&P->d_items_scan, is));
@@ -820,7 +822,7 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   for (int t : P->used) {
     const TypeHost &T = *ctx->types[t];
     if (!ctx->use_walk || T.ws.mode == 0) {
-      smem_f = std::max(smem_f, frame_qt_smem_bytes(T.n, T.seg.nseg, P->C_frame[t]));
+      smem_f = std::max(smem_f, scan_qt_smem_bytes(T.n, T.seg.nseg, P->C_frame[t]));
       continue;
     }
     walk_t[t] = 1;
@@ -892,7 +894,7 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->d_items_frame = nullptr;
   CK(cudaMalloc(&P->d_items_frame, std::max(1, std::max(slots, slots_cta)) * sizeof(WorkItem)));
   const int grid = ctx->sm_count * ctx->ctas_per_sm;
-  P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_s, 16),
+  P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_q, 16),
                  ctx->ctas_per_sm >= 3 ? 3 : 2};
   if (ctx->adj_ctas > 0)
     P->cfg_adj = {kAdjSmallThreads, std::max(1, P->n_items_adj), std::max<size_t>(smem_a, 16)};
@@ -1314,7 +1316,7 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
     LaunchCfg cfg = plan->cfg_scan;
     cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
     cfg.smem = plan->smem_frame;
-    CK(launch_frame_qt(a, cfg, cta_st));
+    CK(launch_scan_qt(0, a, cfg, cta_st));
   }
   if (has_walk) {
     WalkArgs w{};
@@ -1415,7 +1417,7 @@ int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const floa
   LaunchCfg cfg = plan->cfg_scan;
   cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
   cfg.smem = plan->smem_frame_mat;
-  CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
+  CK(launch_scan(a, cfg, (cudaStream_t)stream));
   return ANIM_OK;
 }
 
@@ -1455,7 +1457,7 @@ int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float
   LaunchCfg cfg = plan->cfg_scan;
   cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
   cfg.smem = plan->smem_frame_mat;
-  CK(launch_scan(0, a, cfg, (cudaStream_t)stream));
+  CK(launch_scan(a, cfg, (cudaStream_t)stream));
   return ANIM_OK;
 }
 
@@ -1507,7 +1509,7 @@ int anim_forward_local(anim_ctx *ctx, const anim_plan *plan, const float *d_q, c
   a.t = d_t;
   a.skin = d_skin;
   a.model = d_model;
-  CK(launch_scan(1, a, plan->cfg_scan, st));
+  CK(launch_scan_qt(1, a, plan->cfg_scan, st));
   return ANIM_OK;
 }
 

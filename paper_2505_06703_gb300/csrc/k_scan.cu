@@ -134,16 +134,15 @@ __device__ __forceinline__ void skin_mesh(const ItemBuf &b, const float4 *P, int
   }
 }
 
-// Persistent kernel.  Work item = C characters of one type (for the frame:
-// characters sharing the key index k0, so they read the same key records).
-// Compute warps run passes 1a/1b/2/3 in shared memory and thread 0 streams
-// the finished character blocks out with bulk copies; the producer warp
-// stages the next item meanwhile.
-//   MODE 0: local poses sampled from the type's clips at each character's time;
-//   MODE 1: local poses read from q [total][4] (normalized here), t [total][3].
-// FEAT (frame only): 0 plain, 1 with the skinning pass, 2 with layered
-// blending -- separate instantiations so the plain frame carries neither.
-template <int MODE, bool SKIN, bool MODEL, int MINB, int FEAT>
+// Persistent frame kernel on 3x4 matrices for the frames that need the skin
+// matrices in shared memory after the scan (the plain frame and the forward
+// from local poses run on (q, t) items, k_scan_qt.cu).  Work item = C
+// characters of one type sharing the key index k0, so they read the same key
+// records.  Compute warps run passes 1a/1b/2/3 in shared memory and thread 0
+// streams the finished character blocks out with bulk copies; the producer
+// warp stages the next item meanwhile.
+// FEAT 1: with the skinning pass; FEAT 2: with layered blending.
+template <int MINB, int FEAT>
 __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
@@ -151,9 +150,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
 
   if (tid >= kComputeThreads) {
-    producer_loop<MODE>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time,
-                        a.blend_w, a.status, FEAT == 1 ? a.vert_off : nullptr,
-                        FEAT == 2 ? LayerIn{a.layer_w, a.add_w} : LayerIn{nullptr, nullptr});
+    producer_loop<0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time, a.blend_w,
+                     a.status, FEAT == 1 ? a.vert_off : nullptr,
+                     FEAT == 2 ? LayerIn{a.layer_w, a.add_w} : LayerIn{nullptr, nullptr});
     return;
   }
 
@@ -176,9 +175,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     // ---- pass 1a: local matrices of every (joint, character); the type's
     // tables are staged into shared memory alongside
     stage_tables(b, Lt, tid);
-    if (MODE == 0 && FEAT == 2) {
+    if (FEAT == 2) {
       sample_layers_pass(b, P, cs4, tid);
-    } else if (MODE == 0) {
+    } else {
       const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
       const float4 *KA0 = b.T.keys + (size_t)k0 * n * 2;
       const float4 *KA1 = b.T.keys + (size_t)k1 * n * 2;
@@ -202,8 +201,6 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
         }
         sts_aff(P + c * cs4 + 3 * j, sample_local(r, b.alpha[c], b.blend[c], two));
       }
-    } else {
-      pass1a_qt(b, P, cs4, a.q, a.t, tid);
     }
     compute_sync();
 
@@ -220,22 +217,19 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
         const int grp = (int)b.divN.div(idx), j = idx - grp * n;
         const uint32_t info = Lt.jinfo[j];
         const int g = (int)(info & kJ16Seg);
-        Aff B;
-        if (SKIN) B = ldg_aff(b.T.inv_bind + 3 * j);
+        const Aff B = ldg_aff(b.T.inv_bind + 3 * j);
         const int c1 = min(C, (grp + 1) * cpt);
         for (int c = grp * cpt; c < c1; ++c) {
           float4 *slot = P + c * cs4 + 3 * j;
           Aff m = lds_aff(slot);
           if (info & kJ16Link) m = aff_mul(lds_aff(Y + 3 * (c * nseg + g)), m);
-          if (MODEL && SKIN) stg_aff(reinterpret_cast<float4 *>(a.model) + (b.off[c] + j) * 3, m);
-          if (SKIN) m = aff_mul(m, B);
-          sts_aff(slot, m);
+          sts_aff(slot, aff_mul(m, B));
         }
       }
     }
     fence_proxy_async_smem();
     compute_sync();
-    float *dst = SKIN ? a.skin : a.model;
+    float *dst = a.skin;  // NULL: the skinned frame keeps the skin matrices on chip
     if (tid == 0 && dst) {
       const uint32_t bytes = (uint32_t)n * 48u;
       for (int c = 0; c < C; ++c) bulk_store(dst + b.off[c] * 12, P + c * cs4, bytes);
@@ -244,7 +238,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     }
     // ---- pass 4 (frame with skinning): linear blend skinning of the
     // characters' meshes from the skin matrices still in shared memory
-    if (MODE == 0 && SKIN && FEAT == 1) skin_mesh(b, P, cs4, a.verts, tid);
+    if (FEAT == 1) skin_mesh(b, P, cs4, a.verts, tid);
     cur ^= 1;
     handoff_sync();
   }
@@ -252,9 +246,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   if (tid == 0 && a.done) last_cta_reset(a.queue_head, a.done);
 }
 
-template <int MODE, bool SKIN, bool MODEL, int MINB, int FEAT>
+template <int MINB, int FEAT>
 static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  auto k = k_scan<MODE, SKIN, MODEL, MINB, FEAT>;
+  auto k = k_scan<MINB, FEAT>;
   static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
   if (cfg.smem > set_smem) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
@@ -265,21 +259,10 @@ static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaSt
   return cudaGetLastError();
 }
 
-template <int MINB>
-static cudaError_t launch_scan_m(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  const bool skin = a.skin != nullptr, model = a.model != nullptr;
-  if (mode == 0) {
-    if (a.verts) return launch_scan_t<0, true, false, MINB, 1>(a, cfg, st);
-    if (a.layer_w) return launch_scan_t<0, true, false, MINB, 2>(a, cfg, st);
-    return launch_scan_t<0, true, false, MINB, 0>(a, cfg, st);
-  }
-  if (skin && model) return launch_scan_t<1, true, true, MINB, 0>(a, cfg, st);
-  if (skin) return launch_scan_t<1, true, false, MINB, 0>(a, cfg, st);
-  return launch_scan_t<1, false, true, MINB, 0>(a, cfg, st);
-}
-
-cudaError_t launch_scan(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  return cfg.min_blocks >= 3 ? launch_scan_m<3>(mode, a, cfg, st) : launch_scan_m<2>(mode, a, cfg, st);
+cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
+  if (!a.verts && !a.layer_w) return cudaErrorInvalidValue;  // the plain frame runs on k_scan_qt
+  if (cfg.min_blocks >= 3) return a.verts ? launch_scan_t<3, 1>(a, cfg, st) : launch_scan_t<3, 2>(a, cfg, st);
+  return a.verts ? launch_scan_t<2, 1>(a, cfg, st) : launch_scan_t<2, 2>(a, cfg, st);
 }
 
 // ------------------------------------------------------------ work queue

@@ -1,13 +1,16 @@
-// The plain fused frame (Simulation -> Hierarchy-Scan -> Bind MeshPose,
-// Sec. 1 steps 1-3, Eq. 1) with rigid transforms kept as (quaternion,
-// translation) pairs -- 32 bytes per joint instead of a 48-byte 3x4 matrix
-// -- while the segmented scan runs in shared memory (scan_core.cuh).
+// The segmented Hierarchy-Scan (Eq. 1) with rigid transforms kept as
+// (quaternion, translation) pairs -- 32 bytes per joint instead of a 48-byte
+// 3x4 matrix -- while it runs in shared memory (scan_core.cuh):
+//   MODE 0  the plain fused frame (Simulation -> Hierarchy-Scan -> Bind
+//           MeshPose, Sec. 1 steps 1-3): local poses sampled from the clips;
+//   MODE 1  the forward from given local poses q [total][4] (normalized
+//           here), t [total][3], skin and / or model matrices out.
 // The smaller item footprint lets more characters be in flight per SM, which
 // is what bounds the latency-limited scan passes.  The bind pass normalizes
 // the composed quaternion once (removing the norm drift of long products),
-// forms M = [R(q) | t] and writes S = M B straight to global memory.
-// Same item pipeline as k_scan (producer warp, 8 compute warps, work queue);
-// the skinning and layered-blend variants of the frame keep the matrix form.
+// forms M = [R(q) | t] and writes M and / or S = M B straight to global
+// memory.  Same item pipeline as k_scan (producer warp, 8 compute warps,
+// work queue); the skinning and layered-blend frames keep the matrix form.
 #include <cuda_runtime.h>
 
 #include "anim_internal.h"
@@ -18,19 +21,20 @@ namespace anim {
 
 namespace {
 
-template <int MINB>
-__global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a) {
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
   const int tid = threadIdx.x;
-  // launched with programmatic stream serialization after the work-queue
-  // kernel: wait for its grid to complete before reading anything it wrote
+  // launched with programmatic stream serialization (after the work-queue
+  // kernel, for the frame): wait for the preceding grid to complete before
+  // reading anything it may have written
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
 
   if (tid >= kComputeThreads) {
-    producer_loop<0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time, a.blend_w,
-                     a.status);
+    producer_loop<MODE>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time,
+                        a.blend_w, a.status);
     return;
   }
 
@@ -44,9 +48,23 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
     const ItemLayout Lt = item_layout_qt(sm, C, n, nseg);
     float4 *P = Lt.P;
 
-    // ---- pass 1a: local poses (q, t) from the clips; tables staged alongside
+    // ---- pass 1a: local poses (q, t) from the clips or the caller's rows;
+    // tables staged alongside
     stage_tables(b, Lt, tid);
-    {
+    if (MODE == 1) {
+      // character-major: consecutive lanes read consecutive rows
+      const float4 *q4 = reinterpret_cast<const float4 *>(a.q);
+      const int32_t *gat = b.T.gather;
+      const int CN = C * n;
+#pragma unroll 2
+      for (int idx = tid; idx < CN; idx += kComputeThreads) {
+        const int c = (int)b.divN.div(idx), j = idx - c * n;
+        const long long row = b.off[c] + (gat ? __ldg(gat + j) : j);
+        const float4 q = normalize4(__ldg(q4 + row));
+        const float *tp = a.t + 3 * row;
+        sts_qt(P + c * cs2, j, n, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
+      }
+    } else {
       const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
       const float4 *KA0 = b.T.keys + (size_t)k0 * n * 2;
       const float4 *KA1 = b.T.keys + (size_t)k1 * n * 2;
@@ -93,21 +111,25 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
     // ---- pass 2: pointer jumping over segments
     const float4 *Y = pass2_qt(b, Lt, P, cs2, tid);
 
-    // ---- pass 3: model pose, normalize, matrix, bind, store
+    // ---- pass 3: model pose, normalize, matrix, (bind,) store
     {
       const int W = n * b.cgroups, cpt = b.cpt;
       float4 *skin4 = reinterpret_cast<float4 *>(a.skin);
+      float4 *model4 = reinterpret_cast<float4 *>(a.model);
+      const bool skin = MODE == 0 || skin4 != nullptr, model = MODE == 1 && model4 != nullptr;
       for (int idx = tid; idx < W; idx += kComputeThreads) {
         const int grp = (int)b.divN.div(idx), j = idx - grp * n;
         const uint32_t info = Lt.jinfo[j];
         const int g = (int)(info & kJ16Seg);
-        const Aff B = ldg_aff(b.T.inv_bind + 3 * j);
+        Aff B;
+        if (skin) B = ldg_aff(b.T.inv_bind + 3 * j);
         const int c1 = min(C, (grp + 1) * cpt);
         for (int c = grp * cpt; c < c1; ++c) {
           QT m = lds_qt(P + c * cs2, j, n);
           if (info & kJ16Link) m = qt_mul(lds_qt(Y, c * nseg + g, C * nseg), m);
           const Aff M = aff_from_qt(normalize4(m.q), m.t.x, m.t.y, m.t.z);
-          stg_aff(skin4 + (b.off[c] + j) * 3, aff_mul(M, B));
+          if (model) stg_aff(model4 + (b.off[c] + j) * 3, M);
+          if (skin) stg_aff(skin4 + (b.off[c] + j) * 3, aff_mul(M, B));
         }
       }
     }
@@ -117,16 +139,17 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_frame_qt(const ScanArgs a
   if (tid == 0 && a.done) last_cta_reset(a.queue_head, a.done);
 }
 
-template <int MINB>
+template <int MODE, int MINB>
 static cudaError_t launch_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
   if (cfg.smem > set_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_frame_qt<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_scan_qt<MODE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
     set_smem = cfg.smem;
   }
   // programmatic stream serialization: the CTAs become resident while the
-  // preceding work-queue kernel runs and wait in griddepcontrol.wait
+  // preceding kernel runs and wait in griddepcontrol.wait
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)cfg.ctas);
   lc.blockDim = dim3((unsigned)cfg.threads);
@@ -137,15 +160,16 @@ static cudaError_t launch_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream
   at[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, k_frame_qt<MINB>, a);
+  return cudaLaunchKernelEx(&lc, k_scan_qt<MODE, MINB>, a);
 }
 
 }  // namespace
 
-size_t frame_qt_smem_bytes(int n, int nseg, int C) { return qt_item_bytes(n, nseg, C); }
+size_t scan_qt_smem_bytes(int n, int nseg, int C) { return qt_item_bytes(n, nseg, C); }
 
-cudaError_t launch_frame_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  return cfg.min_blocks >= 3 ? launch_qt<3>(a, cfg, st) : launch_qt<2>(a, cfg, st);
+cudaError_t launch_scan_qt(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
+  if (mode == 0) return cfg.min_blocks >= 3 ? launch_qt<0, 3>(a, cfg, st) : launch_qt<0, 2>(a, cfg, st);
+  return cfg.min_blocks >= 3 ? launch_qt<1, 3>(a, cfg, st) : launch_qt<1, 2>(a, cfg, st);
 }
 
 }  // namespace anim
