@@ -136,7 +136,7 @@ struct ScanArgs {
   const float *add_w;
 };
 
-// The matrix frame kernel: with the skinning pass (a.verts) or layered blending (a.layer_w).
+// The matrix frame kernel with the skinning pass (a.verts).
 cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 // Frame work queue.  The plan cuts the characters of each type (types in
@@ -272,8 +272,8 @@ size_t adjoint_smem_bytes(int n, int nseg, int C);
 size_t scan_qt_smem_bytes(int n, int nseg, int C);
 
 // The scan on (quaternion, translation) items: mode 0 the plain frame (skin
-// matrices out, no skinning or layers), mode 1 the forward from local poses
-// (skin and / or model matrices out).
+// matrices out), mode 1 the forward from local poses (skin and / or model
+// matrices out), mode 2 the frame with layered blending.
 cudaError_t launch_scan_qt(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 }  // namespace anim

@@ -611,6 +611,9 @@ struct anim_plan {
   RangeDev *d_ranges_cta = nullptr;
   int32_t *d_cap_cta = nullptr;
   int n_ranges_cta = 0, n_slots_cta = 0;
+  RangeDev *d_ranges_qa = nullptr;  // (q, t) items of every type: the frame with layered blending
+  int32_t *d_cap_qa = nullptr;
+  int n_ranges_qa = 0, n_slots_qa = 0;
   std::vector<int64_t> vert_off;  // [n_chars + 1]
   int64_t *d_vert_off = nullptr;
   float *d_host_in = nullptr, *d_host_skin = nullptr;  // staging of the host-buffer frame
@@ -619,6 +622,7 @@ struct anim_plan {
                     (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
                     (void *)d_n_items, (void *)d_queue, (void *)d_used,
                     (void *)d_cap, (void *)d_ranges_cta, (void *)d_cap_cta, (void *)d_vert_off,
+                    (void *)d_ranges_qa, (void *)d_cap_qa,
                     (void *)d_host_in, (void *)d_host_skin})
       if (p) cudaFree(p);
   }
@@ -864,35 +868,42 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->n_ranges = (int)ranges.size();
   P->n_slots = slots;
   CK(upload_vec(&P->d_ranges, ranges));
-  // the matrix-item layout of every type for the frame with skinning or layers
-  std::vector<RangeDev> ranges_cta;
-  int slots_cta = 0;
-  {
+  // layouts of every type on one kernel: matrix items (the frame with
+  // skinning) and (q, t) items (the frame with layered blending)
+  auto all_types = [&](const std::vector<int> &Cv, std::vector<RangeDev> &out) {
+    int sl = 0;
     for (size_t u = 0; u < P->used.size(); ++u) {
       const int t = P->used[u];
-      const int cnt = (int)P->by_type[u].size(), C = P->C_scan[t], nk = ctx->types[t]->n_keys;
+      const int cnt = (int)P->by_type[u].size(), C = Cv[t], nk = ctx->types[t]->n_keys;
       for (int k = 0; k < cnt; k += kRangeChars) {
         RangeDev r;
         r.type = t;
         r.start = P->type_chars_start[u] + k;
         r.count = std::min(kRangeChars, cnt - k);
-        r.region = slots_cta;
-        slots_cta += (r.count + C - 1) / C + std::min(r.count, std::max(nk, 1));
-        ranges_cta.push_back(r);
+        r.region = sl;
+        sl += (r.count + C - 1) / C + std::min(r.count, std::max(nk, 1));
+        out.push_back(r);
       }
     }
-  }
+    return sl;
+  };
+  std::vector<RangeDev> ranges_cta, ranges_qa;
+  const int slots_cta = all_types(P->C_scan, ranges_cta), slots_qa = all_types(P->C_frame, ranges_qa);
   P->n_ranges_cta = (int)ranges_cta.size();
   P->n_slots_cta = slots_cta;
   CK(upload_vec(&P->d_ranges_cta, ranges_cta));
   CK(upload_vec(&P->d_cap_cta, P->C_scan));
+  P->n_ranges_qa = (int)ranges_qa.size();
+  P->n_slots_qa = slots_qa;
+  CK(upload_vec(&P->d_ranges_qa, ranges_qa));
+  CK(upload_vec(&P->d_cap_qa, P->C_frame));
   P->vert_off.assign(P->n_chars + 1, 0);
   for (int64_t c = 0; c < P->n_chars; ++c)
     P->vert_off[c + 1] = P->vert_off[c] + ctx->types[P->char_type[c]]->n_verts;
   CK(upload_vec(&P->d_vert_off, P->vert_off));
   if (P->d_items_frame) cudaFree(P->d_items_frame);
   P->d_items_frame = nullptr;
-  CK(cudaMalloc(&P->d_items_frame, std::max(1, std::max(slots, slots_cta)) * sizeof(WorkItem)));
+  CK(cudaMalloc(&P->d_items_frame, std::max({1, slots, slots_cta, slots_qa}) * sizeof(WorkItem)));
   const int grid = ctx->sm_count * ctx->ctas_per_sm;
   P->cfg_scan = {kScanThreads, std::max(1, std::min(grid, P->n_items_scan)), std::max<size_t>(smem_q, 16),
                  ctx->ctas_per_sm >= 3 ? 3 : 2};
@@ -1387,7 +1398,7 @@ int anim_evaluate_frame_skinned(anim_ctx *ctx, const anim_plan *plan, const floa
   if (!d_blend_w || !d_verts) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
   if (!aligned16(d_verts) || (d_skin && !aligned16(d_skin)) || !aligned4(d_blend_w))
     return fail(ctx, ANIM_EINVAL, "d_verts, d_skin must be 16-byte aligned, d_blend_w 4-byte aligned");
-  BucketArgs bk{};  // matrix items of every type (the plain frame's layout differs)
+  BucketArgs bk{};  // matrix items of every type
   bk.ranges = plan->d_ranges_cta;
   bk.n_ranges = plan->n_ranges_cta;
   bk.n_slots = plan->n_slots_cta;
@@ -1428,14 +1439,14 @@ int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float
   if (!d_weights || !d_skin) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
   if (!aligned16(d_skin) || !aligned4(d_weights) || (d_add_w && !aligned4(d_add_w)))
     return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned, d_weights and d_add_w 4-byte aligned");
-  BucketArgs bk{};  // matrix items of every type (the plain frame's layout differs)
-  bk.ranges = plan->d_ranges_cta;
-  bk.n_ranges = plan->n_ranges_cta;
-  bk.n_slots = plan->n_slots_cta;
+  BucketArgs bk{};  // (q, t) items of every type (the plain frame gives some to the walk kernel)
+  bk.ranges = plan->d_ranges_qa;
+  bk.n_ranges = plan->n_ranges_qa;
+  bk.n_slots = plan->n_slots_qa;
   bk.type_chars = plan->d_type_chars;
   bk.time = d_time;
   bk.types = ctx->d_types;
-  bk.cap = plan->d_cap_cta;
+  bk.cap = plan->d_cap_qa;
   bk.sorted = plan->d_sorted;
   bk.items = plan->d_items_frame;
   bk.queue_head = plan->d_queue;
@@ -1454,10 +1465,9 @@ int anim_evaluate_frame_layers(anim_ctx *ctx, const anim_plan *plan, const float
   a.skin = d_skin;
   a.layer_w = d_weights;
   a.add_w = d_add_w;
-  LaunchCfg cfg = plan->cfg_scan;
+  LaunchCfg cfg = plan->cfg_scan;  // its shared memory covers every type's (q, t) item
   cfg.ctas = ctx->sm_count * ctx->ctas_per_sm;
-  cfg.smem = plan->smem_frame_mat;
-  CK(launch_scan(a, cfg, (cudaStream_t)stream));
+  CK(launch_scan_qt(2, a, cfg, (cudaStream_t)stream));
   return ANIM_OK;
 }
 

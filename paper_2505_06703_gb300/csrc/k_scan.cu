@@ -37,67 +37,6 @@ __device__ __forceinline__ Aff sample_local(const KeyRecs &r, float al, float w,
   return aff_from_qt(q, tx, ty, tz);
 }
 
-// Pass 1a of the frame with layered blending: every clip of the type is
-// sampled at the character's key fraction (slerp / lerp between keys k0 and
-// k0 + 1); rotations are blended by incremental slerp (q = q_0, W = w_0, then
-// for each further clip W += w_i and q = slerp(q, q_i, w_i / W) while W > 0),
-// translations by their weighted mean (clip 0's when every weight is 0);
-// an additive layer sampled the same way multiplies on the right,
-// q * slerp(1, q_a, a), and adds a t_a.
-__device__ __forceinline__ void sample_layers_pass(const ItemBuf &b, float4 *P, int cs4, int tid) {
-  const int n = b.T.n, nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1, nc = b.T.n_clips;
-  const int CN = b.C * n;
-  const float4 *add = b.T.add_keys;
-  for (int idx = tid; idx < CN; idx += kComputeThreads) {
-    const int j = (int)b.divC.div(idx), c = idx - j * b.C;
-    const float al = b.alpha[c];
-    float4 q = make_float4(0.f, 0.f, 0.f, 1.f);
-    float tx = 0.f, ty = 0.f, tz = 0.f, t0x = 0.f, t0y = 0.f, t0z = 0.f, W = 0.f;
-    for (int i = 0; i < nc; ++i) {
-      const float4 *A0 = b.T.keys + (((size_t)i * nk + k0) * n + j) * 2;
-      const float4 *A1 = b.T.keys + (((size_t)i * nk + k1) * n + j) * 2;
-      const float4 qa0 = __ldg(A0), ta0 = __ldg(A0 + 1), qa1 = __ldg(A1), ta1 = __ldg(A1 + 1);
-      const float4 qi = slerp_pre(qa0, qa1, ta0.w, al);
-      const float ix = fmaf(al, ta1.x - ta0.x, ta0.x), iy = fmaf(al, ta1.y - ta0.y, ta0.y),
-                  iz = fmaf(al, ta1.z - ta0.z, ta0.z);
-      const float w = b.lw[c][i];
-      if (i == 0) {
-        q = qi;
-        t0x = ix;
-        t0y = iy;
-        t0z = iz;
-      } else if (W + w > 0.f) {
-        q = slerp_unit(q, qi, w / (W + w));
-      }
-      W += w;
-      tx = fmaf(w, ix, tx);
-      ty = fmaf(w, iy, ty);
-      tz = fmaf(w, iz, tz);
-    }
-    if (W > 0.f) {
-      const float inv = 1.f / W;
-      tx *= inv;
-      ty *= inv;
-      tz *= inv;
-    } else {
-      tx = t0x;
-      ty = t0y;
-      tz = t0z;
-    }
-    if (add) {
-      const float aw = b.law[c];
-      const float4 *A0 = add + ((size_t)k0 * n + j) * 2, *A1 = add + ((size_t)k1 * n + j) * 2;
-      const float4 qa0 = __ldg(A0), ta0 = __ldg(A0 + 1), qa1 = __ldg(A1), ta1 = __ldg(A1 + 1);
-      const float4 qa = slerp_pre(qa0, qa1, ta0.w, al);
-      q = qmul(q, slerp_unit(make_float4(0.f, 0.f, 0.f, 1.f), qa, aw));
-      tx = fmaf(aw, fmaf(al, ta1.x - ta0.x, ta0.x), tx);
-      ty = fmaf(aw, fmaf(al, ta1.y - ta0.y, ta0.y), ty);
-      tz = fmaf(aw, fmaf(al, ta1.z - ta0.z, ta0.z), tz);
-    }
-    sts_aff(P + c * cs4 + 3 * j, aff_from_qt(q, tx, ty, tz));
-  }
-}
-
 // Linear blend skinning of the item's characters: vertex v of character c
 // goes to sum_k w_k S_{b_k} [p; 1] with normal normalize(sum_k w_k R_{b_k} n)
 // (rigid skin matrices; zero weights skipped), written as 6 floats at the
@@ -134,15 +73,15 @@ __device__ __forceinline__ void skin_mesh(const ItemBuf &b, const float4 *P, int
   }
 }
 
-// Persistent frame kernel on 3x4 matrices for the frames that need the skin
-// matrices in shared memory after the scan (the plain frame and the forward
-// from local poses run on (q, t) items, k_scan_qt.cu).  Work item = C
-// characters of one type sharing the key index k0, so they read the same key
-// records.  Compute warps run passes 1a/1b/2/3 in shared memory and thread 0
-// streams the finished character blocks out with bulk copies; the producer
-// warp stages the next item meanwhile.
-// FEAT 1: with the skinning pass; FEAT 2: with layered blending.
-template <int MINB, int FEAT>
+// Persistent frame kernel on 3x4 matrices for the frame with linear blend
+// skinning, whose last pass reads the skin matrices from shared memory (the
+// other frames and the forward from local poses run on (q, t) items,
+// k_scan_qt.cu).  Work item = C characters of one type sharing the key index
+// k0, so they read the same key records.  Compute warps run passes 1a/1b/2/3
+// and the skinning pass in shared memory and thread 0 streams the finished
+// skin-matrix blocks out with bulk copies (when the caller wants them); the
+// producer warp stages the next item meanwhile.
+template <int MINB>
 __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
@@ -151,8 +90,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
 
   if (tid >= kComputeThreads) {
     producer_loop<0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time, a.blend_w,
-                     a.status, FEAT == 1 ? a.vert_off : nullptr,
-                     FEAT == 2 ? LayerIn{a.layer_w, a.add_w} : LayerIn{nullptr, nullptr});
+                     a.status, a.vert_off);
     return;
   }
 
@@ -175,9 +113,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     // ---- pass 1a: local matrices of every (joint, character); the type's
     // tables are staged into shared memory alongside
     stage_tables(b, Lt, tid);
-    if (FEAT == 2) {
-      sample_layers_pass(b, P, cs4, tid);
-    } else {
+    {
       const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
       const float4 *KA0 = b.T.keys + (size_t)k0 * n * 2;
       const float4 *KA1 = b.T.keys + (size_t)k1 * n * 2;
@@ -238,7 +174,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
     }
     // ---- pass 4 (frame with skinning): linear blend skinning of the
     // characters' meshes from the skin matrices still in shared memory
-    if (FEAT == 1) skin_mesh(b, P, cs4, a.verts, tid);
+    skin_mesh(b, P, cs4, a.verts, tid);
     cur ^= 1;
     handoff_sync();
   }
@@ -246,9 +182,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   if (tid == 0 && a.done) last_cta_reset(a.queue_head, a.done);
 }
 
-template <int MINB, int FEAT>
+template <int MINB>
 static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  auto k = k_scan<MINB, FEAT>;
+  auto k = k_scan<MINB>;
   static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
   if (cfg.smem > set_smem) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
@@ -260,9 +196,8 @@ static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaSt
 }
 
 cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  if (!a.verts && !a.layer_w) return cudaErrorInvalidValue;  // the plain frame runs on k_scan_qt
-  if (cfg.min_blocks >= 3) return a.verts ? launch_scan_t<3, 1>(a, cfg, st) : launch_scan_t<3, 2>(a, cfg, st);
-  return a.verts ? launch_scan_t<2, 1>(a, cfg, st) : launch_scan_t<2, 2>(a, cfg, st);
+  if (!a.verts) return cudaErrorInvalidValue;  // the other frames run on k_scan_qt
+  return cfg.min_blocks >= 3 ? launch_scan_t<3>(a, cfg, st) : launch_scan_t<2>(a, cfg, st);
 }
 
 // ------------------------------------------------------------ work queue

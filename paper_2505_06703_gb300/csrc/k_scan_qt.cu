@@ -4,7 +4,9 @@
 //   MODE 0  the plain fused frame (Simulation -> Hierarchy-Scan -> Bind
 //           MeshPose, Sec. 1 steps 1-3): local poses sampled from the clips;
 //   MODE 1  the forward from given local poses q [total][4] (normalized
-//           here), t [total][3], skin and / or model matrices out.
+//           here), t [total][3], skin and / or model matrices out;
+//   MODE 2  the frame with layered blending (up to 4 clips by per-character
+//           weights and an additive layer, sample_layers_at).
 // The smaller item footprint lets more characters be in flight per SM, which
 // is what bounds the latency-limited scan passes.  The bind pass normalizes
 // the composed quaternion once (removing the norm drift of long products),
@@ -33,8 +35,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
   const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
 
   if (tid >= kComputeThreads) {
-    producer_loop<MODE>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time,
-                        a.blend_w, a.status);
+    producer_loop<MODE == 1 ? 1 : 0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off,
+                                     a.time, a.blend_w, a.status, nullptr,
+                                     MODE == 2 ? LayerIn{a.layer_w, a.add_w} : LayerIn{nullptr, nullptr});
     return;
   }
 
@@ -63,6 +66,13 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
         const float4 q = normalize4(__ldg(q4 + row));
         const float *tp = a.t + 3 * row;
         sts_qt(P + c * cs2, j, n, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
+      }
+    } else if (MODE == 2) {
+      // character-minor: the lanes of one joint share its key records
+      const int CN = C * n;
+      for (int idx = tid; idx < CN; idx += kComputeThreads) {
+        const int j = (int)b.divC.div(idx), c = idx - j * C;
+        sts_qt(P + c * cs2, j, n, sample_layers_at(b, j, c));
       }
     } else {
       const int nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1;
@@ -116,7 +126,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
       const int W = n * b.cgroups, cpt = b.cpt;
       float4 *skin4 = reinterpret_cast<float4 *>(a.skin);
       float4 *model4 = reinterpret_cast<float4 *>(a.model);
-      const bool skin = MODE == 0 || skin4 != nullptr, model = MODE == 1 && model4 != nullptr;
+      const bool skin = MODE != 1 || skin4 != nullptr, model = MODE == 1 && model4 != nullptr;
       for (int idx = tid; idx < W; idx += kComputeThreads) {
         const int grp = (int)b.divN.div(idx), j = idx - grp * n;
         const uint32_t info = Lt.jinfo[j];
@@ -168,8 +178,10 @@ static cudaError_t launch_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream
 size_t scan_qt_smem_bytes(int n, int nseg, int C) { return qt_item_bytes(n, nseg, C); }
 
 cudaError_t launch_scan_qt(int mode, const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  if (mode == 0) return cfg.min_blocks >= 3 ? launch_qt<0, 3>(a, cfg, st) : launch_qt<0, 2>(a, cfg, st);
-  return cfg.min_blocks >= 3 ? launch_qt<1, 3>(a, cfg, st) : launch_qt<1, 2>(a, cfg, st);
+  const bool m3 = cfg.min_blocks >= 3;
+  if (mode == 0) return m3 ? launch_qt<0, 3>(a, cfg, st) : launch_qt<0, 2>(a, cfg, st);
+  if (mode == 1) return m3 ? launch_qt<1, 3>(a, cfg, st) : launch_qt<1, 2>(a, cfg, st);
+  return m3 ? launch_qt<2, 3>(a, cfg, st) : launch_qt<2, 2>(a, cfg, st);
 }
 
 }  // namespace anim

@@ -361,6 +361,63 @@ __device__ __forceinline__ ItemLayout item_layout_qt(float4 *sm, int C, int n, i
   L.end = reinterpret_cast<float4 *>(t + item_table_bytes(n, nseg));
   return L;
 }
+// Local pose of joint j of character c in the frame with layered blending:
+// every clip of the type is sampled at the character's key fraction (slerp /
+// lerp between keys k0 and k0 + 1); rotations are blended by incremental
+// slerp (q = q_0, W = w_0, then for each further clip W += w_i and
+// q = slerp(q, q_i, w_i / W) while W > 0), translations by their weighted
+// mean (clip 0's when every weight is 0); an additive layer sampled the same
+// way multiplies on the right, q * slerp(1, q_a, a), and adds a t_a.
+__device__ __forceinline__ QT sample_layers_at(const ItemBuf &b, int j, int c) {
+  const int n = b.T.n, nk = b.T.n_keys, k0 = b.k0, k1 = (k0 + 1 == nk) ? 0 : k0 + 1, nc = b.T.n_clips;
+  const float4 *add = b.T.add_keys;
+  const float al = b.alpha[c];
+  float4 q = make_float4(0.f, 0.f, 0.f, 1.f);
+  float tx = 0.f, ty = 0.f, tz = 0.f, t0x = 0.f, t0y = 0.f, t0z = 0.f, W = 0.f;
+  for (int i = 0; i < nc; ++i) {
+    const float4 *A0 = b.T.keys + (((size_t)i * nk + k0) * n + j) * 2;
+    const float4 *A1 = b.T.keys + (((size_t)i * nk + k1) * n + j) * 2;
+    const float4 qa0 = __ldg(A0), ta0 = __ldg(A0 + 1), qa1 = __ldg(A1), ta1 = __ldg(A1 + 1);
+    const float4 qi = slerp_pre(qa0, qa1, ta0.w, al);
+    const float ix = fmaf(al, ta1.x - ta0.x, ta0.x), iy = fmaf(al, ta1.y - ta0.y, ta0.y),
+                iz = fmaf(al, ta1.z - ta0.z, ta0.z);
+    const float w = b.lw[c][i];
+    if (i == 0) {
+      q = qi;
+      t0x = ix;
+      t0y = iy;
+      t0z = iz;
+    } else if (W + w > 0.f) {
+      q = slerp_unit(q, qi, w / (W + w));
+    }
+    W += w;
+    tx = fmaf(w, ix, tx);
+    ty = fmaf(w, iy, ty);
+    tz = fmaf(w, iz, tz);
+  }
+  if (W > 0.f) {
+    const float inv = 1.f / W;
+    tx *= inv;
+    ty *= inv;
+    tz *= inv;
+  } else {
+    tx = t0x;
+    ty = t0y;
+    tz = t0z;
+  }
+  if (add) {
+    const float aw = b.law[c];
+    const float4 *A0 = add + ((size_t)k0 * n + j) * 2, *A1 = add + ((size_t)k1 * n + j) * 2;
+    const float4 qa0 = __ldg(A0), ta0 = __ldg(A0 + 1), qa1 = __ldg(A1), ta1 = __ldg(A1 + 1);
+    const float4 qa = slerp_pre(qa0, qa1, ta0.w, al);
+    q = qmul(q, slerp_unit(make_float4(0.f, 0.f, 0.f, 1.f), qa, aw));
+    tx = fmaf(aw, fmaf(al, ta1.x - ta0.x, ta0.x), tx);
+    ty = fmaf(aw, fmaf(al, ta1.y - ta0.y, ta0.y), ty);
+    tz = fmaf(aw, fmaf(al, ta1.z - ta0.z, ta0.z), tz);
+  }
+  return QT{q, make_float4(tx, ty, tz, 0.f)};
+}
+
 __host__ __device__ inline size_t qt_item_bytes(int n, int nseg, int C) {
   return 16ull * ((size_t)C * (2 * (size_t)n + 1) + 4ull * C * nseg) + item_table_bytes(n, nseg);
 }
