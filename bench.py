@@ -87,6 +87,29 @@ def frame_algorithmic_bytes(w: dict) -> int:
     return joints * 48 + tables + len(ct) * 12
 
 
+def frame_touched_bytes(w: dict) -> int:
+    """Bytes one frame would move if nothing were cached or shared, as
+    context for the algorithmic bytes: per joint four 32-byte key records,
+    the 48-byte inverse bind, a 4-byte table entry and the 48-byte output."""
+    types = w["types"]
+    return sum(len(types[t]["parents"]) for t in w["char_type"]) * (4 * 32 + 48 + 4 + 48)
+
+
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
+def add_nominal_fractions(obj) -> None:
+    """Beside each HBM roofline's fraction of the measured peak, its fraction
+    of the nominal 7.9 TB/s."""
+    if isinstance(obj, dict):
+        rf = obj.get("roofline")
+        if isinstance(rf, dict) and rf.get("unit") == "GB/s" and "achieved" in rf:
+            rf.setdefault("nominal_peak", NOMINAL_HBM_GBS)
+            rf.setdefault("frac_of_nominal", round(rf["achieved"] / NOMINAL_HBM_GBS, 4))
+        for v in obj.values():
+            add_nominal_fractions(v)
+
+
 def fwd_bwd_algorithmic_bytes(w: dict) -> int:
     """loss_backward: read q (16 B), t (12 B), target (12 B) and write dq
     (16 B), dt (12 B) per joint, plus the type's parent table."""
@@ -315,7 +338,9 @@ def run_ours(args) -> dict:
     tr = NCU_TRAFFIC.get(kernel_source_hash())
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr, "kernel": "k_scan_qt<0> (persistent frame)",
-                "kernel_ms": round(k_ms, 5), "algorithmic_bytes": alg, "peak_source": peak_src}
+                "kernel_ms": round(k_ms, 5), "algorithmic_bytes": alg, "peak_source": peak_src,
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
+                "touched_bytes": frame_touched_bytes(w)}
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
               "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -809,6 +834,7 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu:
             r["cpu_baseline"] = cpu_baseline()
+        add_nominal_fractions(r)
         print(json.dumps(r))
 
 
