@@ -256,18 +256,22 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
   // serialization may start now; it waits for this grid's completion (and
   // its memory) in griddepcontrol.wait before reading the queue
   asm volatile("griddepcontrol.launch_dependents;");
-  if (blockIdx.x == 0 && tid == 0) *a.queue_head = 0;  // consumed by the next launch in stream order
+  // launched the same way after the previous frame's kernel: the plan's
+  // tables are read before waiting for it, the times (which the preceding
+  // kernel may have written) and every write of this grid after
   const RangeDev R = a.ranges[blockIdx.x];
   const int nk = a.types[R.type].n_keys;
   const float rate = a.types[R.type].rate;
   const int cap = a.cap[R.type];
   const int region_end = (blockIdx.x + 1 < a.n_ranges) ? a.ranges[blockIdx.x + 1].region : a.n_slots;
   for (int b = tid; b < nk; b += nth) s_hist[b] = 0;
-  __syncthreads();
   int cid = -1, k = 0, pos = 0;
+  if (tid < R.count) cid = __ldg(a.type_chars + R.start + tid);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (blockIdx.x == 0 && tid == 0) *a.queue_head = 0;  // consumed by the next launch in stream order
+  __syncthreads();
   if (tid < R.count) {
-    cid = __ldg(a.type_chars + R.start + tid);
-    k = key_index(__ldg(a.time + cid), rate, nk, a.status);
+    k = key_index(a.time[cid], rate, nk, a.status);
     pos = atomicAdd(&s_hist[k], 1);  // rank inside the bin
   }
   __syncthreads();
@@ -306,8 +310,16 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st) {
   if (a.n_ranges == 0) return cudaSuccess;
-  k_bucket<<<a.n_ranges, kBucketThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)a.n_ranges);
+  lc.blockDim = dim3((unsigned)kBucketThreads);
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, k_bucket, a);
 }
 
 // ------------------------------------------------------------ setup kernels

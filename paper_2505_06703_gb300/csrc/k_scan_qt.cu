@@ -30,7 +30,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
   const int tid = threadIdx.x;
   // launched with programmatic stream serialization (after the work-queue
   // kernel, for the frame): wait for the preceding grid to complete before
-  // reading anything it may have written
+  // reading anything it may have written.  The next frame's work-queue
+  // kernel may start now (it reads only plan tables before its own wait).
+  asm volatile("griddepcontrol.launch_dependents;");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
 
