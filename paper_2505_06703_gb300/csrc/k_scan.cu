@@ -325,7 +325,8 @@ cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st) {
 // ------------------------------------------------------------ setup kernels
 // Arc angle between consecutive keys (shorter arc), stored in the pad slot
 // of the first key of each pair: theta = 2 atan2(|a - b'|, |a + b'|) with
-// b' = +-b on a's hemisphere.  Keys loop, so key n_keys-1 pairs with key 0.
+// b' = +-b on a's hemisphere, carrying the sign of that choice (slerp_pre).
+// Keys loop, so key n_keys-1 pairs with key 0.
 __global__ void k_prepare_keys(float4 *keys, int n_clips, int n_keys, int n) {
   const long long total = (long long)n_clips * n_keys * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -342,7 +343,7 @@ __global__ void k_prepare_keys(float4 *keys, int n_clips, int n_keys, int n) {
     d = a.y - sg * b.y; dm += d * d; d = a.y + sg * b.y; dp += d * d;
     d = a.z - sg * b.z; dm += d * d; d = a.z + sg * b.z; dp += d * d;
     d = a.w - sg * b.w; dm += d * d; d = a.w + sg * b.w; dp += d * d;
-    keys[2 * i + 1].w = 2.f * atan2f(sqrtf(dm), sqrtf(dp));
+    keys[2 * i + 1].w = copysignf(2.f * atan2f(sqrtf(dm), sqrtf(dp)), sg);  // the sign: b's hemisphere
   }
 }
 

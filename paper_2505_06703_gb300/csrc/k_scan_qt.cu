@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
         for (int c = grp * cpt; c < c1; ++c) {
           QT m = lds_qt(P + c * cs2, j, n);
           if (info & kJ16Link) m = qt_mul(lds_qt(Y, c * nseg + g, C * nseg), m);
-          const Aff M = aff_from_qt(normalize4(m.q), m.t.x, m.t.y, m.t.z);
+          const Aff M = aff_from_qt_any(m.q, m.t.x, m.t.y, m.t.z);
           if (model) stg_aff(model4 + (b.off[c] + j) * 3, M);
           if (skin) stg_aff(skin4 + (b.off[c] + j) * 3, aff_mul(M, B));
         }
