@@ -12,7 +12,8 @@
 // the composed quaternion once (removing the norm drift of long products),
 // forms M = [R(q) | t] and writes M and / or S = M B straight to global
 // memory.  Same item pipeline as k_scan (producer warp, 8 compute warps,
-// work queue); the skinning and layered-blend frames keep the matrix form.
+// work queue); the frame with skinning keeps the matrix form there, as its
+// skinning pass reads the skin matrices from shared memory.
 #include <cuda_runtime.h>
 
 #include "anim_internal.h"
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
     // ---- pass 2: pointer jumping over segments
     const float4 *Y = pass2_qt(b, Lt, P, cs2, tid);
 
-    // ---- pass 3: model pose, normalize, matrix, (bind,) store
+    // ---- pass 3: model pose, matrix of its normalized rotation, (bind,) store
     {
       const int W = n * b.cgroups, cpt = b.cpt;
       float4 *skin4 = reinterpret_cast<float4 *>(a.skin);
