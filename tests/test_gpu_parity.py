@@ -113,6 +113,97 @@ def test_frame_from_host_buffers(torch):
     _gpu.assert_skin_close(out.numpy(), oracle.frame(w), w)
 
 
+@pytest.mark.parametrize("walk", [0, 1])
+def test_back_to_back_frames(torch, walk):
+    """Frames enqueued back to back (each work-queue kernel and frame kernel
+    launched with programmatic stream serialization after the previous one),
+    with the times of each frame written by a torch kernel just before it,
+    equal the same frames run one at a time -- on a stream and in a CUDA
+    graph."""
+    w = synth.subset(synth.config3(), list(range(0, 10000, 9)))
+    ctx, plan = _gpu.setup(w)
+    ctx.set_schedule(plan, [16, 3, 2048, walk])
+    base, wt = _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])
+    shifts = [0.0, 0.37, 0.71]
+    refs = []
+    for sh in shifts:
+        tm = torch.remainder(base + sh, 1.0)
+        refs.append(ctx.evaluate_frame(plan, tm, wt).clone())
+        torch.cuda.synchronize()
+    tms = [torch.empty_like(base) for _ in shifts]
+    outs = [torch.zeros((plan.total, 12), device="cuda") for _ in shifts]
+
+    def enqueue():
+        for tm, sh, o in zip(tms, shifts, outs):
+            torch.remainder(base + sh, 1.0, out=tm)  # the frame's input, written by the preceding kernel
+            ctx.evaluate_frame(plan, tm, wt, out=o)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        enqueue()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        enqueue()
+    for o in outs:
+        o.zero_()
+    torch.cuda.synchronize()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
+
+
+@pytest.mark.parametrize("sched", [[16, 3, 2048, 0, 7], [16, 2, 2048, 0, 0]])
+def test_back_to_back_adjoint(torch, sched):
+    """Forward + adjoint launches enqueued back to back (the one-item kernel
+    stages its items before waiting on the preceding grid), each on poses a
+    torch kernel rescales just before it, equal the launches run one at a
+    time -- on a stream and in a CUDA graph."""
+    w = synth.subset(synth.config4(), list(range(0, 1024, 3)))
+    ctx, plan = _gpu.setup(w, with_clips=False)
+    ctx.set_schedule(plan, sched)
+    q0, t, tg = _gpu.cuda(w["q"]), _gpu.cuda(w["t"]), _gpu.cuda(w["target"])
+    scales = [1.0, 1.1, 0.9]
+    refs = []
+    for sc in scales:
+        gq, gt, loss = ctx.loss_backward(plan, q0 * sc, t, tg)
+        torch.cuda.synchronize()
+        refs.append((gq.clone(), gt.clone(), loss.clone()))
+    qs = [torch.empty_like(q0) for _ in scales]
+    outs = [(torch.zeros_like(r[0]), torch.zeros_like(r[1]), torch.zeros_like(r[2])) for r in refs]
+
+    def enqueue():
+        for q, sc, (gq, gt, loss) in zip(qs, scales, outs):
+            torch.mul(q0, sc, out=q)  # the launch's input, written by the preceding kernel
+            ctx.loss_backward(plan, q, t, tg, grad_q=gq, grad_t=gt, loss=loss)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        enqueue()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        for a, b in zip(o, r):
+            assert torch.equal(a, b)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        enqueue()
+    for o in outs:
+        for a in o:
+            a.zero_()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        for a, b in zip(o, r):
+            assert torch.equal(a, b)
+
+
 def test_autotuned_frame_parity(torch):
     """anim_tune picks a schedule by timing candidates; the tuned frame still
     matches the oracle and a second tune of the same mix hits the cache."""
