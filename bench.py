@@ -608,7 +608,7 @@ def run_ik(device, dev, world, peak) -> dict:
     q0 = torch.as_tensor(w["q0"], device=dev)
     q, m, v = q0.clone(), torch.zeros_like(q0), torch.zeros_like(q0)
     loss = torch.zeros(plan.n_chars, device=dev)
-    ctx.tune(plan, 2)  # the adjoint's schedule; the IK object keeps it
+    ctx.tune_ik(plan, eff)  # the IK step's schedule; the IK object keeps it
     ik = ctx.ik(plan, eff)
     n_steps = int(w["n_steps"])
     stream = torch.cuda.Stream()

@@ -324,6 +324,15 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
  * which = 0 needs clips for every type of the plan. */
 ANIM_API int anim_tune(anim_ctx *ctx, anim_plan *plan, int which);
 
+/* The same search for the fused IK step (anim_ik_step): each candidate
+ * schedule gets a temporary IK object for `effectors` (as in anim_ik_create)
+ * and is timed on scratch state it allocates; the fastest is applied and
+ * cached per (type mix, effectors).  An IK object created afterwards keeps
+ * that schedule.  The IK step runs on the effectors' ancestors only, much
+ * smaller than the whole skeletons anim_tune(which = 2) times, so its best
+ * schedule differs.  Synchronous; not capturable. */
+ANIM_API int anim_tune_ik(anim_ctx *ctx, anim_plan *plan, int n_eff, const int32_t *effectors);
+
 /* The schedule the autotuner picked, as 5 integers: segment length, resident
  * CTAs per SM, work-item size in joints, chain-walk kernel for the frame
  * (0/1), adjoint kernel (0: persistent, k = 1..8: one work item per CTA,

@@ -53,6 +53,7 @@ SIGNATURES = {
     "anim_ik_reset": (c_int, [_P, _P, _P]),
     "anim_ik_step": (c_int, [_P, _P, _P, _P, _P, _P, _P, c_float, c_float, c_float, c_float, _P, _P]),
     "anim_tune": (c_int, [_P, _P, c_int]),
+    "anim_tune_ik": (c_int, [_P, _P, c_int, _P]),
     "anim_get_status": (c_int, [_P, _P, POINTER(c_int)]),
     "anim_analyze_skeleton": (c_int, [c_int, _P, c_int, POINTER(c_int32), _P, POINTER(c_int32), POINTER(c_int32)]),
     "anim_forward_local_noalloc": (c_int, [c_int, _P, c_int64, _P, _P, _P, _P, _P]),
@@ -322,6 +323,11 @@ class Context:
 
     def tune(self, plan, which: int = 0):
         self._ck(self.lib.anim_tune(self.h, plan.h, int(which)))
+
+    def tune_ik(self, plan, effectors):
+        """Autotune the schedule for the IK step (effectors: [n_types][n_eff])."""
+        e = np.ascontiguousarray(effectors, dtype=np.int32)
+        self._ck(self.lib.anim_tune_ik(self.h, plan.h, int(e.shape[1]), _np_ptr(e)))
 
     def get_schedule(self, plan):
         """[seg_len, ctas_per_sm, joints_per_item, walk, adj_ctas]"""

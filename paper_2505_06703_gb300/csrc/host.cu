@@ -1772,6 +1772,33 @@ static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps,
 // SM, work-item size) on scratch inputs with CUDA events and keep the best;
 // the result is cached by a hash of (which, type ids, joint counts, depths,
 // character counts) and re-applied by anim_plan_create for the same mix.
+// The autotuner's candidate schedules for a search (which: 0 frame, 1
+// forward_local, 2 loss_backward and the IK step).  The chain-walk kernel
+// serves the frame only, the adjoint kernel choice the adjoint only: the
+// other searches keep the context's settings.
+extern "C++" {  // a template inside the ABI's extern "C" block
+template <class F>
+static void for_each_candidate(const anim_ctx *ctx, int which, F &&f) {
+  const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {256, 512, 1024, 2048, 4096};
+  const int adjs[] = {0, 4, 6, 7, 8};
+  const int walk_lo = which == 0 ? 0 : ctx->use_walk, walk_hi = which == 0 ? 1 : ctx->use_walk;
+  const int adj_keep = ctx->adj_ctas;
+  for (int walk = walk_lo; walk <= walk_hi; ++walk)
+    for (int adj : adjs)
+      for (int seg : segs)
+        for (int cps : cpss)
+          for (int jpi : jpis) {
+            if (which != 2 && adj != adjs[0]) continue;
+            const int adj_c = which == 2 ? adj : adj_keep;
+            if (which != 2 && jpi < 1024) continue;  // small items only pay off in the one-item adjoint
+            if (which == 2 && adj_c == 0 && jpi < 1024) continue;
+            if (which == 2 && adj_c > 0 && cps != 2) continue;  // CTAs per SM of the persistent kernels: unused
+            if (cps == 3 && which == 2) continue;  // the persistent adjoint kernel is built for up to 2 CTAs/SM
+            f(seg, cps, jpi, walk, adj_c);
+          }
+}
+}  // extern "C++"
+
 int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
@@ -1833,35 +1860,93 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
     return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, nullptr);
   };
   anim_ctx::TuneChoice best{0, 0, 0, 0, 0, 1e30f};
-  const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {256, 512, 1024, 2048, 4096};
-  const int adjs[] = {0, 4, 6, 7, 8};
-  // the chain-walk kernel serves the frame only, the adjoint kernel choice
-  // the adjoint only: other searches keep the context's settings
-  const int walk_lo = which == 0 ? 0 : ctx->use_walk, walk_hi = which == 0 ? 1 : ctx->use_walk;
-  const int adj_keep = ctx->adj_ctas;
-  for (int walk = walk_lo; walk <= walk_hi; ++walk)
-    for (int adj : adjs)
-      for (int seg : segs)
-        for (int cps : cpss)
-          for (int jpi : jpis) {
-          if (which != 2 && adj != adjs[0]) continue;
-          const int adj_c = which == 2 ? adj : adj_keep;
-          if (which != 2 && jpi < 1024) continue;        // small items only pay off in the one-item adjoint
-          if (which == 2 && adj_c == 0 && jpi < 1024) continue;
-          if (which == 2 && adj_c > 0 && cps != 2) continue;  // CTAs per SM of the persistent kernels: unused
-          if (cps == 3 && which == 2) continue;  // the persistent adjoint kernel is built for up to 2 CTAs/SM
-          if (apply_choice(ctx, plan, seg, cps, jpi, walk, adj_c) != ANIM_OK) continue;  // e.g. does not fit
-          bool ok = true;
-          for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
-          cudaEventRecord(e0, nullptr);
-          for (int r = 0; r < 5 && ok; ++r) ok = run_once() == ANIM_OK;
-          cudaEventRecord(e1, nullptr);
-          if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          ms /= 5.f;
-          if (ms < best.ms) best = {seg, cps, jpi, walk, adj_c, ms};
-        }
+  for_each_candidate(ctx, which, [&](int seg, int cps, int jpi, int walk, int adj_c) {
+    if (apply_choice(ctx, plan, seg, cps, jpi, walk, adj_c) != ANIM_OK) return;  // e.g. does not fit
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
+    cudaEventRecord(e0, nullptr);
+    for (int r = 0; r < 5 && ok; ++r) ok = run_once() == ANIM_OK;
+    cudaEventRecord(e1, nullptr);
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) return;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 5.f;
+    if (ms < best.ms) best = {seg, cps, jpi, walk, adj_c, ms};
+  });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release();
+  if (best.seg_len == 0) return fail(ctx, ANIM_ECUDA, "no candidate schedule ran");
+  ctx->tune_cache[key] = best;
+  ctx->err.clear();
+  return apply_choice(ctx, plan, best.seg_len, best.ctas_per_sm, best.joints_per_item, best.walk,
+                      best.adj_ctas);
+}
+
+int anim_tune_ik(anim_ctx *ctx, anim_plan *plan, int n_eff, const int32_t *effectors) {
+  int rc = check_plan(ctx, plan);
+  if (rc) return rc;
+  if (n_eff < 1 || !effectors) return fail(ctx, ANIM_EINVAL, "need n_eff >= 1 effectors per type");
+  if (plan->n_chars == 0) return ANIM_OK;
+  CK(cudaSetDevice(ctx->device));
+  uint64_t key = mix_hash(ctx, plan, 3);  // and the used types' effectors
+  for (int t : plan->used)
+    for (int e = 0; e < n_eff; ++e)
+      key = (key ^ (uint64_t)(uint32_t)effectors[(size_t)t * n_eff + e]) * 1099511628211ull;
+  auto hit = ctx->tune_cache.find(key);
+  if (hit != ctx->tune_cache.end())
+    return apply_choice(ctx, plan, hit->second.seg_len, hit->second.ctas_per_sm, hit->second.joints_per_item,
+                        hit->second.walk, hit->second.adj_ctas);
+  // scratch state (tuning may allocate; steps never do): identity poses,
+  // zero moments, targets near the origin
+  const int64_t N = plan->n_chars, J = plan->total;
+  float *d_q = nullptr, *d_m = nullptr, *d_v = nullptr, *d_t = nullptr, *d_tg = nullptr;
+  auto release = [&]() {
+    for (float *p : {d_q, d_m, d_v, d_t, d_tg})
+      if (p) cudaFree(p);
+  };
+  bool ok = cudaMalloc(&d_q, J * 16) == cudaSuccess && cudaMalloc(&d_m, J * 16) == cudaSuccess &&
+            cudaMalloc(&d_v, J * 16) == cudaSuccess && cudaMalloc(&d_t, J * 12) == cudaSuccess &&
+            cudaMalloc(&d_tg, std::max<int64_t>(N * n_eff * 12, 16)) == cudaSuccess;
+  if (!ok) {
+    release();
+    return fail(ctx, ANIM_ENOMEM, "IK tuning buffers");
+  }
+  {
+    std::vector<float> q(J * 4, 0.f), t(J * 3, 0.05f), tg(N * n_eff * 3, 0.1f);
+    for (int64_t j = 0; j < J; ++j) q[4 * j + 3] = 1.f;
+    cudaError_t e = cudaMemcpy(d_q, q.data(), J * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_m, 0, J * 16);
+    if (e == cudaSuccess) e = cudaMemset(d_v, 0, J * 16);
+    if (e == cudaSuccess) e = cudaMemcpy(d_t, t.data(), J * 12, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && N > 0) e = cudaMemcpy(d_tg, tg.data(), N * n_eff * 12, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      release();
+      return fail(ctx, ANIM_ECUDA, "IK tuning inputs: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  anim_ctx::TuneChoice best{0, 0, 0, 0, 0, 1e30f};
+  for_each_candidate(ctx, 2, [&](int seg, int cps, int jpi, int walk, int adj_c) {
+    if (apply_choice(ctx, plan, seg, cps, jpi, walk, adj_c) != ANIM_OK) return;  // e.g. does not fit
+    anim_ik *ik = nullptr;
+    if (anim_ik_create(ctx, plan, n_eff, effectors, &ik) != ANIM_OK) return;  // a view does not fit
+    auto step = [&]() {
+      return anim_ik_step(ctx, ik, d_q, d_m, d_v, d_t, d_tg, 1e-2f, 0.9f, 0.999f, 1e-8f, nullptr, nullptr);
+    };
+    bool good = anim_ik_reset(ctx, ik, nullptr) == ANIM_OK;
+    for (int w = 0; w < 2 && good; ++w) good = step() == ANIM_OK;
+    cudaEventRecord(e0, nullptr);
+    for (int r = 0; r < 5 && good; ++r) good = step() == ANIM_OK;
+    cudaEventRecord(e1, nullptr);
+    good = good && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.f;
+    if (good) cudaEventElapsedTime(&ms, e0, e1);
+    anim_ik_destroy(ctx, ik);
+    if (good && ms / 5.f < best.ms) best = {seg, cps, jpi, walk, adj_c, ms / 5.f};
+  });
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   release();

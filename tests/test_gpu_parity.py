@@ -331,15 +331,22 @@ def _ik_setup(torch, w):
     return ctx, plan, t, targets
 
 
-def test_config5_ik_first_step(torch):
+@pytest.mark.parametrize("tuned", [False, True])
+def test_config5_ik_first_step(torch, tuned):
     """The first fused IK step (forward, effector loss, adjoint, Adam) equals
     the oracle's first step wherever the gradient is above FP32 noise (Adam's
-    first update is lr * g / (|g| + eps), a sign-like step)."""
+    first update is lr * g / (|g| + eps), a sign-like step) -- under the
+    default schedule and under the one anim_tune_ik picks."""
     w = synth.subset(synth.config5(), list(range(32)))
     types, ct, eff = w["types"], w["char_type"], w["effectors"]
     targets_ref = oracle.ik_targets(w)
     q1_ref, hist = oracle.ik(types, ct, w["t"], w["q0"], eff, targets_ref, 1)
     ctx, plan, t, targets = _ik_setup(torch, w)
+    if tuned:
+        ctx.tune_ik(plan, eff)
+        sched = ctx.get_schedule(plan)
+        ctx.tune_ik(plan, eff)  # cached: applies the same schedule without timing
+        assert ctx.get_schedule(plan) == sched
     assert np.abs(targets.cpu().numpy() - targets_ref).max() < 1e-5
     q = _gpu.cuda(w["q0"])
     m, v = torch.zeros_like(q), torch.zeros_like(q)
