@@ -462,7 +462,7 @@ def run_skinned_frame(device, dev, world, peak) -> dict:
     ctx, plan = setup_ctx(w, device)
     for i, t in enumerate(w["types"]):
         ctx.upload_mesh(i, t["mesh"])
-    ctx.tune(plan, 0)
+    ctx.tune(plan, 3)  # the skinned frame's own schedule
     nv = int(ctx.vertex_offsets(plan)[-1])
     n_out = max(2, math.ceil(2.5 * L2_BYTES / (nv * 24)))
     outs = [torch.empty((nv, 6), dtype=torch.float32, device=dev) for _ in range(n_out)]
@@ -504,7 +504,7 @@ def run_layered_frame(device, dev, world, peak) -> dict:
     ctx, plan = setup_ctx(w, device)
     for i, t in enumerate(w["types"]):
         ctx.upload_additive(i, t["add_keys"], t["rate_hz"])
-    ctx.tune(plan, 0)
+    ctx.tune(plan, 4)  # the layered frame's own schedule
     joints = plan.total
     n_out = max(2, math.ceil(2.5 * L2_BYTES / (joints * 48)))
     outs = [torch.empty((joints, 12), dtype=torch.float32, device=dev) for _ in range(n_out)]
@@ -547,7 +547,7 @@ def run_crowd(device, dev, world) -> dict:
     for i, t in enumerate(w["types"]):
         ctx.upload_mesh(i, t["mesh"])
         ctx.upload_faces(i, t["mesh"]["faces"])
-    ctx.tune(plan, 0)
+    ctx.tune(plan, 3)  # the skinned frame's schedule
     nv = int(ctx.vertex_offsets(plan)[-1])
     tris = sum(len(w["types"][int(t)]["mesh"]["faces"]) for t in w["char_type"])
     verts = torch.empty((nv, 6), dtype=torch.float32, device=dev)

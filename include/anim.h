@@ -314,14 +314,16 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
  * frame whether walkable types (chain schedules of at most 160 steps with
  * most lanes busy, and pure chains) run on the one-warp chain-walk kernel
  * beside the segmented kernel -- of
- * `which` (0 = fused frame, 1 = forward_local, 2 = loss_backward) with CUDA
- * events on scratch inputs it allocates, and keeps the fastest.  The result
+ * `which` (0 = fused frame, 1 = forward_local, 2 = loss_backward, 3 = frame
+ * with skinning, 4 = frame with layered blending) with CUDA events on scratch
+ * inputs it allocates, and keeps the fastest.  The result
  * is cached in the context per hash of (which, type ids, joint counts,
  * depths, character counts); calling anim_tune again for the same mix
  * applies the cached schedule without timing.  The schedule is per context
  * (segment lengths of the plan's types, CTAs per SM, item size), so it also
  * applies to other plans of the context.  Synchronous; not capturable;
- * which = 0 needs clips for every type of the plan. */
+ * which = 0, 3 and 4 need clips for every type of the plan (3 skins the
+ * meshes uploaded, 4 blends the clips and additive layers uploaded). */
 ANIM_API int anim_tune(anim_ctx *ctx, anim_plan *plan, int which);
 
 /* The same search for the fused IK step (anim_ik_step): each candidate

@@ -1773,9 +1773,10 @@ static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps,
 // the result is cached by a hash of (which, type ids, joint counts, depths,
 // character counts) and re-applied by anim_plan_create for the same mix.
 // The autotuner's candidate schedules for a search (which: 0 frame, 1
-// forward_local, 2 loss_backward and the IK step).  The chain-walk kernel
-// serves the frame only, the adjoint kernel choice the adjoint only: the
-// other searches keep the context's settings.
+// forward_local, 2 loss_backward and the IK step, 3 the skinned frame, 4 the
+// layered frame).  The chain-walk kernel serves the plain frame only, the
+// adjoint kernel choice the adjoint only: the other searches keep the
+// context's settings.
 extern "C++" {  // a template inside the ABI's extern "C" block
 template <class F>
 static void for_each_candidate(const anim_ctx *ctx, int which, F &&f) {
@@ -1802,9 +1803,9 @@ static void for_each_candidate(const anim_ctx *ctx, int which, F &&f) {
 int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
-  if (which < 0 || which > 2) return fail(ctx, ANIM_EINVAL, "which must be 0, 1 or 2");
+  if (which < 0 || which > 4) return fail(ctx, ANIM_EINVAL, "which must be 0 to 4");
   if (plan->n_chars == 0) return ANIM_OK;
-  if (which == 0)
+  if (which == 0 || which >= 3)
     for (int t : plan->used)
       if (ctx->types[t]->n_clips == 0) return fail(ctx, ANIM_ESTATE, "type %d has no clips uploaded", t);
   CK(cudaSetDevice(ctx->device));
@@ -1826,23 +1827,23 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   auto release = [&]() {
     for (void *p : bufs) cudaFree(p);
   };
-  float *d_time = (float *)dalloc(N * 4), *d_w = (float *)dalloc(N * 4);
+  const int64_t V = plan->vert_off.empty() ? 0 : plan->vert_off.back();
+  float *d_time = (float *)dalloc(N * 4), *d_w = (float *)dalloc(N * 16);  // [N] blend or [N][4] layer weights
   float *d_q = (float *)dalloc(J * 16), *d_t = (float *)dalloc(J * 12), *d_tg = (float *)dalloc(J * 12);
   float *d_out = (float *)dalloc(J * 48), *d_gq = (float *)dalloc(J * 16), *d_gt = (float *)dalloc(J * 12);
-  if (bufs.size() != 8 || std::count(bufs.begin(), bufs.end(), nullptr)) {
+  float *d_verts = which == 3 ? (float *)dalloc(V * 24) : nullptr;
+  if (bufs.size() != (which == 3 ? 9u : 8u) || std::count(bufs.begin(), bufs.end(), nullptr)) {
     release();
     return fail(ctx, ANIM_ENOMEM, "tuning buffers");
   }
   {
-    std::vector<float> h(std::max<int64_t>(N, 1)), hw(std::max<int64_t>(N, 1));
-    for (int64_t c = 0; c < N; ++c) {
-      h[c] = (float)std::fmod(0.6180339887 * (double)c, 1.0);
-      hw[c] = (float)std::fmod(0.4142135623 * (double)c, 1.0);
-    }
+    std::vector<float> h(std::max<int64_t>(N, 1)), hw(std::max<int64_t>(4 * N, 1));
+    for (int64_t c = 0; c < N; ++c) h[c] = (float)std::fmod(0.6180339887 * (double)c, 1.0);
+    for (int64_t c = 0; c < 4 * N; ++c) hw[c] = (float)std::fmod(0.4142135623 * (double)c, 1.0);
     std::vector<float> q(J * 4, 0.f), t(J * 3, 0.05f);
     for (int64_t j = 0; j < J; ++j) q[4 * j + 3] = 1.f;
     cudaError_t e = cudaMemcpy(d_time, h.data(), N * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_w, hw.data(), N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_w, hw.data(), N * 16, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_q, q.data(), J * 16, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_t, t.data(), J * 12, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_tg, t.data(), J * 12, cudaMemcpyHostToDevice);
@@ -1857,6 +1858,8 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   auto run_once = [&]() -> int {
     if (which == 0) return anim_evaluate_frame(ctx, plan, d_time, d_w, d_out, nullptr);
     if (which == 1) return anim_forward_local(ctx, plan, d_q, d_t, d_out, nullptr, nullptr);
+    if (which == 3) return anim_evaluate_frame_skinned(ctx, plan, d_time, d_w, nullptr, d_verts, nullptr);
+    if (which == 4) return anim_evaluate_frame_layers(ctx, plan, d_time, d_w, d_w, d_out, nullptr);
     return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, nullptr);
   };
   anim_ctx::TuneChoice best{0, 0, 0, 0, 0, 1e30f};

@@ -509,6 +509,27 @@ def test_skinned_frame(torch, walk):
         _gpu.assert_skin_close(run_frame_on(ctx, plan, w), S_ref, w)
 
 
+def test_tuned_skinned_and_layered_frames(torch):
+    """anim_tune's searches for the frame with skinning (which = 3) and the
+    frame with layered blending (which = 4) time those frames themselves;
+    under the schedules they pick, both still match the oracle."""
+    w = synth.with_meshes(synth.subset(synth.config2(), list(range(0, 4096, 64)) + [4096]), n_verts=600, seed=23)
+    S_ref = oracle.frame(w)
+    V_ref = oracle.skin_vertices(w, S_ref)
+    ctx, plan = _gpu.setup(w)
+    ctx.tune(plan, 3)
+    voff = ctx.vertex_offsets(plan)
+    v = ctx.evaluate_frame_skinned(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])).cpu().numpy()
+    for c, ty in enumerate(w["char_type"]):
+        sl = slice(voff[c], voff[c + 1])
+        assert np.abs(v[sl] - V_ref[sl]).max(initial=0.0) <= 2 * _gpu.tol_for_depth(w["types"][ty]["depth"])
+    w = synth.with_layers(synth.subset(synth.config3(), list(range(0, 10000, 50))), n_clips=4, seed=43)
+    ctx, plan = _gpu.setup(w)
+    ctx.tune(plan, 4)
+    got = ctx.evaluate_frame_layers(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weights"]), _gpu.cuda(w["add_w"]))
+    _gpu.assert_skin_close(got.cpu().numpy(), oracle.frame_layers(w), w)
+
+
 def run_frame_on(ctx, plan, w):
     return ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])).cpu().numpy()
 
