@@ -52,7 +52,7 @@ L2_BYTES = 129 * 1024 * 1024
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources it was taken on (comments and whitespace aside); reported
 # as null once the code changes.
-NCU_TRAFFIC = {"547a9e6143bd28a7": 1355008 + 40273920}
+NCU_TRAFFIC = {"d3d8f4820574178a": 1357568 + 39923968}
 
 
 # ------------------------------------------------------------------ helpers
