@@ -277,6 +277,11 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
   __shared__ ItemBuf bufs[2];
   __shared__ float4 wsF[32], wsT[32];
   const int tid = threadIdx.x;
+  // launched with programmatic stream serialization: the CTAs become
+  // resident while the preceding kernel finishes; the queue, the IK step
+  // counter and the inputs are touched only after it has completed
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (tid >= kComputeThreads) {
     producer_loop<1>(bufs, a.queue_head, a.n_items, a.items, a.types, a.item_chars, a.row_off, nullptr, nullptr,
@@ -370,8 +375,17 @@ static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cuda
     if (e != cudaSuccess) return e;
     set_smem = cfg.smem;
   }
-  k_adjoint<MODE><<<cfg.ctas, cfg.threads, cfg.smem, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)cfg.ctas);
+  lc.blockDim = dim3((unsigned)cfg.threads);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, k_adjoint<MODE>, a);
 }
 
 cudaError_t launch_adjoint(int mode, const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
