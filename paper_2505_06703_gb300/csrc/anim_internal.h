@@ -23,20 +23,15 @@ struct TypeDev {
   const int32_t *parent;     // [n]
   const int32_t *depth;      // [n]
   const int32_t *seg_start;  // [nseg + 1]
-  const uint16_t *seg_of;    // [n]
   const int32_t *seg_link;   // [nseg]  parent joint of the segment's first joint, -1 for roots
-  const int16_t *jump;       // [rounds][nseg] parent segment at the start of each round, -1 when done
-  int njobs;                 // pass-1 lane jobs: runs of whole consecutive segments, about seg_len joints each
-  int pad1;
-  const int32_t *job_start;  // [njobs + 1] first joint of each job
   const uint32_t *jinfo;     // [n] segment of the joint (bits 0-15) | kJStart | kJLink
   const float4 *inv_bind;    // [n][3] rows of B_i
-  const float4 *keys;        // [n_clips][n_keys][n][2]: (qx qy qz qw), (tx ty tz theta)
+  const float4 *keys;        // [n_clips][n_keys][n][2]: (qx qy qz qw), (tx ty tz theta); theta's sign
+                             // bit: the next key lies on the other hemisphere
   const float4 *add_keys;    // additive layer [n_keys][n][2] in the same format, or nullptr
-  // adjoint: depth-first pre-order of the joints (subtrees are contiguous)
-  const int32_t *dfs;        // [n] joint at pre-order slot i
-  const int32_t *dfs_slot;   // [n] slot of joint j
-  const int32_t *sub_end;    // [n] slot one past the subtree of the joint at slot i
+  // adjoint (on views numbered in depth-first pre-order, so a joint's slot
+  // is its index and its subtree is [j, sub_end[j]))
+  const int32_t *sub_end;    // [n] one past the subtree of joint j
   // IK views: the active subtree of a type; view joint j reads row gather[j]
   // of the full type (nullptr = identity).
   const int32_t *gather;

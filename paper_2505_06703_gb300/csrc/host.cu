@@ -33,16 +33,14 @@ struct Segments {
   int nseg = 0, rounds = 0;
   std::vector<int32_t> start, link;
   std::vector<uint16_t> seg_of;
-  std::vector<int16_t> jump;  // [rounds][nseg]
-  std::vector<int32_t> job_start;  // pass-1 lane jobs (runs of whole segments)
   std::vector<uint32_t> jinfo;     // per joint: segment | kJStart | kJLink
 };
 
 // Segments: maximal runs of consecutive joints where each joint's parent is
 // the previous joint (natural chains), each cut into ceil(m / seg_len)
-// pieces of nearly equal length.  Then the pointer-jumping tables over the
-// segment tree: jump[0][g] = segment of the joint g hangs from, and
-// jump[r+1][g] = jump[r][jump[r][g]], until every pointer is -1.
+// pieces of nearly equal length.  Then the number of pointer-jumping rounds
+// over the segment tree: ptr[g] = segment the segment g hangs from, doubled
+// (ptr[g] = ptr[ptr[g]]) until every pointer is -1.
 Segments analyze_segments(const std::vector<int32_t> &par, int seg_len) {
   Segments S;
   const int n = (int)par.size();
@@ -70,25 +68,11 @@ Segments analyze_segments(const std::vector<int32_t> &par, int seg_len) {
     bool any = false;
     for (int g = 0; g < S.nseg; ++g) any |= ptr[g] >= 0;
     if (!any) break;
-    for (int g = 0; g < S.nseg; ++g) S.jump.push_back((int16_t)ptr[g]);
     std::vector<int> nxt(S.nseg);
     for (int g = 0; g < S.nseg; ++g) nxt[g] = ptr[g] < 0 ? -1 : ptr[ptr[g]];
     ptr.swap(nxt);
     ++S.rounds;
   }
-  // lane jobs: consecutive whole segments, greedily grouped to about seg_len
-  // joints, so the pass-1 lanes get balanced walks
-  int acc = 0;
-  S.job_start.push_back(0);
-  for (int g = 0; g < S.nseg; ++g) {
-    const int len = S.start[g + 1] - S.start[g];
-    if (acc > 0 && acc + len > seg_len) {
-      S.job_start.push_back(S.start[g]);
-      acc = 0;
-    }
-    acc += len;
-  }
-  S.job_start.push_back(n);
   S.jinfo.resize(n);
   for (int j = 0; j < n; ++j) {
     const int g = S.seg_of[j];
@@ -424,14 +408,9 @@ struct TypeHost {
     const size_t o_par = B.add(parent.data(), parent.size() * 4);
     const size_t o_dep = B.add(depth.data(), depth.size() * 4);
     const size_t o_ss = B.add(seg.start.data(), seg.start.size() * 4);
-    const size_t o_so = B.add(seg.seg_of.data(), seg.seg_of.size() * 2);
     const size_t o_sl = B.add(seg.link.data(), seg.link.size() * 4);
-    const size_t o_j = B.add(seg.jump.data(), seg.jump.size() * 2);
-    const size_t o_d = B.add(dfsord.dfs.data(), dfsord.dfs.size() * 4);
-    const size_t o_ds = B.add(dfsord.slot.data(), dfsord.slot.size() * 4);
     const size_t o_se = B.add(dfsord.sub_end.data(), dfsord.sub_end.size() * 4);
     const size_t o_g = B.add(gather.data(), gather.size() * 4);
-    const size_t o_js = B.add(seg.job_start.data(), seg.job_start.size() * 4);
     const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
     const size_t o_wt = B.add(ws.tab.data(), ws.tab.size() * 4);
     std::vector<int32_t> blk_out(n);
@@ -456,15 +435,9 @@ struct TypeHost {
     dev.parent = (const int32_t *)(base + o_par);
     dev.depth = (const int32_t *)(base + o_dep);
     dev.seg_start = (const int32_t *)(base + o_ss);
-    dev.seg_of = (const uint16_t *)(base + o_so);
     dev.seg_link = (const int32_t *)(base + o_sl);
-    dev.jump = (const int16_t *)(base + o_j);
-    dev.dfs = (const int32_t *)(base + o_d);
-    dev.dfs_slot = (const int32_t *)(base + o_ds);
     dev.sub_end = (const int32_t *)(base + o_se);
     dev.gather = gather.empty() ? nullptr : (const int32_t *)(base + o_g);
-    dev.njobs = (int)seg.job_start.size() - 1;
-    dev.job_start = (const int32_t *)(base + o_js);
     dev.jinfo = (const uint32_t *)(base + o_ji);
     dev.wk_mode = ws.mode;
     dev.wk_P = ws.P;

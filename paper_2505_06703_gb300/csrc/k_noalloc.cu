@@ -22,7 +22,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kNoAllocMaxRounds = 12;  // ceil(log2(ANIM_MAX_JOINTS)) + 1
 constexpr int kNoAllocSegLen = 16;
 
 // Scratch layout (byte offsets inside g_noalloc_scratch).
@@ -32,8 +31,7 @@ constexpr size_t kOffParent = 512;
 constexpr size_t kOffSegStart = kOffParent + 4 * ANIM_MAX_JOINTS;
 constexpr size_t kOffSegLink = kOffSegStart + 4 * (ANIM_MAX_JOINTS + 64);
 constexpr size_t kOffJinfo = kOffSegLink + 4 * ANIM_MAX_JOINTS;
-constexpr size_t kOffJump = kOffJinfo + 4 * ANIM_MAX_JOINTS;
-constexpr size_t kScratchUsed = kOffJump + 2 * (size_t)kNoAllocMaxRounds * ANIM_MAX_JOINTS;
+constexpr size_t kScratchUsed = kOffJinfo + 4 * ANIM_MAX_JOINTS;
 static_assert(kScratchUsed <= kNoAllocScratchBytes, "scratch layout exceeds the static array");
 static_assert(sizeof(TypeDev) <= kOffQueue, "type record overlaps the queue counter");
 
@@ -193,7 +191,6 @@ extern "C" ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *
   int32_t *start = reinterpret_cast<int32_t *>(h + kOffSegStart);
   int32_t *link = reinterpret_cast<int32_t *>(h + kOffSegLink);
   uint32_t *jinfo = reinterpret_cast<uint32_t *>(h + kOffJinfo);
-  int16_t *jump = reinterpret_cast<int16_t *>(h + kOffJump);
   memcpy(par, parents, sizeof(int32_t) * n_joints);
   int nseg = 0;
   for (int a = 0; a < n_joints;) {  // natural chains cut into near-equal pieces of <= 16
@@ -217,8 +214,6 @@ extern "C" ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *
     bool any = false;
     for (int g = 0; g < nseg; ++g) any |= ptr[g] >= 0;
     if (!any) break;
-    if (rounds == kNoAllocMaxRounds) return set_msg(ANIM_EUNSUPPORTED, "segment tree too deep");
-    memcpy(jump + (size_t)rounds * nseg, ptr, sizeof(int16_t) * nseg);
     for (int g = 0; g < nseg; ++g) nxt[g] = ptr[g] < 0 ? -1 : ptr[ptr[g]];
     memcpy(ptr, nxt, sizeof(int16_t) * nseg);
     ++rounds;
@@ -235,7 +230,6 @@ extern "C" ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *
   T.seg_start = reinterpret_cast<const int32_t *>(scratch + kOffSegStart);
   T.seg_link = reinterpret_cast<const int32_t *>(scratch + kOffSegLink);
   T.jinfo = reinterpret_cast<const uint32_t *>(scratch + kOffJinfo);
-  T.jump = reinterpret_cast<const int16_t *>(scratch + kOffJump);
   T.inv_bind = reinterpret_cast<const float4 *>(d_inv_bind);
   memcpy(h + kOffType, &T, sizeof T);  // queue counter at kOffQueue stays 0 (memset above)
 
