@@ -100,11 +100,10 @@ struct LaunchCfg {
 };
 
 // ---------------------------------------------------------------- kernels
-// Fused persistent scan.  mode: 0 = sampled frame (keys), 1 = local poses (q,t).
+// Arguments of the persistent scan kernels (k_scan_qt's modes, k_scan).
 struct ScanArgs {
   const TypeDev *types;
   const WorkItem *items;
-  const int32_t *n_items_dev;  // device count (frame) or nullptr (use n_items)
   int n_items;
   const int32_t *item_chars;   // character ids referenced by items
   const int64_t *row_off;      // [n_chars + 1]

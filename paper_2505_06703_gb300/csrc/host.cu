@@ -566,8 +566,8 @@ struct anim_plan {
   WorkItem *d_items_frame = nullptr;
   RangeDev *d_ranges = nullptr;
   int n_ranges = 0, n_slots = 0;
-  int32_t *d_n_items = nullptr;
-  int *d_queue = nullptr;  // [0] work-queue head, [1] finished-CTA counter (both back to 0 after each launch)
+  int *d_queue = nullptr;  // work-queue heads and finished-CTA counters, back to 0 after each launch:
+                           // [2], [3] the plain frame's CTA kernel; [0], [1] every other persistent launch
   int32_t *d_used = nullptr, *d_cap = nullptr;
   LaunchCfg cfg_scan{}, cfg_adj{};
   size_t smem_frame = 0;     // plain frame, (q, t) items
@@ -593,7 +593,7 @@ struct anim_plan {
   ~anim_plan() {
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
                     (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
-                    (void *)d_n_items, (void *)d_queue, (void *)d_used,
+                    (void *)d_queue, (void *)d_used,
                     (void *)d_cap, (void *)d_ranges_cta, (void *)d_cap_cta, (void *)d_vert_off,
                     (void *)d_ranges_qa, (void *)d_cap_qa,
                     (void *)d_host_in, (void *)d_host_skin})
@@ -1186,7 +1186,6 @@ int anim_plan_create(anim_ctx *ctx, int64_t n_chars, const int32_t *char_type, a
   std::vector<int32_t> used32(P->used.begin(), P->used.end());
   CK(upload_vec(&P->d_used, used32));
   CK(cudaMalloc(&P->d_sorted, std::max<int64_t>(1, n_chars) * sizeof(int32_t)));
-  CK(cudaMalloc(&P->d_n_items, sizeof(int32_t)));
   CK(cudaMalloc(&P->d_queue, 4 * sizeof(int)));
   CK(cudaMemset(P->d_queue, 0, 4 * sizeof(int)));
   const int rc = plan_schedule(ctx, P.get());

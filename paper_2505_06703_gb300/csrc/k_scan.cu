@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
   const int tid = threadIdx.x;
-  const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
+  const int n_items = a.n_items;
 
   if (tid >= kComputeThreads) {
     producer_loop<0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off, a.time, a.blend_w,

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
   // kernel may start now (it reads only plan tables before its own wait).
   asm volatile("griddepcontrol.launch_dependents;");
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
+  const int n_items = a.n_items;
 
   if (tid >= kComputeThreads) {
     producer_loop<MODE == 1 ? 1 : 0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off,
