@@ -47,3 +47,37 @@ def test_single_rank_helpers():
     w = bench.rank_workload(0)
     assert bench.frame_algorithmic_bytes(w) > 48 * 2_000_000
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_roofline_helpers():
+    """The nominal-peak fractions sit beside every HBM roofline object, and
+    the frame's touched bytes count 228 B per joint."""
+    import bench
+    r = {"roofline": {"unit": "GB/s", "achieved": 790.0},
+         "fwd_bwd": {"roofline": {"unit": "GB/s", "achieved": 395.0}},
+         "other": {"roofline": {"unit": "TFLOP/s", "achieved": 1.0}}}
+    bench.add_nominal_fractions(r)
+    assert r["roofline"]["frac_of_nominal"] == 0.1
+    assert r["fwd_bwd"]["roofline"]["frac_of_nominal"] == 0.05
+    assert "frac_of_nominal" not in r["other"]["roofline"]
+    w = bench.rank_workload(0)
+    joints = sum(len(w["types"][t]["parents"]) for t in w["char_type"])
+    assert bench.frame_touched_bytes(w) == joints * 228
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The stored ncu traffic is keyed by a hash of the frame kernel's
+    sources that a comment edit leaves alone and a code edit changes."""
+    import shutil
+    import bench
+    src = os.path.join(bench.ROOT, "paper_2505_06703_gb300", "csrc")
+    dst = tmp_path / "paper_2505_06703_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    f = dst / "k_scan_qt.cu"
+    text = f.read_text()
+    f.write_text(text.replace("#include <cuda_runtime.h>", "#include <cuda_runtime.h>  // a comment\n/* and a block */", 1))
+    assert bench.kernel_source_hash() == h0
+    f.write_text(text.replace("const int cs2 = 2 * n + 1;", "const int cs2 = 2 * n + 2;", 1))
+    assert bench.kernel_source_hash() != h0
