@@ -56,21 +56,6 @@ __device__ __forceinline__ float dot4(const float4 a, const float4 b) {
   return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
 }
 
-// [R(q / |q|) | t] for any nonzero quaternion q: the quadratic terms are
-// scaled by 2 / |q|^2 instead of normalizing q first.
-__device__ __forceinline__ Aff aff_from_qt_any(const float4 q, const float tx, const float ty, const float tz) {
-  const float s = __fdividef(2.f, dot4(q, q));
-  const float x2 = q.x * s, y2 = q.y * s, z2 = q.z * s;
-  const float xx = q.x * x2, yy = q.y * y2, zz = q.z * z2;
-  const float xy = q.x * y2, xz = q.x * z2, yz = q.y * z2;
-  const float wx = q.w * x2, wy = q.w * y2, wz = q.w * z2;
-  Aff a;
-  a.r0 = make_float4(1.f - (yy + zz), xy - wz, xz + wy, tx);
-  a.r1 = make_float4(xy + wz, 1.f - (xx + zz), yz - wx, ty);
-  a.r2 = make_float4(xz - wy, yz + wx, 1.f - (xx + yy), tz);
-  return a;
-}
-
 __device__ __forceinline__ float4 normalize4(const float4 a) {
   const float s = rsqrtf(dot4(a, a));
   return make_float4(a.x * s, a.y * s, a.z * s, a.w * s);

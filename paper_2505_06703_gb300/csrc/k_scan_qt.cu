@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
     // ---- pass 2: pointer jumping over segments
     const float4 *Y = pass2_qt(b, Lt, P, cs2, tid);
 
-    // ---- pass 3: model pose, matrix of its normalized rotation, (bind,) store
+    // ---- pass 3: model pose, normalize, matrix, (bind,) store
     {
       const int W = n * b.cgroups, cpt = b.cpt;
       float4 *skin4 = reinterpret_cast<float4 *>(a.skin);
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
         for (int c = grp * cpt; c < c1; ++c) {
           QT m = lds_qt(P + c * cs2, j, n);
           if (info & kJ16Link) m = qt_mul(lds_qt(Y, c * nseg + g, C * nseg), m);
-          const Aff M = aff_from_qt_any(m.q, m.t.x, m.t.y, m.t.z);
+          const Aff M = aff_from_qt(normalize4(m.q), m.t.x, m.t.y, m.t.z);
           if (model) stg_aff(model4 + (b.off[c] + j) * 3, M);
           if (skin) stg_aff(skin4 + (b.off[c] + j) * 3, aff_mul(M, B));
         }
