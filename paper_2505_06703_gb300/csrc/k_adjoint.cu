@@ -317,6 +317,10 @@ static_assert(sizeof(ItemBuf) + 2 * (kAdjSmallThreads / 32) * 16 <= kAdjSmallSta
 // no producer warp, small enough that several CTAs share an SM; the
 // hardware schedules the items in waves.  Suits many small items, where the
 // persistent kernel would run each CTA's items one after another.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const AdjointArgs a) {
   extern __shared__ __align__(128) float4 sm[];
@@ -331,10 +335,28 @@ __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const Adj
     const WorkItem wi = a.items[blockIdx.x];
     stage_item<1>(b, (int)blockIdx.x, wi, a.types, a.item_chars, a.row_off, nullptr, nullptr, a.status);
   }
+  __syncthreads();
+  if (MODE != 2) {
+    // warm L2 with the item's rows of poses and loss inputs while the
+    // preceding grid finishes: a prefetch loads nothing into the kernel, and
+    // L2 is coherent, so the loads after the wait see that grid's writes.
+    // The view's rows are a permutation of the character's n rows.
+    const int n = b.T.n;
+    const float *in = MODE == 0 ? a.grad_pos : a.target;
+    for (int c = 0; c < b.C; ++c) {
+      const char *rq = reinterpret_cast<const char *>(a.q + 4 * b.off[c]);
+      const char *rt = reinterpret_cast<const char *>(a.t + 3 * b.off[c]);
+      const char *rg = reinterpret_cast<const char *>(in + 3 * b.off[c]);
+      for (int k = tid; k * 128 < 16 * n; k += kAdjSmallThreads) prefetch_l2(rq + k * 128);
+      for (int k = tid; k * 128 < 12 * n; k += kAdjSmallThreads) {
+        prefetch_l2(rt + k * 128);
+        prefetch_l2(rg + k * 128);
+      }
+    }
+  }
   // poses, targets, the IK step counter and the outputs may belong to the
   // preceding kernel in the stream: wait for it to complete
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  __syncthreads();
   const int step = (MODE == 2) ? *a.step + 1 : 0;
   adjoint_item<MODE, kAdjSmallThreads>(a, b, sm, wsF, wsT, tid, step);
   if (MODE == 2 && tid == 0) {  // the last CTA advances the IK step
