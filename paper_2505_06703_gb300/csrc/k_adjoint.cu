@@ -279,13 +279,19 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a)
   const int tid = threadIdx.x;
   // launched with programmatic stream serialization: the CTAs become
   // resident while the preceding kernel finishes; the queue, the IK step
-  // counter and the inputs are touched only after it has completed
+  // counter and the inputs are read only after it has completed (the first
+  // wave's rows are only prefetched into L2 before that: the work items and
+  // views are plan data)
   asm volatile("griddepcontrol.launch_dependents;");
+  const RowPrefetch pf = MODE == 2 ? RowPrefetch{{a.q, a.t, a.m, a.v}, {4, 3, 4, 4}, 0}
+                                   : RowPrefetch{{a.q, a.t, MODE == 0 ? a.grad_pos : a.target, nullptr}, {4, 3, 3, 0}, 1};
+  if (tid >= kComputeThreads)
+    prefetch_first_wave(bufs[1], a.n_items, a.items, a.types, a.item_chars, a.row_off, pf);
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (tid >= kComputeThreads) {
     producer_loop<1>(bufs, a.queue_head, a.n_items, a.items, a.types, a.item_chars, a.row_off, nullptr, nullptr,
-                     a.status);
+                     a.status, nullptr, LayerIn{nullptr, nullptr}, pf);
     return;
   }
   const int step = (MODE == 2) ? *a.step + 1 : 0;  // 1-based Adam step of this launch
@@ -317,10 +323,6 @@ static_assert(sizeof(ItemBuf) + 2 * (kAdjSmallThreads / 32) * 16 <= kAdjSmallSta
 // no producer warp, small enough that several CTAs share an SM; the
 // hardware schedules the items in waves.  Suits many small items, where the
 // persistent kernel would run each CTA's items one after another.
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const AdjointArgs a) {
   extern __shared__ __align__(128) float4 sm[];

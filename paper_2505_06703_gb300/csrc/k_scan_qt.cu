@@ -33,14 +33,20 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
   // kernel, for the frame): wait for the preceding grid to complete before
   // reading anything it may have written.  The next frame's work-queue
   // kernel may start now (it reads only plan tables before its own wait).
+  // The forward from local poses (fixed work items) prefetches its first
+  // wave's rows of q and t into L2 before the wait, and each next item's
+  // while the current one runs.
   asm volatile("griddepcontrol.launch_dependents;");
+  const RowPrefetch pf = MODE == 1 ? RowPrefetch{{a.q, a.t, nullptr, nullptr}, {4, 3, 0, 0}, 0} : RowPrefetch{};
+  if (MODE == 1 && tid >= kComputeThreads)
+    prefetch_first_wave(bufs[1], a.n_items, a.items, a.types, a.item_chars, a.row_off, pf);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int n_items = a.n_items;
 
   if (tid >= kComputeThreads) {
     producer_loop<MODE == 1 ? 1 : 0>(bufs, a.queue_head, n_items, a.items, a.types, a.item_chars, a.row_off,
                                      a.time, a.blend_w, a.status, nullptr,
-                                     MODE == 2 ? LayerIn{a.layer_w, a.add_w} : LayerIn{nullptr, nullptr});
+                                     MODE == 2 ? LayerIn{a.layer_w, a.add_w} : LayerIn{nullptr, nullptr}, pf);
     return;
   }
 

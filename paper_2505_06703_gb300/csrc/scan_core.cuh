@@ -153,13 +153,72 @@ __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &w
   __syncwarp();
 }
 
-// Producer warp main loop: keep one item ahead of the compute warps.
+// Per-joint input arrays that the compute warps read from global memory,
+// row r of array i at base[i] + floats[i] * r (unused slots nullptr).
+// perm: a view's rows are a permutation of the character's n rows (the
+// adjoint's depth-first views), so the contiguous range covers them.
+struct RowPrefetch {
+  const float *base[4];
+  int floats[4];
+  int perm;
+};
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
+// One warp: hint L2 to fetch the rows of item b's characters (rows off..off+n
+// of each, or off + gather[j] for a view) of every array of pf.  A prefetch
+// returns nothing to the kernel, so it may run ahead of the wait for a
+// preceding grid: L2 is the point of coherence for that grid's writes.
+__device__ __forceinline__ void prefetch_rows(const ItemBuf &b, const RowPrefetch &pf) {
+  const int lane = threadIdx.x & 31;
+  const int n = b.T.n;
+  const int32_t *gat = b.T.gather;
+  for (int c = 0; c < b.C; ++c) {
+    const long long off = b.off[c];
+    if (!gat || pf.perm) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (!pf.base[i]) continue;
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(pf.base[i] + pf.floats[i] * off);
+        const uintptr_t hi = lo + (uintptr_t)(4 * pf.floats[i]) * (uintptr_t)n;
+        for (uintptr_t p = (lo & ~(uintptr_t)127) + 128 * (uintptr_t)lane; p < hi; p += 32 * 128)
+          prefetch_l2(reinterpret_cast<const void *>(p));
+      }
+    } else {
+      // a view's rows: one hint per 128-byte line where the row starts it
+      // (the previous joint's row from the lane below)
+      long long carry = -1;
+#pragma unroll 4
+      for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + lane;
+        const long long r = j < n ? off + __ldg(gat + j) : -1;
+        long long rp = __shfl_up_sync(0xffffffffu, r, 1);
+        if (lane == 0) rp = carry;
+        carry = __shfl_sync(0xffffffffu, r, 31);
+        if (r < 0) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (!pf.base[i]) continue;
+          const long long bytes = 4LL * pf.floats[i];
+          if (rp < 0 || ((r * bytes) >> 7) != ((rp * bytes) >> 7)) prefetch_l2(pf.base[i] + pf.floats[i] * r);
+        }
+      }
+    }
+  }
+}
+
+// Producer warp main loop: keep one item ahead of the compute warps, and
+// (pf non-empty) warm L2 with the next item's rows while the current one
+// runs.
 template <int MODE>
 __device__ __forceinline__ void producer_loop(ItemBuf *bufs, int *queue_head, int n_items, const WorkItem *items,
                                               const TypeDev *types, const int32_t *item_chars,
                                               const int64_t *row_off, const float *time, const float *blend_w,
                                               int *status, const int64_t *vert_off = nullptr,
-                                              LayerIn layers = LayerIn{nullptr, nullptr}) {
+                                              LayerIn layers = LayerIn{nullptr, nullptr},
+                                              const RowPrefetch &pf = RowPrefetch{}) {
   int cur = 0;
   fetch_item<MODE>(bufs[0], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status,
                    vert_off, layers);
@@ -169,9 +228,27 @@ __device__ __forceinline__ void producer_loop(ItemBuf *bufs, int *queue_head, in
     cur ^= 1;
     fetch_item<MODE>(bufs[cur], queue_head, n_items, items, types, item_chars, row_off, time, blend_w, status,
                      vert_off, layers);
+    if (pf.base[0] && bufs[cur].item >= 0) prefetch_rows(bufs[cur], pf);
     __threadfence_block();
     handoff_sync();
   }
+}
+
+// Before the wait for a preceding grid: stage item blockIdx.x (the first
+// wave of the queue holds items 0 .. gridDim.x - 1, in some order across the
+// CTAs) into scratch buffer b and prefetch its rows.  Only for queues and
+// tables that no preceding grid writes, and only when the CTAs get more than
+// one item each: with one, the compute warps read the rows right after the
+// wait anyway, and the extra staging measured slower (a persistent fwd+bwd
+// launch of one 8-character item per CTA: 18.4 -> 22.8 us).
+__device__ __forceinline__ void prefetch_first_wave(ItemBuf &b, int n_items, const WorkItem *items,
+                                                    const TypeDev *types, const int32_t *item_chars,
+                                                    const int64_t *row_off, const RowPrefetch &pf) {
+  if (n_items <= (int)gridDim.x) return;
+  const WorkItem wi = items[blockIdx.x];
+  if (wi.count <= 0) return;
+  stage_item<1>(b, (int)blockIdx.x, wi, types, item_chars, row_off, nullptr, nullptr, nullptr);
+  prefetch_rows(b, pf);
 }
 
 // Dynamic shared memory of one work item:
