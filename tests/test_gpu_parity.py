@@ -410,6 +410,90 @@ def test_config5_ik_subset(torch):
     assert abs(err_g.mean() - err_r.mean()) <= 0.25 * err_r.mean()
 
 
+def _rows(off, chars):
+    return np.concatenate([np.arange(off[c], off[c + 1]) for c in chars])
+
+
+def test_forward_local_full_back_to_back(torch):
+    """The forward from local poses on config 2's 2,098,176 joints under the
+    schedule the bench times ([32, 3, 2048, 0]: 1,025 work items on 456
+    persistent CTAs, so the producer warps prefetch their first items' rows
+    ahead of the grid-dependency wait and each next item's rows during the
+    current one).  Three launches back to back on one stream: two input sets,
+    then the first set rewritten in place by a torch kernel and run again;
+    sampled characters against the oracle."""
+    w = synth.config2()
+    types, ct = w["types"], w["char_type"]
+    off = oracle.offsets(ct, types)
+    n = int(off[-1])
+    ctx, plan = _gpu.setup(w)
+    ctx.set_schedule(plan, [32, 3, 2048, 0])
+    rng = np.random.default_rng(77)
+    q1, t1 = synth.local_poses(rng, n, unnormalized=True)
+    q2, t2 = synth.local_poses(rng, n)
+    dq1, dt1, dq2, dt2 = _gpu.cuda(q1), _gpu.cuda(t1), _gpu.cuda(q2), _gpu.cuda(t2)
+    s1, _ = ctx.forward_local(plan, dq1, dt1, skin=True, model=False)
+    s2, _ = ctx.forward_local(plan, dq2, dt2, skin=True, model=False)
+    dq1.copy_(dq1[:, [3, 0, 1, 2]])
+    dt1.mul_(2.0)
+    s3, m3 = ctx.forward_local(plan, dq1, dt1, skin=True, model=True)
+    sel = list(range(0, len(ct), 61)) + [len(ct) - 1]
+    rows = _rows(off, sel)
+    ws = synth.subset(w, sel)
+    for got, q, t in ((s1, q1, t1), (s2, q2, t2), (s3, q1[:, [3, 0, 1, 2]], 2.0 * t1)):
+        ref, mref = oracle.forward_qt(types, ct[sel], q[rows], t[rows])
+        _gpu.assert_skin_close(got.cpu().numpy().reshape(n, 12)[rows], ref, ws)
+    _gpu.assert_skin_close(m3.cpu().numpy().reshape(n, 12)[rows], mref, ws)
+
+
+def test_config5_ik_full_second_step(torch):
+    """Two IK steps on all 8,192 characters of config 5 under the bench's
+    schedule ([8, 2, 4096, 1, 0]: persistent kernel, several items per CTA,
+    rows prefetched ahead of the grid-dependency wait).  The second launch
+    reads the q, m and v the first one wrote; on sampled characters its
+    result must equal one oracle Adam step (gradient of the effector loss by
+    the oracle's reverse pass) taken from the GPU's own state after step 1."""
+    w = synth.config5()
+    types, ct, eff = w["types"], w["char_type"], w["effectors"]
+    ctx, plan, t, targets = _ik_setup(torch, w)
+    ctx.set_schedule(plan, [8, 2, 4096, 1, 0])
+    q = _gpu.cuda(w["q0"])
+    m, v = torch.zeros_like(q), torch.zeros_like(q)
+    loss = torch.zeros(len(ct), device="cuda")
+    ik = ctx.ik(plan, eff)
+    ik.reset()
+    ik.step(q, m, v, t, targets, lr=w["lr"], betas=w["betas"], eps=w["eps"], loss=loss)
+    q1, m1, v1 = (x.cpu().numpy().astype(np.float64) for x in (q, m, v))
+    ik.step(q, m, v, t, targets, lr=w["lr"], betas=w["betas"], eps=w["eps"], loss=loss)
+    q2, m2, v2 = (x.cpu().numpy() for x in (q, m, v))
+    off = oracle.offsets(ct, types)
+    sel = list(range(0, len(ct), 257)) + [len(ct) - 2, len(ct) - 1]
+    rows = _rows(off, sel)
+    offs = oracle.offsets(ct[sel], types)
+    tg = targets.cpu().numpy().astype(np.float64)
+    _, M = oracle.forward_qt(types, ct[sel], q1[rows], w["t"][rows], with_skin=False)
+    g = np.zeros((len(rows), 3))
+    for k, c in enumerate(sel):
+        for e, j in enumerate(eff[ct[c]]):
+            g[offs[k] + j] = 2 * (M[offs[k] + j, :, 3] - tg[c, e])
+    dq, _ = oracle.grad(types, ct[sel], q1[rows], w["t"][rows], g)
+    p_ref, m_ref, v_ref = q1[rows].copy(), m1[rows].copy(), v1[rows].copy()
+    oracle.adam(p_ref, np.ascontiguousarray(dq), m_ref, v_ref, 2, w["lr"], *w["betas"], w["eps"])
+    scale = max(1.0, np.abs(dq).max())
+    # m and v are linear in the gradient, within the gradient tolerance
+    # (1e-4 * max(1, max |gradient|)); a stale q, m or v read by the second
+    # launch would be off by orders more
+    assert np.abs(m2[rows] - m_ref).max() <= 1e-4 * scale
+    assert np.abs(v2[rows] - v_ref).max() <= 1e-4 * scale * scale
+    # q moves by lr * m_hat / (sqrt(v_hat) + eps), whose error grows as the
+    # gradient shrinks: compare where it is well above FP32 noise in both
+    # steps (1 % of the largest), to 1 % of a step of size lr
+    big = np.abs(dq).max()
+    clear = (np.abs(dq) > 1e-2 * big) & (np.abs(m1[rows]) > 1e-3 * big)
+    assert clear.sum() > 100
+    assert np.abs(q2[rows] - p_ref)[clear].max() < 1e-2 * w["lr"]
+
+
 # ------------------------------------------------------------------ edge cases
 def _edge_types(rng):
     return [synth.make_type(np.array([-1], np.int32), rng, with_clips=True),               # one joint
