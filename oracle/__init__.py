@@ -12,8 +12,10 @@ Functions and the passages they follow (paper section, equation):
     special cases (endpoints, same-axis closed form, constant angular
     velocity, near-parallel branch) and the sampling special cases (exact
     key times, wrap, blend weights 0 and 1).  The combination of the two
-    for general inputs follows the reading stated in the header of
-    oracle.c; beyond those special cases it is "parity unpinned".
+    for general inputs (the reading stated in the header of oracle.c) is
+    pinned against scipy's Slerp composed stage by stage -- each clip's
+    bracketing keys at the key fraction, then the two clip poses at the
+    blend weight -- on random keys, signs, times and weights.
   * forward / forward_qt  -- Hierarchy-Scan, Eq. 1, by the sequential
     parent-before-child traversal (Sec. 3.2.1 ordering).  Pinned by a
     brute-force root-to-joint product over every tree of up to 7 joints,

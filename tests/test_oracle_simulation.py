@@ -1,6 +1,7 @@
 """Pins for the oracle's Simulation stage (Sec. 1 step 1; Sec. 2 keeps
 keyframe interpolation and blending): slerp, key sampling and the two-clip
-blend.  Checked against scipy's Slerp (a library routine), closed forms for
+blend.  Checked against scipy's Slerp (a library routine; for general keys
+and weights the whole sample-and-blend composed from it), closed forms for
 same-axis rotations, the constant-angular-velocity property, and exact
 special cases (key times, wrap-around, blend weights 0 and 1)."""
 import numpy as np
@@ -146,6 +147,38 @@ def test_sample_same_axis_closed_form():
             tref = (1 - wgt) * ((1 - al) * kt[0, k0, j] + al * kt[0, k1, j]) + \
                 wgt * ((1 - al) * kt[1, k0, j] + al * kt[1, k1, j])
             np.testing.assert_allclose(t[j], tref, atol=1e-12)
+
+
+def test_sample_general_matches_scipy_composition():
+    """General keys (random axes, random quaternion signs), times and
+    weights: the sampled pose is scipy's Slerp of each clip's bracketing keys
+    at the key fraction, then scipy's Slerp of the two clip poses at the
+    blend weight; translations lerp likewise."""
+    rng = np.random.default_rng(8)
+    keys = _keys(rng, n=9)
+    flip = rng.random(keys.shape[:3]) < 0.5
+    keys[..., :4][flip] *= -1.0  # q and -q: the shorter arc must be taken either way
+    nk = keys.shape[1]
+    for tm, wgt in zip(rng.uniform(-1.5, 2.5, 40), rng.uniform(0, 1, 40)):
+        tm, wgt = float(np.float32(tm)), float(np.float32(wgt))
+        u = np.float32(tm) * np.float32(30.0)
+        k0 = int(np.floor(u)) % nk
+        k1 = (k0 + 1) % nk
+        al = float(u - np.floor(u))
+        q, t = oracle.sample_local(keys, 30.0, tm, wgt)
+        kq = keys[..., :4].astype(np.float64)
+        kt = keys[..., 4:7].astype(np.float64)
+        for j in range(keys.shape[2]):
+            qa = Slerp([0, 1], Rotation.from_quat([kq[0, k0, j], kq[0, k1, j]]))([al])
+            qb = Slerp([0, 1], Rotation.from_quat([kq[1, k0, j], kq[1, k1, j]]))([al])
+            ref = Slerp([0, 1], Rotation.concatenate([qa, qb]))([wgt]).as_matrix()[0]
+            # the oracle takes the angle by arccos of the dot product, which
+            # loses digits as two rotations approach each other (error about
+            # machine epsilon / angle; 3e-10 seen here): hence 1e-8
+            np.testing.assert_allclose(Rotation.from_quat(q[j]).as_matrix(), ref, atol=1e-8)
+            ta = (1 - al) * kt[0, k0, j] + al * kt[0, k1, j]
+            tb = (1 - al) * kt[1, k0, j] + al * kt[1, k1, j]
+            np.testing.assert_allclose(t[j], (1 - wgt) * ta + wgt * tb, atol=1e-12)
 
 
 def test_frame_chain_matches_stagewise():
