@@ -237,6 +237,15 @@ def setup_ctx(w: dict, device: int):
     return ctx, plan
 
 
+def set_or_tune(ctx, plan, schedule, which: int):
+    """Apply a given schedule, else run the library's autotuner (anim_tune
+    mode `which`) for this workload."""
+    if schedule:
+        ctx.set_schedule(plan, schedule)
+    else:
+        ctx.tune(plan, which)
+
+
 def time_events(fn, steps: int, warmup: int):
     """Run fn(s) warmup + steps times on the current stream; return the
     CUDA-event milliseconds of the timed steps (synchronized on both sides)."""
@@ -420,14 +429,14 @@ def run_ours(args) -> dict:
     return result
 
 
-def run_mixed_frame(device, dev, world, peak) -> dict:
+def run_mixed_frame(device, dev, world, peak, schedule=None) -> dict:
     """Batched heterogeneous frame (10,000 characters of 5 types, 32 to 2,048
     joints, depths 8 to 2,048): the autotuned schedule, frames replayed from
     one CUDA graph with outputs rotated over buffers larger than L2."""
     import torch
     w = synth.config3()
     ctx, plan = setup_ctx(w, device)
-    ctx.tune(plan, 0)
+    set_or_tune(ctx, plan, schedule, 0)
     joints = plan.total
     n_out = max(2, math.ceil(2.5 * L2_BYTES / (joints * 48)))
     outs = [torch.empty((joints, 12), dtype=torch.float32, device=dev) for _ in range(n_out)]
@@ -457,7 +466,7 @@ def run_mixed_frame(device, dev, world, peak) -> dict:
                          "note": "whole frame (work queue + kernels), frames back to back in one CUDA graph"}}
 
 
-def run_skinned_frame(device, dev, world, peak) -> dict:
+def run_skinned_frame(device, dev, world, peak, schedule=None) -> dict:
     """The frame with linear blend skinning fused in: the frame's characters
     with a 1,500-vertex mesh per type (about 3,000 faces), positions and
     normals written, skin matrices kept on chip; frames back to back in one
@@ -467,7 +476,7 @@ def run_skinned_frame(device, dev, world, peak) -> dict:
     ctx, plan = setup_ctx(w, device)
     for i, t in enumerate(w["types"]):
         ctx.upload_mesh(i, t["mesh"])
-    ctx.tune(plan, 3)  # the skinned frame's own schedule
+    set_or_tune(ctx, plan, schedule, 3)  # the skinned frame's own schedule
     nv = int(ctx.vertex_offsets(plan)[-1])
     n_out = max(2, math.ceil(2.5 * L2_BYTES / (nv * 24)))
     outs = [torch.empty((nv, 6), dtype=torch.float32, device=dev) for _ in range(n_out)]
@@ -500,7 +509,7 @@ def run_skinned_frame(device, dev, world, peak) -> dict:
                          "frac": round(achieved / peak, 4), "algorithmic_bytes": alg}}
 
 
-def run_layered_frame(device, dev, world, peak) -> dict:
+def run_layered_frame(device, dev, world, peak, schedule=None) -> dict:
     """The frame with layered blending: the frame's characters with 4 clips
     per type blended by per-character weights plus an additive layer;
     frames back to back in one CUDA graph, outputs rotated past L2."""
@@ -509,7 +518,7 @@ def run_layered_frame(device, dev, world, peak) -> dict:
     ctx, plan = setup_ctx(w, device)
     for i, t in enumerate(w["types"]):
         ctx.upload_additive(i, t["add_keys"], t["rate_hz"])
-    ctx.tune(plan, 4)  # the layered frame's own schedule
+    set_or_tune(ctx, plan, schedule, 4)  # the layered frame's own schedule
     joints = plan.total
     n_out = max(2, math.ceil(2.5 * L2_BYTES / (joints * 48)))
     outs = [torch.empty((joints, 12), dtype=torch.float32, device=dev) for _ in range(n_out)]
@@ -585,7 +594,7 @@ def run_crowd(device, dev, world) -> dict:
                         "triangles each) at 1920x1080", "schedule": ctx.get_schedule(plan)}
 
 
-def run_ik(device, dev, world, peak) -> dict:
+def run_ik(device, dev, world, peak, schedule=None) -> dict:
     """Batched IK (8,192 characters, 128- and 1,024-joint types, 8 effectors
     each): 200 Adam steps, each one fused launch (forward over the effector
     ancestors, effector loss, adjoint, Adam), the whole run one CUDA graph.
@@ -613,7 +622,10 @@ def run_ik(device, dev, world, peak) -> dict:
     q0 = torch.as_tensor(w["q0"], device=dev)
     q, m, v = q0.clone(), torch.zeros_like(q0), torch.zeros_like(q0)
     loss = torch.zeros(plan.n_chars, device=dev)
-    ctx.tune_ik(plan, eff)  # the IK step's schedule; the IK object keeps it
+    if schedule:
+        ctx.set_schedule(plan, schedule)
+    else:
+        ctx.tune_ik(plan, eff)  # the IK step's schedule; the IK object keeps it
     ik = ctx.ik(plan, eff)
     n_steps = int(w["n_steps"])
     stream = torch.cuda.Stream()
@@ -660,7 +672,7 @@ def run_ik(device, dev, world, peak) -> dict:
                          "note": "108 B per active joint (q, t, m, v in; q, m, v out) + targets"}}
 
 
-def time_forward_methods(w: dict, device: int, dev: str, world: int, algs=(1, 2, 3, 4, 5)) -> dict:
+def time_forward_methods(w: dict, device: int, dev: str, world: int, algs=(1, 2, 3, 4, 5), schedule=None) -> dict:
     """Hierarchy-Scan + bind from given local poses on workload w: our
     autotuned forward kernel, the plain level-synchronous kernel and the
     paper's Algorithms 1-4 (one CTA per character, one thread per joint), each
@@ -668,7 +680,7 @@ def time_forward_methods(w: dict, device: int, dev: str, world: int, algs=(1, 2,
     past the L2 size.  Milliseconds per launch."""
     import torch
     ctx, plan = setup_ctx(w, device)
-    ctx.tune(plan, 1)
+    set_or_tune(ctx, plan, schedule, 1)
     q, t = synth.local_poses(np.random.default_rng(7), plan.total, t_half=0.0005)
     q, t = torch.as_tensor(q, device=dev), torch.as_tensor(t, device=dev)
     n_out = max(2, math.ceil(2.5 * L2_BYTES / (plan.total * 48)))
@@ -815,6 +827,28 @@ def run_reference(args) -> dict | None:
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_only(args) -> dict:
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    peak = measured_peaks().get("hbm_gbs") or 6800.0
+    sched = [int(x) for x in args.schedule.split(",")] if args.schedule else None
+    if args.only == "forward":
+        res = time_forward_methods(rank_workload(rank), local, dev, world, algs=(), schedule=sched)
+    else:
+        fn = {"mixed": run_mixed_frame, "ik": run_ik, "skinned": run_skinned_frame, "layers": run_layered_frame}
+        res = fn[args.only](local, dev, world, peak, schedule=sched)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return {"only": args.only, "n_gpus": world, "result": res}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -826,6 +860,9 @@ def main():
     ap.add_argument("--schedule", default="", help="seg_len,ctas_per_sm,joints_per_item,walk[,adj_ctas] for the frame "
                                                    "instead of running the autotuner")
     ap.add_argument("--schedule-bwd", default="", help="the same for the forward+adjoint measurement")
+    ap.add_argument("--only", choices=["mixed", "ik", "skinned", "layers", "forward"], default="",
+                    help="run one of the extra workloads alone (under --schedule if given, else autotuned) and "
+                         "print its result object; a short command for profiling its kernel")
     ap.add_argument("--paper-sweep", action="store_true",
                     help="print the depth sweep of the paper's experiment (our forward kernel, the plain kernel, "
                          "the paper's Algorithms 1-4) instead of the bench line")
@@ -839,6 +876,11 @@ def main():
         return
     if args.paper_sweep:
         r = run_paper_sweep(args)
+        if dist_env()[1] == 0:
+            print(json.dumps(r))
+        return
+    if args.only:
+        r = run_only(args)
         if dist_env()[1] == 0:
             print(json.dumps(r))
         return
