@@ -883,7 +883,8 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   if (ctx->adj_ctas > 0)
     P->cfg_adj = {kAdjSmallThreads, std::max(1, P->n_items_adj), std::max<size_t>(smem_a, 16)};
   else
-    P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16)};
+    P->cfg_adj = {kAdjThreads, std::max(1, std::min(grid, P->n_items_adj)), std::max<size_t>(smem_a, 16),
+                  ctx->ctas_per_sm >= 3 ? 3 : 2};
   P->smem_frame = std::max<size_t>(smem_f, 16);
   P->smem_frame_mat = std::max<size_t>(smem_s, 16);
   P->version = ctx->version;
@@ -1636,7 +1637,8 @@ int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_
   if (ctx->adj_ctas > 0)
     K->cfg = {kAdjSmallThreads, std::max(1, K->n_items), smem};
   else
-    K->cfg = {kAdjThreads, std::max(1, std::min(ctx->sm_count * ctx->ctas_per_sm, K->n_items)), smem};
+    K->cfg = {kAdjThreads, std::max(1, std::min(ctx->sm_count * ctx->ctas_per_sm, K->n_items)), smem,
+              ctx->ctas_per_sm >= 3 ? 3 : 2};
   ctx->iks.insert(K.get());
   *out = K.release();
   return ANIM_OK;
@@ -1766,7 +1768,6 @@ static void for_each_candidate(const anim_ctx *ctx, int which, F &&f) {
             if (which != 2 && jpi < 1024) continue;  // small items only pay off in the one-item adjoint
             if (which == 2 && adj_c == 0 && jpi < 1024) continue;
             if (which == 2 && adj_c > 0 && cps != 2) continue;  // CTAs per SM of the persistent kernels: unused
-            if (cps == 3 && which == 2) continue;  // the persistent adjoint kernel is built for up to 2 CTAs/SM
             f(seg, cps, jpi, walk, adj_c);
           }
 }

@@ -270,9 +270,10 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
 }
 
 // Persistent kernel: 8 compute warps and one producer warp staging the next
-// item, items from the queue (the frame kernel's CTA layout).
-template <int MODE>
-__global__ void __launch_bounds__(kCtaThreads, 2) k_adjoint(const AdjointArgs a) {
+// item, items from the queue (the frame kernel's CTA layout); built for 2 or
+// 3 resident CTAs per SM (MINB).
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kCtaThreads, MINB) k_adjoint(const AdjointArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
   __shared__ float4 wsF[32], wsT[32];
@@ -371,6 +372,9 @@ __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const Adj
   }
 }
 
+template <int MODE, int MINB>
+static cudaError_t launch_adj_persistent(const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st);
+
 template <int MODE>
 static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   if (cfg.threads == kAdjSmallThreads) {
@@ -393,9 +397,15 @@ static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cuda
     lc.numAttrs = 1;
     return cudaLaunchKernelEx(&lc, k_adjoint_small<MODE>, a);
   }
+  return cfg.min_blocks >= 3 ? launch_adj_persistent<MODE, 3>(a, cfg, st) : launch_adj_persistent<MODE, 2>(a, cfg, st);
+}
+
+template <int MODE, int MINB>
+static cudaError_t launch_adj_persistent(const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   static size_t set_smem = 0;
   if (cfg.smem > set_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_adjoint<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_adjoint<MODE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
     set_smem = cfg.smem;
   }
@@ -409,7 +419,7 @@ static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cuda
   at[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, k_adjoint<MODE>, a);
+  return cudaLaunchKernelEx(&lc, k_adjoint<MODE, MINB>, a);
 }
 
 cudaError_t launch_adjoint(int mode, const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
