@@ -446,17 +446,18 @@ def test_forward_local_full_back_to_back(torch):
     _gpu.assert_skin_close(m3.cpu().numpy().reshape(n, 12)[rows], mref, ws)
 
 
-def test_config5_ik_full_second_step(torch):
-    """Two IK steps on all 8,192 characters of config 5 under the bench's
-    schedule ([8, 2, 4096, 1, 0]: persistent kernel, several items per CTA,
-    rows prefetched ahead of the grid-dependency wait).  The second launch
+@pytest.mark.parametrize("sched", [[8, 2, 4096, 1, 0], [4, 3, 1024, 1, 0]])
+def test_config5_ik_full_second_step(torch, sched):
+    """Two IK steps on all 8,192 characters of config 5 under schedules the IK
+    autotuner picks (persistent kernel, its 2- and 3-CTA/SM builds, several
+    items per CTA, rows prefetched ahead of the grid-dependency wait).  The second launch
     reads the q, m and v the first one wrote; on sampled characters its
     result must equal one oracle Adam step (gradient of the effector loss by
     the oracle's reverse pass) taken from the GPU's own state after step 1."""
     w = synth.config5()
     types, ct, eff = w["types"], w["char_type"], w["effectors"]
     ctx, plan, t, targets = _ik_setup(torch, w)
-    ctx.set_schedule(plan, [8, 2, 4096, 1, 0])
+    ctx.set_schedule(plan, sched)
     q = _gpu.cuda(w["q0"])
     m, v = torch.zeros_like(q), torch.zeros_like(q)
     loss = torch.zeros(len(ct), device="cuda")
