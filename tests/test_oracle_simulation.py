@@ -172,10 +172,11 @@ def test_sample_general_matches_scipy_composition():
             qa = Slerp([0, 1], Rotation.from_quat([kq[0, k0, j], kq[0, k1, j]]))([al])
             qb = Slerp([0, 1], Rotation.from_quat([kq[1, k0, j], kq[1, k1, j]]))([al])
             ref = Slerp([0, 1], Rotation.concatenate([qa, qb]))([wgt]).as_matrix()[0]
-            # the oracle takes the angle by arccos of the dot product, which
-            # loses digits as two rotations approach each other (error about
-            # machine epsilon / angle; 3e-10 seen here): hence 1e-8
-            np.testing.assert_allclose(Rotation.from_quat(q[j]).as_matrix(), ref, atol=1e-8)
+            # the oracle interpolates the float32 keys as stored, whose norms
+            # differ from 1 by float32 rounding, while scipy normalizes them
+            # first: the two paths differ by up to about 2e-8 (a wrong term,
+            # sign, key or weight shows at 1e-3 and above)
+            np.testing.assert_allclose(Rotation.from_quat(q[j]).as_matrix(), ref, atol=1e-7)
             ta = (1 - al) * kt[0, k0, j] + al * kt[0, k1, j]
             tb = (1 - al) * kt[1, k0, j] + al * kt[1, k1, j]
             np.testing.assert_allclose(t[j], (1 - wgt) * ta + wgt * tb, atol=1e-12)
