@@ -805,6 +805,14 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def host_cores() -> int:
+    """Cores this process may run on (its affinity mask where the OS has one)."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def _oracle_share(share: int, n_shares: int, warm: int, reps: int, ready, start, out) -> None:
     """One process of the all-cores oracle timing: its contiguous share of the
     frame's characters, `warm` untimed frames, then `reps` timed ones after the
@@ -831,7 +839,7 @@ def oracle_all_cores(reps: int, warm: int = 1, workers: int | None = None) -> tu
     has started), all shares run `reps` frames at once; returns (wall seconds
     from the start signal to the last share's end, processes)."""
     import multiprocessing as mp
-    n = workers or os.cpu_count() or 1
+    n = workers or host_cores()
     ctx = mp.get_context("spawn")
     ready, out, start = ctx.Queue(), ctx.Queue(), ctx.Event()
     procs = [ctx.Process(target=_oracle_share, args=(i, n, warm, reps, ready, start, out)) for i in range(n)]
@@ -879,7 +887,7 @@ def cpu_baseline(min_seconds: float = 6.0) -> dict:
     dt = time.perf_counter() - t0
     single = {"value": reps * joints / dt, "cores": 1,
               "sample": f"full frame ({joints:,} joints) x {reps} in {dt:.1f} s, FP64, one host thread"}
-    n = os.cpu_count() or 1
+    n = host_cores()
     reps_all = max(1, math.ceil(min_seconds / (dt / reps) * n / 2))  # about min_seconds / 2 of wall time
     try:
         dt_all, n = oracle_all_cores(reps_all)
