@@ -81,3 +81,13 @@ def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.kernel_source_hash() == h0
     f.write_text(text.replace("const int cs2 = 2 * n + 1;", "const int cs2 = 2 * n + 2;", 1))
     assert bench.kernel_source_hash() != h0
+
+
+def test_oracle_on_all_cores_helper():
+    """The all-cores CPU baseline: spawned processes each time their share of
+    the frame's characters from one start signal; the CPU model is named."""
+    import bench
+    dt, n = bench.oracle_all_cores(reps=1, warm=1, workers=2)
+    assert n == 2 and dt > 0
+    assert bench.host_cores() >= 1
+    assert bench.cpu_model()
