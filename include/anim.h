@@ -309,8 +309,8 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
 
 /* Autotuner (no counterpart in the paper; it picks the schedule of the
  * scan): times every candidate schedule -- segment length 4/8/16/32 for the
- * pointer-jumping scan, 1, 2 or 3 resident CTAs per SM (3 for the frame and
- * forward only), work items of about 1,024/2,048/4,096 joints, and for the
+ * pointer-jumping scan, 1, 2 or 3 resident CTAs per SM of the persistent
+ * kernels, work items of about 1,024/2,048/4,096 joints, and for the
  * frame whether walkable types (chain schedules of at most 160 steps with
  * most lanes busy, and pure chains) run on the one-warp chain-walk kernel
  * beside the segmented kernel -- of
