@@ -290,19 +290,26 @@ ANIM_API int anim_loss_backward(anim_ctx *ctx, const anim_plan *plan, const floa
 
 /* Batched IK: n_eff effector joints per type (host [n_types_of_ctx][n_eff],
  * entries for types the plan does not use are ignored).  The IK object owns
- * the active-subtree tables and a device step counter. */
+ * the active-subtree tables, a device step counter and its own Adam state
+ * for the active joints only (2 x 16 B per active joint, zeroed here). */
 ANIM_API int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_t *effectors, anim_ik **out);
 ANIM_API int anim_ik_destroy(anim_ctx *ctx, anim_ik *ik);
 
-/* Reset the IK step counter to 0 (asynchronous on stream). */
+/* Reset the IK step counter to 0 and zero the object's own Adam state
+ * (asynchronous on stream). */
 ANIM_API int anim_ik_reset(anim_ctx *ctx, anim_ik *ik, void *stream);
 
 /* One IK step, all in one kernel: forward over the effectors' ancestors,
  * loss sum_e |p_e - target_e|^2, adjoint, and an Adam update (PyTorch's
- * definition, step counter kept on the device and incremented) of d_q,
- * d_m, d_v ([total][4], updated in place).  d_t [total][3] fixed;
- * d_targets [n_chars][n_eff][3]; d_loss[n_chars] (nullable) receives each
- * character's loss before the update. */
+ * definition, step counter kept on the device and incremented) of d_q
+ * ([total][4], updated in place) with the moments in d_m, d_v ([total][4],
+ * updated in place), or -- both NULL -- in the object's own state, which
+ * holds the active joints only, contiguous in the active subtree's order
+ * (whole 32-byte sectors instead of the caller's scattered 16-byte rows).
+ * Only the active joints' rows of d_q, d_m, d_v are read or written.  d_t [total][3] fixed; d_targets
+ * [n_chars][n_eff][3]; d_loss[n_chars] (nullable) receives each
+ * character's loss before the update.  ANIM_EINVAL if exactly one of d_m,
+ * d_v is NULL. */
 ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v, const float *d_t,
                  const float *d_targets, float lr, float beta1, float beta2, float eps, float *d_loss,
                  void *stream);

@@ -384,6 +384,8 @@ class IK:
         self.ctx._ck(self.ctx.lib.anim_ik_reset(self.ctx.h, self.h, _stream(stream)))
 
     def step(self, q, m, v, t, targets, lr=1e-2, betas=(0.9, 0.999), eps=1e-8, loss=None, stream=None):
+        """One fused IK step; m = v = None keeps Adam's moments in the IK
+        object's own state (active joints only; zeroed by reset())."""
         self.ctx._ck(self.ctx.lib.anim_ik_step(self.ctx.h, self.h, _dptr(q), _dptr(m), _dptr(v), _dptr(t),
                                                _dptr(targets), float(lr), float(betas[0]), float(betas[1]),
                                                float(eps), _dptr(loss), _stream(stream)))

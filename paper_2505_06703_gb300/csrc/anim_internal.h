@@ -176,7 +176,8 @@ struct LevelArgs {
 };
 cudaError_t launch_levelsync(int mode, const LevelArgs &a, int threads, cudaStream_t s);
 
-// Adjoint.  mode: 0 = grad_pos given, 1 = loss vs targets, 2 = IK step.
+// Adjoint.  mode: 0 = grad_pos given, 1 = loss vs targets, 2 = IK step, 3 =
+// IK step with the IK object's own Adam state.
 struct AdjointArgs {
   const TypeDev *types;
   const WorkItem *items;
@@ -196,6 +197,10 @@ struct AdjointArgs {
   const int32_t *eff_slot;       // [n_types][n_eff] view joint ids
   int n_eff;
   float *m, *v;
+  // mode 3 (IK with the object's own Adam state): m, v hold one row per
+  // view joint in view order, character c's rows from state_off[c]; in mode
+  // 2 they are the caller's [total][4] rows
+  const int64_t *state_off;
   float *q_mut;
   int *step;         // device step counter (read at start, incremented by the last CTA)
   float lr, beta1, beta2, eps;

@@ -611,9 +611,15 @@ struct anim_ik {
   WorkItem *d_items = nullptr;
   int n_items = 0;
   int *d_counters = nullptr;  // [0] queue, [1] step, [2] done
+  // the object's own Adam state (m rows, then v rows): one row per view
+  // joint of each character, character c's rows from d_state_off[c]
+  float *d_state = nullptr;
+  int64_t *d_state_off = nullptr;
+  int64_t state_rows = 0;
   LaunchCfg cfg{};
   ~anim_ik() {
-    for (void *p : {(void *)d_views, (void *)d_eff, (void *)d_items, (void *)d_counters})
+    for (void *p : {(void *)d_views, (void *)d_eff, (void *)d_items, (void *)d_counters, (void *)d_state,
+                    (void *)d_state_off})
       if (p) cudaFree(p);
   }
 };
@@ -1634,6 +1640,14 @@ int anim_ik_create(anim_ctx *ctx, const anim_plan *plan, int n_eff, const int32_
   CK(upload_vec(&K->d_items, items));
   CK(cudaMalloc(&K->d_counters, 4 * sizeof(int)));
   CK(cudaMemset(K->d_counters, 0, 4 * sizeof(int)));
+  std::vector<int64_t> state_off(plan->n_chars);
+  for (int64_t c = 0; c < plan->n_chars; ++c) {
+    state_off[c] = K->state_rows;
+    K->state_rows += K->views[plan->char_type[c]]->n;
+  }
+  CK(upload_vec(&K->d_state_off, state_off));
+  CK(cudaMalloc(&K->d_state, std::max<int64_t>(1, 2 * K->state_rows) * 16));
+  CK(cudaMemset(K->d_state, 0, std::max<int64_t>(1, 2 * K->state_rows) * 16));
   if (ctx->adj_ctas > 0)
     K->cfg = {kAdjSmallThreads, std::max(1, K->n_items), smem};
   else
@@ -1656,6 +1670,7 @@ int anim_ik_destroy(anim_ctx *ctx, anim_ik *ik) {
 int anim_ik_reset(anim_ctx *ctx, anim_ik *ik, void *stream) {
   if (!ctx || !ik || !ctx->iks.count(ik)) return ctx ? fail(ctx, ANIM_EINVAL, "unknown IK object") : ANIM_EINVAL;
   CK(cudaMemsetAsync(ik->d_counters, 0, 4 * sizeof(int), (cudaStream_t)stream));
+  CK(cudaMemsetAsync(ik->d_state, 0, std::max<int64_t>(1, 2 * ik->state_rows) * 16, (cudaStream_t)stream));
   return ANIM_OK;
 }
 
@@ -1664,8 +1679,9 @@ int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v,
   if (!ctx || !ik || !ctx->iks.count(ik)) return ctx ? fail(ctx, ANIM_EINVAL, "unknown IK object") : ANIM_EINVAL;
   const anim_plan *plan = ik->plan;
   if (plan->n_chars == 0) return ANIM_OK;
-  if (!d_q || !d_m || !d_v || !d_t || !d_targets) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
-  if (!aligned16(d_q) || !aligned16(d_m) || !aligned16(d_v))
+  if (!d_q || !d_t || !d_targets) return fail(ctx, ANIM_EINVAL, "NULL device pointer");
+  if (!d_m != !d_v) return fail(ctx, ANIM_EINVAL, "d_m and d_v must both be given or both be NULL");
+  if (!aligned16(d_q) || (d_m && (!aligned16(d_m) || !aligned16(d_v))))
     return fail(ctx, ANIM_EINVAL, "d_q, d_m, d_v must be 16-byte aligned");
   if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
     return fail(ctx, ANIM_EINVAL, "bad Adam hyper-parameters");
@@ -1684,8 +1700,14 @@ int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v,
   a.loss = d_loss;
   a.eff_slot = ik->d_eff;
   a.n_eff = ik->n_eff;
-  a.m = d_m;
-  a.v = d_v;
+  if (d_m) {
+    a.m = d_m;
+    a.v = d_v;
+  } else {  // the object's own state
+    a.m = ik->d_state;
+    a.v = ik->d_state + 4 * ik->state_rows;
+    a.state_off = ik->d_state_off;
+  }
   a.q_mut = d_q;
   a.step = ik->d_counters + 1;
   a.done = ik->d_counters + 2;
@@ -1693,7 +1715,7 @@ int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, float *d_v,
   a.beta1 = beta1;
   a.beta2 = beta2;
   a.eps = eps;
-  CK(launch_adjoint(2, a, ik->cfg, st));
+  CK(launch_adjoint(d_m ? 2 : 3, a, ik->cfg, st));
   return ANIM_OK;
 }
 
@@ -1874,15 +1896,15 @@ int anim_tune_ik(anim_ctx *ctx, anim_plan *plan, int n_eff, const int32_t *effec
     return apply_choice(ctx, plan, hit->second.seg_len, hit->second.ctas_per_sm, hit->second.joints_per_item,
                         hit->second.walk, hit->second.adj_ctas);
   // scratch state (tuning may allocate; steps never do): identity poses,
-  // zero moments, targets near the origin
+  // targets near the origin; the candidates' IK objects keep their own
+  // (zeroed) Adam state
   const int64_t N = plan->n_chars, J = plan->total;
-  float *d_q = nullptr, *d_m = nullptr, *d_v = nullptr, *d_t = nullptr, *d_tg = nullptr;
+  float *d_q = nullptr, *d_t = nullptr, *d_tg = nullptr;
   auto release = [&]() {
-    for (float *p : {d_q, d_m, d_v, d_t, d_tg})
+    for (float *p : {d_q, d_t, d_tg})
       if (p) cudaFree(p);
   };
-  bool ok = cudaMalloc(&d_q, J * 16) == cudaSuccess && cudaMalloc(&d_m, J * 16) == cudaSuccess &&
-            cudaMalloc(&d_v, J * 16) == cudaSuccess && cudaMalloc(&d_t, J * 12) == cudaSuccess &&
+  bool ok = cudaMalloc(&d_q, J * 16) == cudaSuccess && cudaMalloc(&d_t, J * 12) == cudaSuccess &&
             cudaMalloc(&d_tg, std::max<int64_t>(N * n_eff * 12, 16)) == cudaSuccess;
   if (!ok) {
     release();
@@ -1892,8 +1914,6 @@ int anim_tune_ik(anim_ctx *ctx, anim_plan *plan, int n_eff, const int32_t *effec
     std::vector<float> q(J * 4, 0.f), t(J * 3, 0.05f), tg(N * n_eff * 3, 0.1f);
     for (int64_t j = 0; j < J; ++j) q[4 * j + 3] = 1.f;
     cudaError_t e = cudaMemcpy(d_q, q.data(), J * 16, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(d_m, 0, J * 16);
-    if (e == cudaSuccess) e = cudaMemset(d_v, 0, J * 16);
     if (e == cudaSuccess) e = cudaMemcpy(d_t, t.data(), J * 12, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && N > 0) e = cudaMemcpy(d_tg, tg.data(), N * n_eff * 12, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -1910,7 +1930,7 @@ int anim_tune_ik(anim_ctx *ctx, anim_plan *plan, int n_eff, const int32_t *effec
     anim_ik *ik = nullptr;
     if (anim_ik_create(ctx, plan, n_eff, effectors, &ik) != ANIM_OK) return;  // a view does not fit
     auto step = [&]() {
-      return anim_ik_step(ctx, ik, d_q, d_m, d_v, d_t, d_tg, 1e-2f, 0.9f, 0.999f, 1e-8f, nullptr, nullptr);
+      return anim_ik_step(ctx, ik, d_q, nullptr, nullptr, d_t, d_tg, 1e-2f, 0.9f, 0.999f, 1e-8f, nullptr, nullptr);
     };
     bool good = anim_ik_reset(ctx, ik, nullptr) == ANIM_OK;
     for (int w = 0; w < 2 && good; ++w) good = step() == ANIM_OK;

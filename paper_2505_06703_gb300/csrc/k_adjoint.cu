@@ -106,7 +106,8 @@ __device__ void prefix_pairs(float4 *F, float4 *T, int n, float4 *wsF, float4 *w
 }
 
 // One work item: MODE 0 grad_pos given; MODE 1 loss sum |p - target|^2;
-// MODE 2 IK step (effector loss, adjoint, Adam update of q, m, v).  NT
+// MODE 2 IK step (effector loss, adjoint, Adam update of q, m, v), MODE 3
+// the same with the moments in the IK object's own state.  NT
 // threads run the passes (tid < NT); `step` is the 1-based Adam step.
 template <int MODE, int NT>
 __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf &b, float4 *sm, float4 *wsF,
@@ -142,7 +143,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       const float4 q = normalize4(__ldg(q4 + row));
       const float *tp = a.t + 3 * row;
       sts_qt(P + c * cs2, j, n, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
-      if (MODE != 2) {
+      if (MODE < 2) {
         const float *src = (MODE == 0 ? a.grad_pos : a.target) + 3 * row;
         PF[c * (n + 1) + j] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), 0.f);
       }
@@ -189,7 +190,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     }
   }
   pass_sync<NT>();
-  if (MODE == 2) {
+  if (MODE >= 2) {
     const int CE = C * a.n_eff;
     for (int idx = tid; idx < CE; idx += NT) {
       const int c = idx / a.n_eff, e = idx - c * a.n_eff;
@@ -213,7 +214,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
 
   // ---- per-joint gradients (and the Adam update in IK mode)
   float bc2s = 1.f, step_size = 0.f;
-  if (MODE == 2) {
+  if (MODE >= 2) {
     bc2s = sqrtf(1.f - powf(a.beta2, (float)step));
     step_size = a.lr / (1.f - powf(a.beta1, (float)step));
   }
@@ -243,14 +244,15 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     const float4 r = qmul(make_float4(tau.x, tau.y, tau.z, 0.f), u);
     const float k2 = 2.f * inv;
     const float4 dq = make_float4(k2 * r.x, k2 * r.y, k2 * r.z, k2 * r.w);
-    if (MODE != 2) {
+    if (MODE < 2) {
       reinterpret_cast<float4 *>(a.grad_q)[row] = dq;
       a.grad_t[3 * row] = dt.x;
       a.grad_t[3 * row + 1] = dt.y;
       a.grad_t[3 * row + 2] = dt.z;
     } else {
-      float4 m = reinterpret_cast<float4 *>(a.m)[row];
-      float4 v = reinterpret_cast<float4 *>(a.v)[row];
+      const long long srow = MODE == 3 ? b.voff[c] + j : row;  // the Adam state's row
+      float4 m = reinterpret_cast<float4 *>(a.m)[srow];
+      float4 v = reinterpret_cast<float4 *>(a.v)[srow];
       float4 qn = q;
       const float b1 = a.beta1, b2 = a.beta2;
       const float gq[4] = {dq.x, dq.y, dq.z, dq.w};
@@ -262,8 +264,8 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
         const float denom = sqrtf(vv[k]) / bc2s + a.eps;
         qq[k] = qq[k] - step_size * (mm[k] / denom);
       }
-      reinterpret_cast<float4 *>(a.m)[row] = m;
-      reinterpret_cast<float4 *>(a.v)[row] = v;
+      reinterpret_cast<float4 *>(a.m)[srow] = m;
+      reinterpret_cast<float4 *>(a.v)[srow] = v;
       reinterpret_cast<float4 *>(a.q_mut)[row] = qn;
     }
   }
@@ -284,18 +286,20 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_adjoint(const AdjointArgs
   // wave's rows are only prefetched into L2 before that: the work items and
   // views are plan data)
   asm volatile("griddepcontrol.launch_dependents;");
-  const RowPrefetch pf = MODE == 2 ? RowPrefetch{{a.q, a.t, a.m, a.v}, {4, 3, 4, 4}, 0}
-                                   : RowPrefetch{{a.q, a.t, MODE == 0 ? a.grad_pos : a.target, nullptr}, {4, 3, 3, 0}, 1};
+  const RowPrefetch pf =
+      MODE == 3   ? RowPrefetch{{a.q, a.t, nullptr, nullptr}, {4, 3, 0, 0}, 0}
+      : MODE == 2 ? RowPrefetch{{a.q, a.t, a.m, a.v}, {4, 3, 4, 4}, 0}
+                : RowPrefetch{{a.q, a.t, MODE == 0 ? a.grad_pos : a.target, nullptr}, {4, 3, 3, 0}, 1};
   if (tid >= kComputeThreads)
     prefetch_first_wave(bufs[1], a.n_items, a.items, a.types, a.item_chars, a.row_off, pf);
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (tid >= kComputeThreads) {
     producer_loop<1>(bufs, a.queue_head, a.n_items, a.items, a.types, a.item_chars, a.row_off, nullptr, nullptr,
-                     a.status, nullptr, LayerIn{nullptr, nullptr}, pf);
+                     a.status, MODE == 3 ? a.state_off : nullptr, LayerIn{nullptr, nullptr}, pf);
     return;
   }
-  const int step = (MODE == 2) ? *a.step + 1 : 0;  // 1-based Adam step of this launch
+  const int step = (MODE >= 2) ? *a.step + 1 : 0;  // 1-based Adam step of this launch
   int cur = 0;
   handoff_sync();
   for (;;) {
@@ -310,7 +314,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_adjoint(const AdjointArgs
   if (tid == 0) {  // the last CTA resets the queue (and advances the IK step)
     __threadfence();
     if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
-      if (MODE == 2) *a.step = *a.step + 1;
+      if (MODE >= 2) *a.step = *a.step + 1;
       *a.queue_head = 0;
       *a.done = 0;
       __threadfence();
@@ -336,10 +340,11 @@ __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const Adj
   asm volatile("griddepcontrol.launch_dependents;");
   if (tid < 32) {
     const WorkItem wi = a.items[blockIdx.x];
-    stage_item<1>(b, (int)blockIdx.x, wi, a.types, a.item_chars, a.row_off, nullptr, nullptr, a.status);
+    stage_item<1>(b, (int)blockIdx.x, wi, a.types, a.item_chars, a.row_off, nullptr, nullptr, a.status,
+                  MODE == 3 ? a.state_off : nullptr);
   }
   __syncthreads();
-  if (MODE != 2) {
+  if (MODE < 2) {
     // warm L2 with the item's rows of poses and loss inputs while the
     // preceding grid finishes: a prefetch loads nothing into the kernel, and
     // L2 is coherent, so the loads after the wait see that grid's writes.
@@ -360,9 +365,9 @@ __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const Adj
   // poses, targets, the IK step counter and the outputs may belong to the
   // preceding kernel in the stream: wait for it to complete
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  const int step = (MODE == 2) ? *a.step + 1 : 0;
+  const int step = (MODE >= 2) ? *a.step + 1 : 0;
   adjoint_item<MODE, kAdjSmallThreads>(a, b, sm, wsF, wsT, tid, step);
-  if (MODE == 2 && tid == 0) {  // the last CTA advances the IK step
+  if (MODE >= 2 && tid == 0) {  // the last CTA advances the IK step
     __threadfence();
     if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
       *a.step = *a.step + 1;
@@ -425,7 +430,8 @@ static cudaError_t launch_adj_persistent(const AdjointArgs &a, const LaunchCfg &
 cudaError_t launch_adjoint(int mode, const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   if (mode == 0) return launch_adj_t<0>(a, cfg, st);
   if (mode == 1) return launch_adj_t<1>(a, cfg, st);
-  return launch_adj_t<2>(a, cfg, st);
+  if (mode == 2) return launch_adj_t<2>(a, cfg, st);
+  return launch_adj_t<3>(a, cfg, st);
 }
 
 }  // namespace anim

@@ -495,6 +495,38 @@ def test_config5_ik_full_second_step(torch, sched):
     assert np.abs(q2[rows] - p_ref)[clear].max() < 1e-2 * w["lr"]
 
 
+@pytest.mark.parametrize("sched", [[4, 3, 1024, 1, 0], [8, 2, 4096, 1, 0], [16, 2, 512, 1, 4]])
+def test_ik_own_adam_state_matches_caller_state(torch, sched):
+    """Five IK steps on all of config 5 with Adam's moments in the caller's
+    [total][4] rows and, after a reset, in the IK object's own compact state
+    (the same arithmetic on other rows): bit-identical poses and losses, also
+    for a second run after another reset; persistent (2- and 3-CTA/SM builds)
+    and one-item kernels."""
+    w = synth.config5()
+    ct, eff = w["char_type"], w["effectors"]
+    ctx, plan, t, targets = _ik_setup(torch, w)
+    ctx.set_schedule(plan, sched)
+    ik = ctx.ik(plan, eff)
+    q0 = _gpu.cuda(w["q0"])
+
+    def run(own):
+        q = q0.clone()
+        m, v = (None, None) if own else (torch.zeros_like(q), torch.zeros_like(q))
+        loss = torch.zeros(len(ct), device="cuda")
+        ik.reset()
+        for _ in range(5):
+            ik.step(q, m, v, t, targets, lr=w["lr"], betas=w["betas"], eps=w["eps"], loss=loss)
+        torch.cuda.synchronize()
+        return q, loss
+
+    q_c, l_c = run(False)
+    q_o, l_o = run(True)
+    q_o2, _ = run(True)
+    assert torch.equal(q_c, q_o) and torch.equal(l_c, l_o)
+    assert torch.equal(q_o, q_o2)
+    assert not torch.equal(q_c, q0)
+
+
 # ------------------------------------------------------------------ edge cases
 def _edge_types(rng):
     return [synth.make_type(np.array([-1], np.int32), rng, with_clips=True),               # one joint
