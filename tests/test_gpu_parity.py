@@ -525,6 +525,9 @@ def test_ik_own_adam_state_matches_caller_state(torch, sched):
     assert torch.equal(q_c, q_o) and torch.equal(l_c, l_o)
     assert torch.equal(q_o, q_o2)
     assert not torch.equal(q_c, q0)
+    import paper_2505_06703_gb300 as pk
+    with pytest.raises(pk.AnimError, match="EINVAL"):  # one moment array alone
+        ik.step(q0.clone(), torch.zeros_like(q0), None, t, targets)
 
 
 # ------------------------------------------------------------------ edge cases
