@@ -10,7 +10,10 @@ asks to keep clip blending, Sec. 2, without a method, so this is a reading).
   * scaling every weight changes nothing;
   * an additive layer of weight 0, or of identity keys, leaves the pose; on
     an identity base, an additive rotation about one axis by b gives the
-    angle a * b.
+    angle a * b;
+  * for general keys, weights and an additive layer, the whole layered
+    sample equals the same steps composed from scipy's Slerp (a library
+    routine).
 """
 import numpy as np
 import pytest
@@ -111,3 +114,62 @@ def test_additive_layer_special_cases():
     q, _ = oracle.sample_layers(base, 30.0, 0.5, [1.0], add_keys=za, add_w=0.3)
     np.testing.assert_allclose(q[:, 2], np.sin(0.3 * b / 2), atol=1e-7)
     np.testing.assert_allclose(q[:, 3], np.cos(0.3 * b / 2), atol=1e-7)
+
+
+def test_general_layers_match_scipy_composition():
+    """General keys (random axes and quaternion signs), weights and an
+    additive layer: each clip is scipy's Slerp of its bracketing keys at the
+    key fraction, the clips blend by incremental scipy Slerp (weight w_i / W
+    after W += w_i), translations by weighted mean, and the additive layer
+    multiplies on the right by scipy's Slerp from identity to its sampled
+    rotation at weight a (translation + a * t_a)."""
+    from scipy.spatial.transform import Rotation, Slerp
+    rng = np.random.default_rng(17)
+    n, nk, nc = 6, 30, 4
+    keys = np.zeros((nc, nk, n, 8), np.float32)
+    add = np.zeros((nk, n, 8), np.float32)
+    for k in range(nk):
+        for c in range(nc):
+            keys[c, k, :, :4] = synth.random_unit_quats(rng, n, 70.0)
+            keys[c, k, :, 4:7] = rng.uniform(-1, 1, (n, 3))
+        add[k, :, :4] = synth.random_unit_quats(rng, n, 50.0)
+        add[k, :, 4:7] = rng.uniform(-0.2, 0.2, (n, 3))
+    keys[..., :4][rng.random(keys.shape[:3]) < 0.5] *= -1.0
+    add[..., :4][rng.random(add.shape[:2]) < 0.5] *= -1.0
+
+    def sample(kk, k0, k1, al, j):
+        r = Slerp([0, 1], Rotation.from_quat([kk[k0, j, :4].astype(np.float64), kk[k1, j, :4].astype(np.float64)]))
+        t = (1 - al) * kk[k0, j, 4:7].astype(np.float64) + al * kk[k1, j, 4:7].astype(np.float64)
+        return r([al]), t
+
+    for trial in range(12):
+        tm = float(np.float32(rng.uniform(-1, 2)))
+        wts = rng.uniform(0, 1, nc).astype(np.float32)
+        if trial % 3 == 0:
+            wts[rng.integers(0, nc)] = 0.0  # a zero weight inside the sequence
+        aw = float(np.float32(rng.uniform(0, 1)))
+        u = np.float32(tm) * np.float32(30.0)
+        k0 = int(np.floor(u)) % nk
+        k1 = (k0 + 1) % nk
+        al = float(u - np.floor(u))
+        q, t = oracle.sample_layers(keys, 30.0, tm, wts, add_keys=add, add_w=aw)
+        wd = wts.astype(np.float64)
+        for j in range(n):
+            rot, W, tsum = None, 0.0, np.zeros(3)
+            t0 = None
+            for c in range(nc):
+                rc, tc = sample(keys[c], k0, k1, al, j)
+                if c == 0:
+                    rot, t0 = rc, tc
+                elif W + wd[c] > 0:
+                    rot = Slerp([0, 1], Rotation.concatenate([rot, rc]))([wd[c] / (W + wd[c])])
+                W += wd[c]
+                tsum += wd[c] * tc
+            tref = tsum / W if W > 0 else t0
+            ra, ta = sample(add, k0, k1, al, j)
+            rref = rot * Slerp([0, 1], Rotation.concatenate([Rotation.identity(), ra]))([aw])
+            tref = tref + aw * ta
+            # float32 keys as stored (norms off 1 by rounding) against scipy's
+            # normalized inputs: agreement to about 1e-7
+            np.testing.assert_allclose(Rotation.from_quat(q[j]).as_matrix(), rref.as_matrix()[0], atol=1e-7)
+            np.testing.assert_allclose(t[j], tref, atol=1e-12)
