@@ -13,6 +13,8 @@ tests check it against things that are not the oracle:
 """
 import itertools
 
+import os
+
 import numpy as np
 import pytest
 
@@ -96,6 +98,19 @@ def _schedule_trees():
     return trees
 
 
+def _paper_counts():
+    """The paper's stated per-thread product and barrier counts
+    (tests/golden/paper_schedule_counts.txt, with their passages)."""
+    out = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_schedule_counts.txt")
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, base, per64, barriers = line.split()[:4]
+                out[name] = (base, int(per64), barriers)
+    return out
+
+
 @pytest.mark.parametrize("k", range(5))
 def test_paper_schedules_equal_oracle(k):
     parents = _schedule_trees()[k]
@@ -109,18 +124,22 @@ def test_paper_schedules_equal_oracle(k):
     np.testing.assert_allclose(m1, ref, atol=1e-10)
     assert (p1 == ps.depths(parents) - 1).all()  # O(depth) per thread (Sec. 2)
 
+    counts = _paper_counts()
     m2, p2, rounds = ps.alg2_jump(parents, L)
     np.testing.assert_allclose(m2, ref, atol=1e-10)
-    assert rounds == int(np.ceil(np.log2(D)))  # log2 n rounds/barriers (Sec. 3.1)
+    assert counts["alg2"] == ("log2", 0, "log2")
+    assert rounds == int(np.ceil(np.log2(D)))  # log2 rounds and barriers (Sec. 3.1)
     assert p2.max() <= rounds
 
     m3, p3, b3 = ps.alg3_blocks(parents, L)
     np.testing.assert_allclose(m3, ref, atol=1e-10)
-    assert b3 == 6 and p3.max() <= 6 + int(np.ceil(n / 64))  # 6 + n/64 (Sec. 3.2.1)
+    base, per64, bars = counts["alg3"]  # 6 + n/64, 6 rounds (Sec. 3.2.1)
+    assert b3 == int(bars) and p3.max() <= int(base) + per64 * int(np.ceil(n / 64))
 
     m4, p4, b4 = ps.alg4_compress(parents, L)
     np.testing.assert_allclose(m4, ref, atol=1e-10)
-    assert b4 == 2 and p4.max() <= 14 + int(np.ceil(n / 64))  # 14 + n/64, 2 barriers (Sec. 3.2.2)
+    base, per64, bars = counts["alg4"]  # 14 + n/64, 2 barriers (Sec. 3.2.2)
+    assert b4 == int(bars) and p4.max() <= int(base) + per64 * int(np.ceil(n / 64))
 
 
 def test_same_axis_chain_closed_form():
