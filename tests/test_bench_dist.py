@@ -91,3 +91,16 @@ def test_oracle_on_all_cores_helper():
     assert n == 2 and dt > 0
     assert bench.host_cores() >= 1
     assert bench.cpu_model()
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference: the oracle on the host cores prints the
+    contract's line (impl, metric, value, unit, cpu_baseline, e2e)."""
+    import argparse
+    import bench
+    r = bench.run_reference(argparse.Namespace(steps=2, warmup=1))
+    assert r["impl"] == "reference" and r["metric"] == bench.METRIC and r["unit"] == bench.UNIT
+    assert r["value"] > 0 and r["higher_is_better"] is True and r["steps"] == 2 and r["warmup"] == 1
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
+    assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
