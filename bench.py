@@ -46,6 +46,8 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "joint transforms/s fwd and fwd+bwd on 1 GB300, % of HBM roofline, vs plain kernel"
+# The frame both arms time, named the same way in both JSON lines.
+WORKLOAD = "frame: 4,096 x 512-joint biped (depth 70) + 1 x 1,024-joint dragon chain, 2 clips x 30 keys"
 UNIT = "joints/s"
 L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes per launch of the persistent frame kernel from one ncu capture
@@ -367,9 +369,8 @@ def run_ours(args) -> dict:
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
               "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
               "dtype": "f32", "data": "synthetic (seeded skeletons, clips, times and blend weights)",
-              "config": {"workload": "frame: 4,096 chars x 512-joint biped+8x59 chains (depth 70) + 1 x 1,024-joint "
-                                     "dragon chain; 2 clips x 30 keys @30 Hz; slerp keys, slerp 2-clip blend, "
-                                     "hierarchy scan, bind",
+              "config": {"workload": WORKLOAD,
+                         "steps_of_the_frame": "slerp keys, slerp 2-clip blend, hierarchy scan, bind",
                          "joints_per_step_per_gpu": joints, "characters_per_gpu": n_chars,
                          "l2": f"output rotated over {n_out} buffers ({n_out * out_bytes / 1e6:.0f} MB > 129 MB L2)",
                          "timing": "CUDA graphs (work queue + persistent kernel), CUDA events",
@@ -928,7 +929,7 @@ def run_reference(args) -> dict | None:
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "frame: 4,096 x 512-joint + 1,024-joint dragon"},
+            "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "cpu": cpu_model(),
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -954,6 +955,30 @@ def run_only(args) -> dict:
         import torch.distributed as dist
         dist.destroy_process_group()
     return {"only": args.only, "n_gpus": world, "result": res}
+
+
+def summary(r: dict) -> dict:
+    """The headline figures of every workload in one flat object: ms per step
+    and the fraction of the measured HBM peak (frame kernel, fwd+bwd, mixed
+    frame, IK step), the plain kernel's time and the fused frame's speedup
+    over it, and the IK's agreement with the FP64 oracle run."""
+    out = {"frame_ms": r.get("ms_per_step"), "frame_kernel_frac": r.get("roofline", {}).get("frac")}
+    for key, name in (("fwd_bwd", "fwd_bwd"), ("frame_mixed", "mixed"), ("ik", "ik")):
+        x = r.get(key)
+        if isinstance(x, dict):
+            out[f"{name}_ms"] = x.get("ms_per_step")
+            out[f"{name}_frac"] = x.get("roofline", {}).get("frac")
+    p = r.get("plain")
+    if isinstance(p, dict):
+        out["plain_ms"] = p.get("ms_per_step")
+        out["fused_vs_plain"] = p.get("speedup_fused_vs_plain")
+    ik = r.get("ik")
+    if isinstance(ik, dict) and isinstance(ik.get("vs_oracle"), dict):
+        v = ik["vs_oracle"]
+        out["ik_max_dev_from_oracle"] = v.get("max_abs_effector_diff")
+        out["ik_final_err_gpu"] = v.get("final_mean_gpu")
+        out["ik_final_err_oracle"] = v.get("final_mean_oracle")
+    return {k: (round(v, 6) if isinstance(v, float) else v) for k, v in out.items()}
 
 
 def main():
@@ -997,6 +1022,7 @@ def main():
         if world == 1 and not args.no_cpu:
             r["cpu_baseline"] = cpu_baseline()
         add_nominal_fractions(r)
+        r["summary"] = summary(r)  # last, so that the end of the line carries it
         print(json.dumps(r))
 
 

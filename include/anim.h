@@ -387,16 +387,25 @@ ANIM_API int anim_analyze_skeleton(int n, const int32_t *parents, int seg_len, i
  *                         [n_chars*n_joints][3] local poses;
  *   d_inv_bind          : device [n_joints][12] inverse bind poses;
  *   d_skin              : device [n_chars*n_joints][12], written.
- * d_q, d_inv_bind and d_skin must be 16-byte aligned.  Returns ANIM_EINVAL
- * (NULL pointer, bad parent, misalignment), ANIM_EUNSUPPORTED (a size beyond
- * the limits above) or ANIM_ECUDA; there is no message string.  The first call
- * on a device looks up the device address of the static array
+ * d_q, d_inv_bind and d_skin must be 16-byte aligned.  Besides the joint
+ * count, the skeleton's shape is limited by shared memory: one character's
+ * work item takes 16 * (3 n + 1 + 6 nseg) bytes plus its tables, nseg the
+ * number of segments (natural chains, parent[i+1] == i, cut into pieces of at
+ * most 16 joints), and must fit one CTA's opt-in shared memory (about 213 KB
+ * here): a 2,048-joint chain fits, a 2,048-joint star (nseg about n) does not.
+ * Returns ANIM_EINVAL (NULL pointer, bad parent, misalignment),
+ * ANIM_EUNSUPPORTED (a size beyond the limits above, or `stream` is being
+ * captured into a CUDA graph) or ANIM_ECUDA; there is no message string.
+ * n_chars == 0 returns ANIM_OK and touches nothing.  The first call on a
+ * device looks up the device address of the static array
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Each call writes the tables into the array
- * with an asynchronous copy on `stream` and launches the kernel after it:
- * every call shares the one array, so calls whose work overlaps on the GPU
- * (other streams, other host threads) race and must be serialized by the
- * caller. */
+ * with an asynchronous copy from a host staging buffer of the calling thread
+ * on `stream` and launches the kernel after it, which is why a capturing
+ * stream is refused: the recorded copy would replay the buffer's contents at
+ * replay time.  Every call shares the one array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller. */
 ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *parents, int64_t n_chars, const float *d_q,
                                         const float *d_t, const float *d_inv_bind, float *d_skin, void *stream);
 

@@ -15,6 +15,7 @@
 #include "anim_internal.h"
 #include "dev_math.cuh"
 #include "scan_core.cuh"
+#include "smem_limit.h"
 
 namespace anim {
 
@@ -383,13 +384,9 @@ static cudaError_t launch_adj_persistent(const AdjointArgs &a, const LaunchCfg &
 template <int MODE>
 static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   if (cfg.threads == kAdjSmallThreads) {
-    static size_t set_small = 0;
-    if (cfg.smem > set_small) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k_adjoint_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-      if (e != cudaSuccess) return e;
-      set_small = cfg.smem;
-    }
+    static SmemLimit lim_small;
+    cudaError_t e = ensure_smem_limit((const void *)k_adjoint_small<MODE>, lim_small, cfg.smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)a.n_items);
     lc.blockDim = dim3((unsigned)kAdjSmallThreads);
@@ -407,13 +404,9 @@ static cudaError_t launch_adj_t(const AdjointArgs &a, const LaunchCfg &cfg, cuda
 
 template <int MODE, int MINB>
 static cudaError_t launch_adj_persistent(const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  static size_t set_smem = 0;
-  if (cfg.smem > set_smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_adjoint<MODE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-    if (e != cudaSuccess) return e;
-    set_smem = cfg.smem;
-  }
+  static SmemLimit lim;
+  cudaError_t e = ensure_smem_limit((const void *)k_adjoint<MODE, MINB>, lim, cfg.smem);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)cfg.ctas);
   lc.blockDim = dim3((unsigned)cfg.threads);

@@ -13,6 +13,7 @@
 
 #include "anim_internal.h"
 #include "dev_math.cuh"
+#include "smem_limit.h"
 
 namespace anim {
 
@@ -106,13 +107,10 @@ __global__ void __launch_bounds__(1024) k_levelsync(const LevelArgs a) {
 cudaError_t launch_levelsync(int mode, const LevelArgs &a, int threads, cudaStream_t st) {
   if (a.n_chars == 0) return cudaSuccess;
   const size_t smem = (size_t)a.type.n * 48;
-  static size_t set_smem[2] = {0, 0};
-  if (smem > set_smem[mode]) {
-    cudaError_t e = cudaFuncSetAttribute(mode == 0 ? k_levelsync<0> : k_levelsync<1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    set_smem[mode] = smem;
-  }
+  static SmemLimit lim[2];
+  cudaError_t e =
+      ensure_smem_limit(mode == 0 ? (const void *)k_levelsync<0> : (const void *)k_levelsync<1>, lim[mode], smem);
+  if (e != cudaSuccess) return e;
   if (mode == 0)
     k_levelsync<0><<<a.n_chars, threads, smem, st>>>(a);
   else

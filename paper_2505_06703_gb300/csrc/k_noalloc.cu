@@ -12,6 +12,7 @@
 #include "anim_internal.h"
 #include "dev_math.cuh"
 #include "scan_core.cuh"
+#include "smem_limit.h"
 
 namespace anim {
 
@@ -171,6 +172,16 @@ extern "C" ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *
   for (int i = 0; i < n_joints; ++i)
     if (parents[i] < -1 || parents[i] >= i) return set_msg(ANIM_EINVAL, "parents[i] must be in [-1, i-1]");
   if (n_chars == 0) return ANIM_OK;
+  // The tables below reach the device by a copy from this thread's host
+  // staging buffer, which the next call overwrites: a graph node recorded
+  // from that copy would replay whatever skeleton was staged last.  So a
+  // stream that is capturing is refused before anything is enqueued.
+  {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (ce != cudaSuccess) return set_msg(ANIM_ECUDA, cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone) return set_msg(ANIM_EUNSUPPORTED, "stream is capturing");
+  }
 
   // ---- once per device: the device address of the scratch array
   int dev = 0;
@@ -244,12 +255,9 @@ extern "C" ANIM_API int anim_forward_local_noalloc(int n_joints, const int32_t *
   while (C > 1 && scan_item_bytes(n_joints, nseg, C) > budget) --C;
   const size_t smem = scan_item_bytes(n_joints, nseg, C);
   if (smem > (size_t)optin - kStaticSmemAllowance) return set_msg(ANIM_EUNSUPPORTED, "skeleton does not fit in shared memory");
-  static size_t set_smem = 0;
-  if (smem > set_smem) {
-    e = cudaFuncSetAttribute(k_scan_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return set_msg(ANIM_ECUDA, cudaGetErrorString(e));
-    set_smem = smem;
-  }
+  static SmemLimit lim;
+  e = ensure_smem_limit((const void *)k_scan_noalloc, lim, smem);
+  if (e != cudaSuccess) return set_msg(ANIM_ECUDA, cudaGetErrorString(e));
   cudaStream_t st = (cudaStream_t)stream;
   e = cudaMemcpyAsync(scratch, h, kScratchUsed, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return set_msg(ANIM_ECUDA, cudaGetErrorString(e));

@@ -25,6 +25,7 @@
 
 #include "anim_internal.h"
 #include "dev_math.cuh"
+#include "smem_limit.h"
 
 namespace anim {
 
@@ -188,12 +189,9 @@ __global__ void k_paper(const PaperArgs a) {
 size_t paper_smem_bytes(int n) { return 3ull * 48ull * n + 4ull * n + 16; }
 
 cudaError_t launch_paper(const PaperArgs &a, int n_chars, int threads, size_t smem, cudaStream_t st) {
-  static size_t set_smem = 48 * 1024;
-  if (smem > set_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_paper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    set_smem = smem;
-  }
+  static SmemLimit lim;
+  cudaError_t e = ensure_smem_limit((const void *)k_paper, lim, smem, 48 * 1024);
+  if (e != cudaSuccess) return e;
   k_paper<<<n_chars, threads, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -5,6 +5,7 @@
 #include "anim_internal.h"
 #include "dev_math.cuh"
 #include "scan_core.cuh"
+#include "smem_limit.h"
 
 #define ANIM_MAX_KEYS_DEV 1024  // keys per clip (ANIM_MAX_KEYS in the ABI)
 
@@ -185,12 +186,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
 template <int MINB>
 static cudaError_t launch_scan_t(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
   auto k = k_scan<MINB>;
-  static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
-  if (cfg.smem > set_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-    if (e != cudaSuccess) return e;
-    set_smem = cfg.smem;
-  }
+  static SmemLimit lim;
+  cudaError_t e = ensure_smem_limit((const void *)k, lim, cfg.smem);
+  if (e != cudaSuccess) return e;
   k<<<cfg.ctas, cfg.threads, cfg.smem, st>>>(a);
   return cudaGetLastError();
 }

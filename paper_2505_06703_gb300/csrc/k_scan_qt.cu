@@ -19,6 +19,7 @@
 #include "anim_internal.h"
 #include "dev_math.cuh"
 #include "scan_core.cuh"
+#include "smem_limit.h"
 
 namespace anim {
 
@@ -160,13 +161,9 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
 
 template <int MODE, int MINB>
 static cudaError_t launch_qt(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st) {
-  static size_t set_smem = 0;  // attribute calls stay out of graph captures after the first launch
-  if (cfg.smem > set_smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_scan_qt<MODE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-    if (e != cudaSuccess) return e;
-    set_smem = cfg.smem;
-  }
+  static SmemLimit lim;
+  cudaError_t e = ensure_smem_limit((const void *)k_scan_qt<MODE, MINB>, lim, cfg.smem);
+  if (e != cudaSuccess) return e;
   // programmatic stream serialization: the CTAs become resident while the
   // preceding kernel runs and wait in griddepcontrol.wait
   cudaLaunchConfig_t lc = {};

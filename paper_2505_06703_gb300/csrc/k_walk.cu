@@ -26,6 +26,7 @@
 
 #include "anim_internal.h"
 #include "dev_math.cuh"
+#include "smem_limit.h"
 
 namespace anim {
 
@@ -227,12 +228,9 @@ int walk_blocks_per_sm(size_t smem) {
 }
 
 cudaError_t launch_walk(const WalkArgs &a, int ctas, size_t smem, cudaStream_t st) {
-  static size_t set_smem = 48 * 1024;  // attribute calls stay out of graph captures after the first launch
-  if (smem > set_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    set_smem = smem;
-  }
+  static SmemLimit lim;
+  cudaError_t e = ensure_smem_limit((const void *)k_walk, lim, smem, 48 * 1024);
+  if (e != cudaSuccess) return e;
   k_walk<<<ctas, 32, smem, st>>>(a);
   return cudaGetLastError();
 }
