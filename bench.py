@@ -59,7 +59,7 @@ NCU_TRAFFIC = {"4165125c1ebdc126": 1353984 + 40237056}
 
 # ------------------------------------------------------------------ helpers
 # The sources the persistent frame kernel is compiled and launched from.
-FRAME_KERNEL_SOURCES = ("anim_internal.h", "dev_math.cuh", "scan_core.cuh", "k_scan_qt.cu", "host.cu")
+FRAME_KERNEL_SOURCES = ("anim_internal.h", "dev_math.cuh", "scan_core.cuh", "k_scan_qt.cu", "k_walk.cu", "host.cu")
 
 
 def kernel_source_hash() -> str:
@@ -361,7 +361,8 @@ def run_ours(args) -> dict:
     achieved = alg / (k_ms / 1e3) / 1e9
     tr = NCU_TRAFFIC.get(kernel_source_hash())
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": tr, "kernel": "k_scan_qt<0> (persistent frame)",
+                "frac": round(achieved / peak, 4), "traffic": tr,
+                "kernel": "k_walk (chain walk in skin space)" if schedule[3] else "k_scan_qt<0> (persistent frame)",
                 "kernel_ms": round(k_ms, 5), "algorithmic_bytes": alg, "peak_source": peak_src,
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "touched_bytes": frame_touched_bytes(w)}

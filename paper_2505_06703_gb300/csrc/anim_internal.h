@@ -46,17 +46,22 @@ struct TypeDev {
   const float4 *mesh;
   const int32_t *faces;      // [n_faces][3] vertex indices (raster)
   // Chain-walk frame kernel (k_walk): a static lane schedule of wk_S steps
-  // for wk_P lanes per character; entry [s][slot] names the joint lane `slot`
-  // composes at step s (kWInvalid: idle).  wk_mode 1: natural chains walked
-  // parent-first, branch-point matrices passed through shared memory;
-  // wk_mode 2: a pure chain cut into wk_P pieces joined by a warp-shuffle
-  // scan; 0: the type runs on the segmented CTA kernels only.
+  // for wk_P lanes per character, staged in chunks of wk_K steps (the table
+  // is padded with idle entries to whole chunks); entry [s][slot] names the
+  // joint lane `slot` composes at step s (kWInvalid: idle).  wk_mode 1: natural chains walked parent-first,
+  // branch-point matrices passed through shared memory; wk_mode 2: a pure
+  // chain cut into wk_P pieces joined by a warp-shuffle scan; 0: the type
+  // runs on the segmented CTA kernels only.
   int wk_mode, wk_P, wk_logP, wk_S;
   int wk_nbs;                // branch-point slots per character (mode 1)
-  int pad2;
+  int wk_K;
   const uint32_t *wk_tab;    // [wk_S][wk_P]
-  const float4 *wk_keys;     // [clip][key][wk_S][4][wk_P] key-pair records in schedule order
-  const float4 *wk_bind;     // [wk_S][3][wk_P] inverse-bind rows in schedule order
+  // key-pair records in schedule order with the inverse binds folded in
+  // (skin-space walk), clips 0 and 1: [clip][key][wk_S][4][wk_P] float4 =
+  // (q0', q_perp', (t0', theta), (t1' - t0', 0)); nullptr: the type does not
+  // run on the walk kernel (no clips yet, or inverse binds that are not rigid)
+  const float4 *wk_keys;
+  const float4 *wk_u;        // [wk_S][wk_P] (u = R_B^T t_B of the slot's joint, 0)
 };
 // Chain-walk schedule entries: joint | flags | load slot | store slot; bit 31
 // set marks an idle entry.
@@ -68,11 +73,15 @@ constexpr int kWLoadShift = 15;             // bits 15-22
 constexpr int kWStoreShift = 23;            // bits 23-30
 constexpr uint32_t kWRootSlot = 255;        // load slot of a chain that starts at a root
 constexpr int kWalkMaxSteps = 160;          // longest schedule the walk kernel takes (latency bound)
-constexpr int kWalkMaxSmem = 12 * 1024;     // shared memory of one walk CTA (branch slots)
+constexpr int kWalkMaxSmem = 32 * 1024;     // shared memory of one walk CTA (staging + branch slots)
 // Static shared memory the persistent kernels may use besides the dynamic
 // item buffers (two staged work items, scan scratch); the host subtracts it
 // from the per-CTA budget.
 constexpr int kStaticSmemAllowance = 14 * 1024;
+
+// Device status word bits (ANIM_STATUS_* in the ABI).
+constexpr int kStatusNonfiniteTime = 1;
+constexpr int kStatusTimeout = 4;
 
 constexpr uint32_t kJStart = 1u << 16;  // joint opens its segment
 constexpr uint32_t kJLink = 1u << 17;   // the joint's segment hangs from a parent joint
@@ -134,17 +143,20 @@ struct ScanArgs {
 cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 // Frame work queue.  The plan cuts the characters of each type (types in
-// cost order) into ranges of at most kRangeChars, each owning a region of
+// cost order) into ranges of at most kRangeChars (kRangeCharsMax for the
+// walk kernel's types, whose items hold 32 / P characters: larger ranges
+// leave fewer part-filled items per key bin), each owning a region of
 // item slots large enough for any key distribution.  One CTA per range sorts
 // its characters by key index k0 (counting sort in shared memory) and writes
 // work items of at most cap[type] characters sharing (type, k0) into its
 // region, then empty items (count 0) into the rest of the region.
 constexpr int kRangeChars = 256;
+constexpr int kRangeCharsMax = 1024;
 constexpr int kMaxRanges = 4096;  // so at most ~900,000 characters per plan
 struct RangeDev {
   int32_t type;
   int32_t start;   // first index into the type-grouped character list
-  int32_t count;   // characters (<= kRangeChars)
+  int32_t count;   // characters (<= kRangeCharsMax)
   int32_t region;  // first item slot of the range
 };
 struct BucketArgs {
@@ -207,29 +219,23 @@ struct AdjointArgs {
 };
 cudaError_t launch_adjoint(int mode, const AdjointArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
-// Chain-walk frame kernel: one-warp CTAs, each pulling work items (at most
-// 32 / wk_P characters of one walk type sharing the key index k0) from the
-// queue and composing them lane-parallel along the type's schedule.
+// Chain-walk frame kernel: one-warp CTAs, CTA i running work-queue slot i
+// (at most 32 / wk_P characters of one walk type sharing the key index k0;
+// empty slots exit), composing them lane-parallel along the type's schedule.
 struct WalkArgs {
   const TypeDev *types;
   const WorkItem *items;
-  int n_items;
+  int n_items;                 // slots (the grid)
   int nbs_max;                 // branch-point slot capacity per character
   const int32_t *item_chars;
   const int64_t *row_off;
-  int *queue_head;             // 0 at launch; reset by the last CTA
-  int *done;
   int *status;
   const float *time, *blend_w;
   float *skin;
 };
 size_t walk_smem_bytes(int chars_per_item, int nbs);
-cudaError_t launch_walk(const WalkArgs &a, int ctas, size_t smem, cudaStream_t s);
+cudaError_t launch_walk(const WalkArgs &a, size_t smem, cudaStream_t s);
 int walk_blocks_per_sm(size_t smem);  // resident one-warp CTAs per SM at this shared-memory size
-// Fill a type's schedule-ordered key records and inverse-bind rows from its
-// key table ([clip][key][n][2] float4) and inverse binds ([n][3] float4).
-cudaError_t launch_build_walk(const TypeDev &T, const float4 *keys, float4 *wk_keys, float4 *wk_bind,
-                              cudaStream_t s);
 
 // The paper's Algorithms 1-4 (comparators): one CTA per character.
 constexpr int kPaperMaxJoints = 1024;

@@ -135,8 +135,21 @@ int default_seg_len(int) { return 16; }
 // by interval colouring).  mode 2: a pure chain cut into P pieces.
 struct WalkSched {
   int mode = 0, P = 0, logP = 0, S = 0, nbs = 0;
-  std::vector<uint32_t> tab;  // [S][P]
+  int K = 1;                  // steps per staged chunk
+  std::vector<uint32_t> tab;  // [S][P], then idle entries up to a multiple of K steps
 };
+
+// Steps per staged chunk: K P <= 32 lane-steps (one chunk buffer), K <= 4.
+int walk_chunk_steps(int P) { return std::max(1, std::min(4, 32 / P)); }
+
+// Chunk length of a checked schedule; its table gets idle entries up to a
+// whole chunk (the kernel copies whole chunks of entries, 16-byte multiples,
+// and only the steps < S of key records).
+void walk_pad(WalkSched &W) {
+  W.K = walk_chunk_steps(W.P);
+  const int S = (W.S + W.K - 1) / W.K * W.K;
+  W.tab.resize((size_t)S * W.P, kWInvalid);
+}
 
 static int ilog2(int p) {
   int l = 0;
@@ -310,7 +323,9 @@ WalkSched choose_walk(const std::vector<int32_t> &par) {
     int P = 1;
     while (P < 32 && n / (2 * P) >= 16) P *= 2;
     WalkSched W = walk_chain(n, P);
-    return walk_check(W, par) ? W : WalkSched{};
+    if (!walk_check(W, par)) return WalkSched{};
+    walk_pad(W);
+    return W;
   }
   std::vector<WalkSched> cand;
   double best = 0.0;
@@ -326,7 +341,73 @@ WalkSched choose_walk(const std::vector<int32_t> &par) {
   WalkSched *pick = nullptr;
   for (auto &W : cand)
     if ((double)n / ((double)W.S * W.P) >= 0.85 * best && (!pick || W.S < pick->S)) pick = &W;
-  return pick ? std::move(*pick) : WalkSched{};
+  if (!pick) return WalkSched{};
+  walk_pad(*pick);
+  return std::move(*pick);
+}
+
+// ------------------------------------------------------------ rigid transforms
+// Host-side double-precision quaternion algebra for the walk kernel's tables
+// (quaternions stored x y z w, Hamilton product, R(q) for unit q).
+void dq_mul(const double *a, const double *b, double *r) {
+  const double x = a[3] * b[0] + a[0] * b[3] + a[1] * b[2] - a[2] * b[1];
+  const double y = a[3] * b[1] - a[0] * b[2] + a[1] * b[3] + a[2] * b[0];
+  const double z = a[3] * b[2] + a[0] * b[1] - a[1] * b[0] + a[2] * b[3];
+  const double w = a[3] * b[3] - a[0] * b[0] - a[1] * b[1] - a[2] * b[2];
+  r[0] = x;
+  r[1] = y;
+  r[2] = z;
+  r[3] = w;
+}
+void dq_conj(const double *a, double *r) {
+  r[0] = -a[0];
+  r[1] = -a[1];
+  r[2] = -a[2];
+  r[3] = a[3];
+}
+void dq_normalize(double *q) {
+  const double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) q[k] = n > 0.0 ? q[k] / n : (k == 3 ? 1.0 : 0.0);
+}
+// r = R(q) v: v + 2 w (u x v) + 2 u x (u x v), u = q.xyz
+void dq_rot(const double *q, const double *v, double *r) {
+  const double cx = 2.0 * (q[1] * v[2] - q[2] * v[1]), cy = 2.0 * (q[2] * v[0] - q[0] * v[2]),
+               cz = 2.0 * (q[0] * v[1] - q[1] * v[0]);
+  r[0] = v[0] + q[3] * cx + (q[1] * cz - q[2] * cy);
+  r[1] = v[1] + q[3] * cy + (q[2] * cx - q[0] * cz);
+  r[2] = v[2] + q[3] * cz + (q[0] * cy - q[1] * cx);
+}
+// Unit quaternion of a rotation matrix (Shepperd's method: the largest of
+// 4w^2, 4x^2, 4y^2, 4z^2 is taken from the diagonal, the others from the
+// off-diagonal sums and differences).
+void dq_from_rot(const double R[3][3], double *q) {
+  const double tr = R[0][0] + R[1][1] + R[2][2];
+  if (tr > 0.0) {
+    const double s = 2.0 * std::sqrt(tr + 1.0);
+    q[3] = 0.25 * s;
+    q[0] = (R[2][1] - R[1][2]) / s;
+    q[1] = (R[0][2] - R[2][0]) / s;
+    q[2] = (R[1][0] - R[0][1]) / s;
+  } else if (R[0][0] > R[1][1] && R[0][0] > R[2][2]) {
+    const double s = 2.0 * std::sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]);
+    q[3] = (R[2][1] - R[1][2]) / s;
+    q[0] = 0.25 * s;
+    q[1] = (R[0][1] + R[1][0]) / s;
+    q[2] = (R[0][2] + R[2][0]) / s;
+  } else if (R[1][1] > R[2][2]) {
+    const double s = 2.0 * std::sqrt(1.0 + R[1][1] - R[0][0] - R[2][2]);
+    q[3] = (R[0][2] - R[2][0]) / s;
+    q[0] = (R[0][1] + R[1][0]) / s;
+    q[1] = 0.25 * s;
+    q[2] = (R[1][2] + R[2][1]) / s;
+  } else {
+    const double s = 2.0 * std::sqrt(1.0 + R[2][2] - R[0][0] - R[1][1]);
+    q[3] = (R[1][0] - R[0][1]) / s;
+    q[0] = (R[0][2] + R[2][0]) / s;
+    q[1] = (R[1][2] + R[2][1]) / s;
+    q[2] = 0.25 * s;
+  }
+  dq_normalize(q);
 }
 
 // ------------------------------------------------------------ device blocks
@@ -381,11 +462,17 @@ struct TypeHost {
   int n_verts = 0;
   int32_t *d_faces = nullptr;   // [n_faces][3]
   int n_faces = 0;
-  float4 *d_wkeys = nullptr;    // schedule-ordered key records
-  float4 *d_wbind = nullptr;    // schedule-ordered inverse binds
+  float4 *d_wkeys = nullptr;    // schedule-ordered key records, inverse binds folded in
+  float4 *d_wu = nullptr;       // schedule-ordered u = R_B^T t_B
+  // the inverse binds as rigid transforms (q x y z w, t), when they are
+  // rigid: from the rest pose in double precision, or from the given
+  // matrices (rotation block orthonormal to 1e-5, determinant > 0)
+  bool bind_rigid = false;
+  std::vector<double> bind_q, bind_t;  // [n][4], [n][3]
+  std::vector<float> keys_h;           // host copy of clips 0 and 1: [clip][key][n][8]
   TypeDev dev{};
   ~TypeHost() {
-    for (void *p : {(void *)d_tables, (void *)d_inv_bind, (void *)d_keys, (void *)d_wkeys, (void *)d_wbind,
+    for (void *p : {(void *)d_tables, (void *)d_inv_bind, (void *)d_keys, (void *)d_wkeys, (void *)d_wu,
                     (void *)d_mesh, (void *)d_add, (void *)d_faces})
       if (p) cudaFree(p);
   }
@@ -444,6 +531,7 @@ struct TypeHost {
     dev.wk_logP = ws.logP;
     dev.wk_S = ws.S;
     dev.wk_nbs = ws.nbs;
+    dev.wk_K = ws.K;
     dev.wk_tab = ws.mode ? (const uint32_t *)(base + o_wt) : nullptr;
     dev.blk_out = (const int32_t *)(base + o_bo);
     sync_dev();
@@ -458,29 +546,167 @@ struct TypeHost {
     dev.keys = d_keys;
     dev.add_keys = d_add;
     dev.wk_keys = d_wkeys;
-    dev.wk_bind = d_wbind;
+    dev.wk_u = d_wu;
     dev.n_verts = n_verts;
     dev.mesh = d_mesh;
     dev.n_faces = n_faces;
     dev.faces = d_faces;
   }
-  // Schedule-ordered key records (when clips are uploaded) and inverse binds
-  // of a walkable type; synchronous.
+  bool walk_ready() const { return ws.mode != 0 && d_wkeys != nullptr; }
+  // The walk kernel's tables of a walkable type with rigid inverse binds and
+  // clips (synchronous; a type without them stays on the segmented kernel).
+  // Record of (clip c, key k, step s, slot p) for the joint j of entry
+  // [s][p], parent pj, keys a = key k and b = key k + 1 (mod n_keys) of joint
+  // j, normalized, b on a's hemisphere:
+  //   theta = 2 atan2(|a - b|, |a + b|),  q_perp = (b - (a.b) a) / |...| (0 if
+  //   b == a),  and with the parent's inverse bind (q_Bp, t_Bp) (identity at
+  //   a root) and the joint's q_Bj folded in:
+  //   q0' = conj(q_Bp) a q_Bj,  q_perp' = conj(q_Bp) q_perp q_Bj,
+  //   t0' = R(conj(q_Bp)) (t_a - t_Bp),  dt' = R(conj(q_Bp)) (t_b - t_a).
+  // u of the entry's joint: R(conj(q_Bj)) t_Bj.  Computed in double, stored
+  // as float.
   cudaError_t build_walk_data() {
-    if (ws.mode == 0 || !d_inv_bind) return cudaSuccess;
-    cudaError_t e = cudaSuccess;
-    if (!d_wbind) e = cudaMalloc(&d_wbind, (size_t)ws.S * ws.P * 3 * sizeof(float4));
-    if (e != cudaSuccess) return e;
-    if (n_clips > 0) {
+    if (d_wkeys) cudaFree(d_wkeys);
+    if (d_wu) cudaFree(d_wu);
+    d_wkeys = nullptr;
+    d_wu = nullptr;
+    if (ws.mode == 0 || !bind_rigid || n_clips == 0 || keys_h.empty()) {
+      sync_dev();
+      return cudaSuccess;
+    }
+    const int P = ws.P, S = ws.S, nc = std::min(n_clips, 2), nk = n_keys;
+    std::vector<float4> rec((size_t)nc * nk * S * 4 * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<float4> u((size_t)S * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    const double ident[4] = {0.0, 0.0, 0.0, 1.0}, zero[3] = {0.0, 0.0, 0.0};
+    for (int st = 0; st < S; ++st)
+      for (int p = 0; p < P; ++p) {
+        const uint32_t e = ws.tab[(size_t)st * P + p];
+        if (e == kWInvalid) continue;
+        const int j = (int)(e & kWJoint), pj = parent[j];
+        const double *qBj = &bind_q[4 * j], *tBj = &bind_t[3 * j];
+        const double *qBp = pj >= 0 ? &bind_q[4 * pj] : ident, *tBp = pj >= 0 ? &bind_t[3 * pj] : zero;
+        double cBp[4], cBj[4], uj[3];
+        dq_conj(qBp, cBp);
+        dq_conj(qBj, cBj);
+        dq_rot(cBj, tBj, uj);
+        u[(size_t)st * P + p] = make_float4((float)uj[0], (float)uj[1], (float)uj[2], 0.f);
+        for (int c = 0; c < nc; ++c)
+          for (int k = 0; k < nk; ++k) {
+            const int k1 = k + 1 == nk ? 0 : k + 1;
+            const float *ka = &keys_h[(((size_t)c * nk + k) * n + j) * 8];
+            const float *kb = &keys_h[(((size_t)c * nk + k1) * n + j) * 8];
+            double a[4], b[4];
+            for (int m = 0; m < 4; ++m) {
+              a[m] = ka[m];
+              b[m] = kb[m];
+            }
+            dq_normalize(a);
+            dq_normalize(b);
+            double d = a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
+            if (d < 0.0) {
+              for (int m = 0; m < 4; ++m) b[m] = -b[m];
+              d = -d;
+            }
+            double dm = 0.0, dp = 0.0, v[4], nv = 0.0;
+            for (int m = 0; m < 4; ++m) {
+              dm += (a[m] - b[m]) * (a[m] - b[m]);
+              dp += (a[m] + b[m]) * (a[m] + b[m]);
+              v[m] = b[m] - d * a[m];
+              nv += v[m] * v[m];
+            }
+            const double theta = 2.0 * std::atan2(std::sqrt(dm), std::sqrt(dp));
+            nv = std::sqrt(nv);
+            for (int m = 0; m < 4; ++m) v[m] = nv > 0.0 ? v[m] / nv : 0.0;
+            double q0[4], qp[4], tmp[4], ta[3], dt[3], t0f[3], dtf[3];
+            dq_mul(cBp, a, tmp);
+            dq_mul(tmp, qBj, q0);
+            dq_mul(cBp, v, tmp);
+            dq_mul(tmp, qBj, qp);
+            for (int m = 0; m < 3; ++m) {
+              ta[m] = (double)ka[4 + m] - tBp[m];
+              dt[m] = (double)kb[4 + m] - (double)ka[4 + m];
+            }
+            dq_rot(cBp, ta, t0f);
+            dq_rot(cBp, dt, dtf);
+            float4 *r = &rec[((((size_t)c * nk + k) * S + st) * 4) * P + p];
+            r[0] = make_float4((float)q0[0], (float)q0[1], (float)q0[2], (float)q0[3]);
+            r[P] = make_float4((float)qp[0], (float)qp[1], (float)qp[2], (float)qp[3]);
+            r[2 * P] = make_float4((float)t0f[0], (float)t0f[1], (float)t0f[2], (float)theta);
+            r[3 * P] = make_float4((float)dtf[0], (float)dtf[1], (float)dtf[2], 0.f);
+          }
+      }
+    cudaError_t e = cudaMalloc(&d_wkeys, rec.size() * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&d_wu, u.size() * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpy(d_wkeys, rec.data(), rec.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_wu, u.data(), u.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
       if (d_wkeys) cudaFree(d_wkeys);
+      if (d_wu) cudaFree(d_wu);
       d_wkeys = nullptr;
-      e = cudaMalloc(&d_wkeys, (size_t)n_clips * n_keys * ws.S * ws.P * 4 * sizeof(float4));
-      if (e != cudaSuccess) return e;
+      d_wu = nullptr;
     }
     sync_dev();
-    e = launch_build_walk(dev, d_keys, n_clips > 0 ? d_wkeys : nullptr, d_wbind, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;
+  }
+  // Inverse binds as rigid transforms: from the rest pose (composed down
+  // the joint list in double, then inverted), or from 3x4 matrices when
+  // their rotation blocks are rotations to 1e-5.
+  void set_bind_from_rest(const float *rq, const float *rt) {
+    bind_q.assign(4 * (size_t)n, 0.0);
+    bind_t.assign(3 * (size_t)n, 0.0);
+    std::vector<double> gq(4 * (size_t)n), gt(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+      double q[4] = {rq[4 * i], rq[4 * i + 1], rq[4 * i + 2], rq[4 * i + 3]}, t[3] = {rt[3 * i], rt[3 * i + 1],
+                                                                                  rt[3 * i + 2]};
+      dq_normalize(q);
+      const int p = parent[i];
+      if (p < 0) {
+        std::copy(q, q + 4, &gq[4 * i]);
+        std::copy(t, t + 3, &gt[3 * i]);
+      } else {
+        double r[3];
+        dq_mul(&gq[4 * p], q, &gq[4 * i]);
+        dq_rot(&gq[4 * p], t, r);
+        for (int m = 0; m < 3; ++m) gt[3 * i + m] = gt[3 * p + m] + r[m];
+      }
+      double cq[4], r[3];
+      dq_conj(&gq[4 * i], cq);
+      dq_rot(cq, &gt[3 * i], r);
+      std::copy(cq, cq + 4, &bind_q[4 * i]);
+      for (int m = 0; m < 3; ++m) bind_t[3 * i + m] = -r[m];
+    }
+    bind_rigid = true;
+  }
+  void set_bind_from_matrices(const float *B) {
+    bind_q.assign(4 * (size_t)n, 0.0);
+    bind_t.assign(3 * (size_t)n, 0.0);
+    bind_rigid = true;
+    for (int i = 0; i < n && bind_rigid; ++i) {
+      const float *m = B + 12 * (size_t)i;
+      double R[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) R[r][c] = m[4 * r + c];
+      double worst = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double d = 0.0;
+          for (int r = 0; r < 3; ++r) d += R[r][a] * R[r][b];
+          worst = std::max(worst, std::fabs(d - (a == b ? 1.0 : 0.0)));
+        }
+      const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
+                         R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                         R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+      if (!(worst <= 1e-5) || !(det > 0.0)) {
+        bind_rigid = false;
+        break;
+      }
+      dq_from_rot(R, &bind_q[4 * i]);
+      for (int r = 0; r < 3; ++r) bind_t[3 * i + r] = m[4 * r + 3];
+    }
+    if (!bind_rigid) {
+      bind_q.clear();
+      bind_t.clear();
+    }
   }
 };
 
@@ -577,7 +803,7 @@ struct anim_plan {
   // (queue counters d_queue[0..1]), the rest to the segmented CTA kernel
   // (d_queue[2..3])
   int n_slots_walk = 0;
-  int walk_ctas = 0, walk_nbs = 0;
+  int walk_nbs = 0;
   size_t walk_smem = 0;
   // frame with skinning: every type on the segmented CTA kernel (its own
   // range layout when the frame's layout gives some types to the walk kernel)
@@ -804,7 +1030,7 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
   P->walk_nbs = 0;
   for (int t : P->used) {
     const TypeHost &T = *ctx->types[t];
-    if (!ctx->use_walk || T.ws.mode == 0) {
+    if (!ctx->use_walk || !T.walk_ready()) {
       smem_f = std::max(smem_f, scan_qt_smem_bytes(T.n, T.seg.nseg, P->C_frame[t]));
       continue;
     }
@@ -824,11 +1050,12 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
       const int t = P->used[u];
       if (walk_t[t] != (pass == 0)) continue;
       const int cnt = (int)P->by_type[u].size(), C = cap[t], nk = ctx->types[t]->n_keys;
-      for (int k = 0; k < cnt; k += kRangeChars) {
+      const int rc = pass == 0 ? kRangeCharsMax : kRangeChars;
+      for (int k = 0; k < cnt; k += rc) {
         RangeDev r;
         r.type = t;
         r.start = P->type_chars_start[u] + k;
-        r.count = std::min(kRangeChars, cnt - k);
+        r.count = std::min(rc, cnt - k);
         r.region = slots;
         slots += (r.count + C - 1) / C + std::min(r.count, std::max(nk, 1));
         ranges.push_back(r);
@@ -837,13 +1064,8 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
     if (pass == 0) P->n_slots_walk = slots;
   }
   P->walk_smem = P->n_slots_walk > 0 ? walk_smem_bytes(wcmax, P->walk_nbs) : 0;
-  P->walk_ctas = 0;
-  if (P->n_slots_walk > 0) {
-    const int nb = walk_blocks_per_sm(P->walk_smem);
-    if (nb < 1) return fail(ctx, ANIM_ECUDA, "chain-walk kernel: no resident CTA at %zu bytes of shared memory",
-                            P->walk_smem);
-    P->walk_ctas = ctx->sm_count * nb;
-  }
+  if (P->n_slots_walk > 0 && walk_blocks_per_sm(P->walk_smem) < 1)
+    return fail(ctx, ANIM_ECUDA, "chain-walk kernel: no resident CTA at %zu bytes of shared memory", P->walk_smem);
   P->n_ranges = (int)ranges.size();
   P->n_slots = slots;
   CK(upload_vec(&P->d_ranges, ranges));
@@ -987,6 +1209,10 @@ int anim_create_skeletons(anim_ctx *ctx, int n_types, const int32_t *joint_count
       cudaFree(dt);
       if (e != cudaSuccess) return fail(ctx, ANIM_ECUDA, "inverse bind from rest pose: %s", cudaGetErrorString(e));
     }
+    if (inv_bind)
+      T->set_bind_from_matrices(inv_bind + off * 12);
+    else
+      T->set_bind_from_rest(rest_q + off * 4, rest_t + off * 3);
     T->sync_dev();
     CK(T->build_walk_data());
     ctx->types.push_back(std::move(T));
@@ -1020,6 +1246,7 @@ int anim_upload_clips(anim_ctx *ctx, int32_t type_id, int n_clips, int n_keys, f
   T.n_clips = n_clips;
   T.n_keys = n_keys;
   T.rate = rate_hz;
+  T.keys_h.assign(keys, keys + (size_t)std::min(n_clips, 2) * n_keys * T.n * 8);
   CK(T.build_walk_data());
   CK(upload_types(ctx));
   return ANIM_OK;
@@ -1316,13 +1543,11 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
     w.nbs_max = plan->walk_nbs;
     w.item_chars = plan->d_sorted;
     w.row_off = plan->d_row_off;
-    w.queue_head = plan->d_queue;
-    w.done = plan->d_queue + 1;
     w.status = ctx->d_status;
     w.time = d_time;
     w.blend_w = d_blend_w;
     w.skin = d_skin;
-    CK(launch_walk(w, plan->walk_ctas, plan->walk_smem, st));
+    CK(launch_walk(w, plan->walk_smem, st));
   }
   if (has_walk && has_cta) {
     CK(cudaEventRecord(ctx->ev_join, ctx->side));

@@ -200,6 +200,8 @@ cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st
 
 // ------------------------------------------------------------ work queue
 constexpr int kBucketThreads = 256;
+constexpr int kBucketPer = kRangeCharsMax / kBucketThreads;  // characters per thread
+static_assert(kBucketPer * kBucketThreads == kRangeCharsMax, "range size");
 
 __device__ __forceinline__ int key_index(float tm, float rate, int nk, int *status) {
   if (!isfinite(tm)) {
@@ -238,7 +240,7 @@ __device__ int block_excl_scan(int v, int *warp_sums, int *total) {
   return before;
 }
 
-// One CTA per range of <= kRangeChars characters of one type: counting sort
+// One CTA per range of <= kRangeCharsMax characters of one type: counting sort
 // by key index k0 in shared memory, items of <= cap characters per (k0) bin
 // written to the range's slot region, and empty items (count 0) in the
 // region's remaining slots.  Regions are laid out in range order (types most
@@ -263,15 +265,23 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
   const int cap = a.cap[R.type];
   const int region_end = (blockIdx.x + 1 < a.n_ranges) ? a.ranges[blockIdx.x + 1].region : a.n_slots;
   for (int b = tid; b < nk; b += nth) s_hist[b] = 0;
-  int cid = -1, k = 0, pos = 0;
-  if (tid < R.count) cid = __ldg(a.type_chars + R.start + tid);
+  int cid[kBucketPer], k[kBucketPer], pos[kBucketPer];
+#pragma unroll
+  for (int m = 0; m < kBucketPer; ++m) {
+    const int i = tid + m * nth;
+    cid[m] = i < R.count ? __ldg(a.type_chars + R.start + i) : -1;
+    k[m] = 0;
+    pos[m] = 0;
+  }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (blockIdx.x == 0 && tid == 0) *a.queue_head = 0;  // consumed by the next launch in stream order
   __syncthreads();
-  if (tid < R.count) {
-    k = key_index(a.time[cid], rate, nk, a.status);
-    pos = atomicAdd(&s_hist[k], 1);  // rank inside the bin
-  }
+#pragma unroll
+  for (int m = 0; m < kBucketPer; ++m)
+    if (cid[m] >= 0) {
+      k[m] = key_index(a.time[cid[m]], rate, nk, a.status);
+      pos[m] = atomicAdd(&s_hist[k[m]], 1);  // rank inside the bin
+    }
   __syncthreads();
   // exclusive scans over the bins: character starts and item starts
   const int per = (nk + nth - 1) / nth;
@@ -290,7 +300,9 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
     ipre += (s_hist[b] + cap - 1) / cap;
   }
   __syncthreads();
-  if (cid >= 0) a.sorted[R.start + s_start[k] + pos] = cid;
+#pragma unroll
+  for (int m = 0; m < kBucketPer; ++m)
+    if (cid[m] >= 0) a.sorted[R.start + s_start[k[m]] + pos[m]] = cid[m];
   for (int b = b0; b < b1; ++b) {
     const int cnt = s_hist[b];
     for (int m = 0; m * cap < cnt; ++m) {

@@ -1,27 +1,37 @@
 // Chain-walk frame kernel: Simulation -> Hierarchy-Scan -> Bind MeshPose
-// (Sec. 1 steps 1-3, Eq. 1) for skeleton types whose natural chains can be
-// walked parent-first with few idle lanes, and for pure chains.
+// (Sec. 1 steps 1-3, Eq. 1) walked directly in skin space, for skeleton
+// types whose natural chains can be list-scheduled on a few lanes with few
+// idle steps, and for pure chains.
 //
-// One CTA is one warp and a persistent worker.  A work item is C = 32 / P
-// characters of one type that share the key index k0; lane = (character
-// c, schedule slot).  The type's static schedule (built on the host) tells
-// each lane which joint it composes at each step, so every lane keeps its
-// model pose M in registers while it walks a natural chain:
-//   sample L_j from the key records (one 64-byte record per clip: q0, the
-//   unit tangent q_perp, t0 with the arc angle, t1 - t0), M = M * L_j (or
-//   slot[link] * L_j at a chain start), S_j = M * B_j, stage S_j.
-// Branch points (joints that other chains hang from) leave M in a shared
-// memory slot for the lane that starts the child chain at a later step.
-// The key records and inverse binds are stored in schedule order, so at
-// step s the P lanes of a character read P consecutive float4 (one or two
-// cache lines per load instruction), and the C characters of an item read
-// the same addresses.  Skin rows go out from registers.
+// Skin-space walk.  With rigid inverse binds B, the skin matrix of joint j
+// satisfies S_j = M_j B_j = S_p (B_p^-1 L_j B_j) = S_p L'_j (p the parent; a
+// root has B_p = I).  Because slerp commutes with multiplying both of its
+// ends by unit quaternions on the left and on the right, and lerp with any
+// affine map, L'_j is sampled exactly like L_j from key records whose
+// rotations are q' = conj(q_Bp) q q_Bj and whose translations are
+// R_Bp^T (t - t_Bp); its translation then needs R' u_j with u_j = R_Bj^T t_Bj
+// (minus the joint's rest position).  The host builds these records once per
+// clip upload, so per joint and character the kernel samples two key pairs,
+// blends them, forms L' = [R(q') | t' + R(q') u] and makes ONE 3x4 product,
+// which is the skin matrix it stores -- no separate bind product, no second
+// pass over the joints, no block barrier.
 //
-// Pure chains (mode 2, e.g. a 1,024-joint tail) cannot be walked this way
-// without a 1,024-step dependency; they are cut into P pieces: pass A forms
-// each piece's product, a warp-shuffle Hillis-Steele scan over the pieces
-// gives each piece's parent transform, and pass B walks the piece again
-// from it (sampling twice instead of storing every local matrix).
+// One CTA is one warp and one work item: C = 32 / P characters of one type
+// that share the key index k0; lane = (character, schedule slot).  The
+// type's static schedule (host-built) names the joint each slot composes at
+// each step.  A lane keeps S in registers along its natural chain; branch
+// points leave S in a shared-memory slot for the lane that starts a child
+// chain at a later step.  Pure chains (mode 2) are cut into P pieces: pass A
+// forms each piece's product, a warp-shuffle Hillis-Steele scan over the
+// pieces gives each piece's parent transform, pass B walks again from it.
+//
+// Staging.  The steps are processed in chunks of K = 32 / P (at most 4)
+// steps.  A chunk's key records (both clips), u vectors and schedule entries
+// are contiguous in schedule order in global memory; lane 0 copies them into
+// a ring of shared-memory buffers with cp.async.bulk (TMA, 1-D), each
+// completing on its own mbarrier, several chunks ahead of the compute.  Within a chunk each lane
+// first samples its K local poses (independent work, so the latency of the
+// trigonometry overlaps), then walks the K steps.
 #include <cuda_runtime.h>
 
 #include "anim_internal.h"
@@ -33,24 +43,113 @@ namespace anim {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before a chunk counts as lost
 
-__device__ __forceinline__ Rec ld_rec(const float4 *p, int P) {
-  Rec r;
-  r.q0 = __ldg(p);
-  r.qp = __ldg(p + P);
-  r.t0 = __ldg(p + 2 * P);
-  r.dt = __ldg(p + 3 * P);
-  return r;
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase of `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i >= 16) __nanosleep(64);
+  }
+  return false;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of
+// 16) completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
 }
 
-__device__ __forceinline__ Aff ld_bind(const float4 *p, int P) {
-  Aff b;
-  b.r0 = __ldg(p);
-  b.r1 = __ldg(p + P);
-  b.r2 = __ldg(p + 2 * P);
-  return b;
+// Chunk buffer layout (bytes): records of clip 0 [K][4][P] float4, records of
+// clip 1, u [K][P] float4, schedule entries [K][P] uint32; K P <= 32.
+constexpr uint32_t kRecBytes = 32 * 4 * 16;
+constexpr uint32_t kUOff = 2 * kRecBytes;
+constexpr uint32_t kTabOff = kUOff + 32 * 16;
+constexpr uint32_t kChunkBytes = kTabOff + 32 * 4;
+static_assert(kChunkBytes % 128 == 0, "chunk buffers stay 128-byte aligned");
+// Chunk buffers per CTA: up to kStages chunks are in flight, so the copy
+// latency (about a microsecond from L2 under load) overlaps several chunks'
+// compute.
+constexpr int kStages = 3;
+
+// Slerp between keys from a record: cos(a theta) q0 + sin(a theta) q_perp
+// (q0, q_perp orthonormal), translation t0 + a (t1 - t0).  r points at the
+// slot's first field; fields are P float4 apart.
+__device__ __forceinline__ void rec_sample(const float4 *r, int P, float al, float4 &q, float3 &t) {
+  const float4 q0 = r[0], qp = r[P], t0 = r[2 * P], dt = r[3 * P];
+  float s, c;
+  __sincosf(al * t0.w, &s, &c);
+  q = make_float4(fmaf(c, q0.x, s * qp.x), fmaf(c, q0.y, s * qp.y), fmaf(c, q0.z, s * qp.z), fmaf(c, q0.w, s * qp.w));
+  t = make_float3(fmaf(al, dt.x, t0.x), fmaf(al, dt.y, t0.y), fmaf(al, dt.z, t0.z));
 }
 
+// atan2(y, x) for y, x >= 0 (the first quadrant), branch-free: with
+// t = min / max in [0, 1], atan(t) = t P(t^2) for a degree-7 polynomial P
+// fitted here to minimize the maximum error on [0, 1] (Lawson's iteratively
+// reweighted least squares on Chebyshev points; approximation error 4e-8,
+// about 1.3e-7 rad with float evaluation), then pi/2 - atan(t) when y > x.
+// Straight-line code, so the compiler can interleave several samples.
+__device__ __forceinline__ float atan2_q1(const float y, const float x) {
+  const float lo = fminf(x, y), hi = fmaxf(fmaxf(x, y), 1e-30f);
+  const float t = __fdividef(lo, hi), u = t * t;
+  float p = -0.004054560791701078f;
+  p = fmaf(p, u, 0.0218629352748394f);
+  p = fmaf(p, u, -0.05591229721903801f);
+  p = fmaf(p, u, 0.09642194956541061f);
+  p = fmaf(p, u, -0.1390862911939621f);
+  p = fmaf(p, u, 0.19946566224098206f);
+  p = fmaf(p, u, -0.33329859375953674f);
+  p = fmaf(p, u, 0.9999993443489075f);
+  const float a = t * p;
+  return y > x ? 1.5707963267948966f - a : a;
+}
+
+// Slerp on the shorter arc between unit quaternions a and b at weight w:
+// with d = a.b, v = sign(d) b - |d| a (orthogonal to a, |v| = sin(theta)),
+// theta = atan2(|v|, |d|), the result is cos(w theta) a + sin(w theta) v/|v|.
+// For v = 0 (equal rotations) theta = 0 and the result is a.
+__device__ __forceinline__ float4 blend_unit(const float4 a, const float4 b, const float w) {
+  const float d = dot4(a, b);
+  const float sg = d < 0.f ? -1.f : 1.f, x = fabsf(d);
+  const float4 v = make_float4(fmaf(sg, b.x, -x * a.x), fmaf(sg, b.y, -x * a.y), fmaf(sg, b.z, -x * a.z),
+                               fmaf(sg, b.w, -x * a.w));
+  const float vv = fmaxf(dot4(v, v), 1e-36f);
+  const float rs = rsqrtf(vv);
+  const float th = atan2_q1(vv * rs, x);
+  float s, c;
+  __sincosf(w * th, &s, &c);
+  const float k = s * rs;
+  return make_float4(fmaf(c, a.x, k * v.x), fmaf(c, a.y, k * v.y), fmaf(c, a.z, k * v.z), fmaf(c, a.w, k * v.w));
+}
+
+// L' = [R(q) | t + R(q) u] for a unit quaternion q.
+__device__ __forceinline__ Aff local_skin(const float4 q, const float3 t, const float4 u) {
+  Aff L = aff_from_qt(q, 0.f, 0.f, 0.f);
+  L.r0.w = fmaf(L.r0.x, u.x, fmaf(L.r0.y, u.y, fmaf(L.r0.z, u.z, t.x)));
+  L.r1.w = fmaf(L.r1.x, u.x, fmaf(L.r1.y, u.y, fmaf(L.r1.z, u.z, t.y)));
+  L.r2.w = fmaf(L.r2.x, u.x, fmaf(L.r2.y, u.y, fmaf(L.r2.z, u.z, t.z)));
+  return L;
+}
 
 __device__ __forceinline__ Aff shfl_up_aff(const Aff &a, int d, int width) {
   Aff r;
@@ -63,194 +162,227 @@ __device__ __forceinline__ Aff shfl_up_aff(const Aff &a, int d, int width) {
   return r;
 }
 
-// The step loop shared by the tree walk (KIND 0) and the two passes of a
-// chain split (KIND 1: piece product only, KIND 2: walk from the piece's
-// parent transform M0).  Loads of step s + 1 are issued before step s is
-// composed.  KIND 0 and 2 store S_j = M_j B_j straight from registers (three
-// 16-byte stores; the three land in the same or adjacent sectors, which L2
-// merges before write-back).
-template <int KIND>
-__device__ __forceinline__ Aff walk_steps(const uint32_t *tab, const float4 *ka, const float4 *kb,
-                                          const float4 *bb, int P, int S, bool act, bool two, float al,
-                                          float w, Aff M, float4 *bsl, float *skin_c) {
-  uint32_t e_n = __ldg(tab);
-  Rec ra_n = ld_rec(ka, P), rb_n = two ? ld_rec(kb, P) : ra_n;
-  Aff b_n;
-  if (KIND != 1) b_n = ld_bind(bb, P);
-  for (int s = 0; s < S; ++s) {
-    const uint32_t e = e_n;
-    const Rec ra = ra_n, rb = rb_n;
-    const Aff B = b_n;
-    if (s + 1 < S) {
-      tab += P;
-      ka += 4 * P;
-      kb += 4 * P;
-      e_n = __ldg(tab);
-      ra_n = ld_rec(ka, P);
-      if (two) rb_n = ld_rec(kb, P);
-      if (KIND != 1) {
-        bb += 3 * P;
-        b_n = ld_bind(bb, P);
-      }
-    }
-    if (act && !(e & 0x80000000u)) {
-      const Aff L = sample_rec(ra, rb, al, w, two);
-      Aff Mp = M;
-      if (KIND == 0 && (e & kWStart)) {
-        const uint32_t ls = (e >> kWLoadShift) & 0xFFu;
-        Mp = ls == kWRootSlot ? aff_identity() : lds_aff(bsl + ls * 3);
-      }
-      M = aff_mul(Mp, L);
-      if (KIND == 0 && (e & kWStore)) sts_aff(bsl + ((e >> kWStoreShift) & 0xFFu) * 3, M);
-      if (KIND != 1) stg_aff(reinterpret_cast<float4 *>(skin_c) + (e & kWJoint) * 3, aff_mul(M, B));
-    }
-    if (KIND == 0) __syncwarp();  // branch slots written this step are read at later steps
-  }
-  return M;
+struct ItemCtx {
+  int P, logP, S, nk, k0, slot, c, count;
+  bool act, two, tree;
+  float al, w;
+  float4 *out;     // the lane's character's skin rows
+  float4 *bslots;  // the lane's character's branch slots [nbs][3]
+  const float4 *ra, *rb, *u;
+  const uint32_t *tab;
+};
+
+// Issue chunk `ch` (steps ch K .. min(S, ch K + K) - 1) into buffer `buf`:
+// the key records and u of its steps, and a whole chunk of schedule entries
+// (the table is padded with idle entries to whole chunks).
+template <int K>
+__device__ __forceinline__ void issue_chunk(const ItemCtx &x, int ch, unsigned char *stage, uint64_t *bar) {
+  const int kc = min(K, x.S - ch * K);
+  const uint32_t rec = (uint32_t)(kc * 4 * x.P * 16), ub = (uint32_t)(kc * x.P * 16), tb = (uint32_t)(K * x.P * 4);
+  const size_t rstep = (size_t)ch * K * 4 * x.P, ustep = (size_t)ch * K * x.P;
+  // No proxy fence: the buffer is only read (ld.shared) by the generic proxy,
+  // and those reads completed before the __syncwarp that precedes this
+  // call.  (A fence here would also wait for the warp's outstanding global
+  // stores, one round trip per chunk.)
+  mbar_expect_tx(bar, (x.two ? 2u : 1u) * rec + ub + tb);
+  bulk_g2s(stage, x.ra + rstep, rec, bar);
+  if (x.two) bulk_g2s(stage + kRecBytes, x.rb + rstep, rec, bar);
+  bulk_g2s(stage + kUOff, x.u + ustep, ub, bar);
+  bulk_g2s(stage + kTabOff, x.tab + ustep, tb, bar);
 }
 
-__global__ void __launch_bounds__(32, 8) k_walk(const WalkArgs a) {
-  extern __shared__ __align__(128) float4 sm[];
+// One staged chunk.  KIND 0: tree walk (branch slots, stores); KIND 1: the
+// product of a chain piece only; KIND 2: a chain piece walked from its parent
+// transform, with stores.  S carries the lane's running skin matrix.
+// The local transforms of all K steps are formed first, without branches
+// (steps past the end of a short last chunk compute unused values from
+// whatever the buffer holds), so their latencies overlap; the walk itself is
+// then one 3x4 product per step.
+template <int K, int KIND>
+__device__ __forceinline__ void walk_chunk(const ItemCtx &x, const unsigned char *stage, Aff &S) {
+  const float4 *ra = reinterpret_cast<const float4 *>(stage) + x.slot;
+  const float4 *rb = reinterpret_cast<const float4 *>(stage + kRecBytes) + x.slot;
+  const float4 *us = reinterpret_cast<const float4 *>(stage + kUOff) + x.slot;
+  const uint32_t *ts = reinterpret_cast<const uint32_t *>(stage + kTabOff) + x.slot;
+  const int P = x.P;
+  Aff L[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float4 q;
+    float3 t;
+    rec_sample(ra + k * 4 * P, P, x.al, q, t);
+    if (x.two) {
+      float4 qb;
+      float3 tb;
+      rec_sample(rb + k * 4 * P, P, x.al, qb, tb);
+      q = blend_unit(q, qb, x.w);
+      t = make_float3(fmaf(x.w, tb.x - t.x, t.x), fmaf(x.w, tb.y - t.y, t.y), fmaf(x.w, tb.z - t.z, t.z));
+    }
+    L[k] = local_skin(q, t, us[k * P]);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t e = ts[k * P];  // idle entries past the schedule's end
+    const bool valid = x.act && e != kWInvalid;
+    Aff Sp = S;
+    if (KIND == 0 && valid && (e & kWStart)) {
+      const uint32_t ls = (e >> kWLoadShift) & 0xFFu;
+      Sp = ls == kWRootSlot ? aff_identity() : lds_aff(x.bslots + 3 * ls);
+    }
+    const Aff Sn = aff_mul(Sp, L[k]);
+    if (valid) {
+      S = Sn;
+      if (KIND == 0 && (e & kWStore)) sts_aff(x.bslots + 3 * ((e >> kWStoreShift) & 0xFFu), Sn);
+      if (KIND != 1) stg_aff(x.out + 3 * (e & kWJoint), Sn);
+    }
+    if (KIND == 0) __syncwarp();  // branch slots written at this step are read at later steps
+  }
+}
+
+// The whole item: the chunk sequence (once for a tree, twice for a chain
+// split), up to kStages chunks staged ahead of the compute.  Returns false if
+// a chunk never arrived (its wait ran out).
+template <int K>
+__device__ bool walk_item(const ItemCtx &x, unsigned char *stage, uint64_t *bars, uint32_t &parity,
+                          uint32_t &inflight) {
   const int lane = threadIdx.x;
-
-  int ticket = 0;
-  if (lane == 0) ticket = atomicAdd(a.queue_head, 1);
-  int it = __shfl_sync(kFull, ticket, 0);
-  while (it < a.n_items) {
-    if (lane == 0) ticket = atomicAdd(a.queue_head, 1);  // next item, consumed at the end of this one
-    const WorkItem wi = a.items[it];
-    if (wi.count > 0) {
-      const TypeDev &T = a.types[wi.type];
-      const int P = T.wk_P, logP = T.wk_logP, S = T.wk_S, nk = T.n_keys;
-      const bool two = T.n_clips >= 2;
-      const int c = lane >> logP, slot = lane & (P - 1);
-      const bool act = c < wi.count;
-      float al = 0.f, w = 0.f;
-      float *skin_c = a.skin;
-      if (act) {
-        const int cid = __ldg(a.item_chars + wi.start + c);
-        skin_c = a.skin + a.row_off[cid] * 12;
-        const float tm = __ldg(a.time + cid);
-        if (isfinite(tm)) {
-          const float u = __fmul_rn(tm, T.rate);
-          al = u - floorf(u);
-        } else {
-          atomicOr(a.status, 1);
-        }
-        w = __ldg(a.blend_w + cid);
-      }
-      const uint32_t *tab = T.wk_tab + slot;
-      const float4 *ka = T.wk_keys + (size_t)wi.k0 * S * 4 * P + slot;
-      const float4 *kb = two ? ka + (size_t)nk * S * 4 * P : ka;
-      const float4 *bb = T.wk_bind + slot;
-      float4 *bsl = sm + (size_t)c * a.nbs_max * 3;
-      if (T.wk_mode == 1) {
-        walk_steps<0>(tab, ka, kb, bb, P, S, act, two, al, w, aff_identity(), bsl, skin_c);
-      } else {
-        // pass A: product of this lane's piece
-        Aff Tp = walk_steps<1>(tab, ka, kb, bb, P, S, act, two, al, w, aff_identity(), bsl, skin_c);
-        // inclusive scan over the character's P pieces, then shift by one
-        for (int d = 1; d < P; d <<= 1) {
-          const Aff X = shfl_up_aff(Tp, d, P);
-          if (slot >= d) Tp = aff_mul(X, Tp);
-        }
-        Aff M0 = shfl_up_aff(Tp, 1, P);
-        if (slot == 0) M0 = aff_identity();
-        // pass B: walk the piece again from its parent transform
-        walk_steps<2>(tab, ka, kb, bb, P, S, act, two, al, w, M0, bsl, skin_c);
-      }
-      __syncwarp();
-    }
-    it = __shfl_sync(kFull, ticket, 0);
+  const int nch = (x.S + K - 1) / K, nq = x.tree ? nch : 2 * nch;
+  for (int b = 0; b < kStages && b < nq; ++b) {
+    if (lane == 0) issue_chunk<K>(x, b % nch, stage + b * kChunkBytes, &bars[b]);
+    inflight |= 1u << b;  // buffers with a copy issued and not yet waited for
   }
-  if (lane == 0 && a.done) {
-    __threadfence();
-    if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
-      *a.queue_head = 0;
-      *a.done = 0;
-      __threadfence();
+  Aff S = aff_identity();
+  for (int q = 0; q < nq; ++q) {
+    const int buf = q % kStages;
+    if (!mbar_wait(&bars[buf], (parity >> buf) & 1u)) return false;
+    parity ^= 1u << buf;
+    inflight &= ~(1u << buf);
+    const unsigned char *st = stage + buf * kChunkBytes;
+    if (x.tree) {
+      walk_chunk<K, 0>(x, st, S);
+    } else if (q < nch) {
+      walk_chunk<K, 1>(x, st, S);
+    } else {
+      if (q == nch) {
+        // S holds this piece's product: inclusive scan over the character's
+        // P pieces, shifted by one, gives the transform the piece hangs from
+        const int slot = x.slot;
+        for (int d = 1; d < x.P; d <<= 1) {
+          const Aff X = shfl_up_aff(S, d, x.P);
+          if (slot >= d) S = aff_mul(X, S);
+        }
+        const Aff M0 = shfl_up_aff(S, 1, x.P);
+        S = slot == 0 ? aff_identity() : M0;
+      }
+      walk_chunk<K, 2>(x, st, S);
+    }
+    __syncwarp();
+    if (q + kStages < nq) {
+      if (lane == 0) issue_chunk<K>(x, (q + kStages) % nch, stage + buf * kChunkBytes, &bars[buf]);
+      inflight |= 1u << buf;
     }
   }
+  return true;
 }
 
-// Schedule-ordered tables.  Record of (clip, key k, step s, slot): the joint
-// j of entry [s][slot]; keys k and k1 = (k + 1) mod n_keys of the clip,
-// normalized, b on a's hemisphere; theta = 2 atan2(|a - b|, |a + b|);
-// q_perp = (b - (a.b) a) / |b - (a.b) a| (0 when b == a).
-__global__ void k_build_walk_keys(const TypeDev T, const float4 *keys, float4 *out) {
-  const int P = T.wk_P, S = T.wk_S, n = T.n, nk = T.n_keys;
-  const long long total = (long long)T.n_clips * nk * S * P;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int slot = (int)(i % P);
-    const long long r = i / P;
-    const int s = (int)(r % S);
-    const long long ck = r / S;
-    const int k = (int)(ck % nk), clip = (int)(ck / nk);
-    float4 *o = out + (ck * S + s) * 4 * P + slot;
-    const uint32_t e = T.wk_tab[s * P + slot];
-    if (e & 0x80000000u) {
-      for (int f = 0; f < 4; ++f) o[f * P] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    float4 rec[4];
-    make_rec(keys, clip, k, nk, n, (int)(e & kWJoint), rec);
-    for (int f = 0; f < 4; ++f) o[f * P] = rec[f];
+__global__ void __launch_bounds__(32, 12) k_walk(const WalkArgs a) {
+  extern __shared__ __align__(128) unsigned char wsm[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  const int lane = threadIdx.x;
+  // launched with programmatic stream serialization after the work-queue
+  // kernel: set up, then wait for it before reading the item
+  asm volatile("griddepcontrol.launch_dependents;");
+  if (lane == 0) {
+    for (int b = 0; b < kStages; ++b) mbar_init(&bars[b]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-}
-
-__global__ void k_build_walk_bind(const TypeDev T, float4 *out) {
-  const int P = T.wk_P, S = T.wk_S;
-  const int total = S * P;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int slot = i % P, s = i / P;
-    const uint32_t e = T.wk_tab[i];
-    float4 *o = out + (size_t)s * 3 * P + slot;
-    for (int r = 0; r < 3; ++r)
-      o[r * P] = (e & 0x80000000u) ? make_float4(0.f, 0.f, 0.f, 0.f) : T.inv_bind[(e & kWJoint) * 3 + r];
+  __syncwarp();
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const WorkItem wi = a.items[blockIdx.x];
+  if (wi.count <= 0) return;
+  const TypeDev &T = a.types[wi.type];
+  ItemCtx x;
+  x.P = T.wk_P;
+  x.logP = T.wk_logP;
+  x.S = T.wk_S;
+  x.nk = T.n_keys;
+  x.k0 = wi.k0;
+  x.two = T.n_clips >= 2;
+  x.tree = T.wk_mode == 1;
+  x.c = lane >> x.logP;
+  x.slot = lane & (x.P - 1);
+  x.count = wi.count;
+  x.act = x.c < wi.count;
+  x.al = 0.f;
+  x.w = 0.f;
+  x.out = reinterpret_cast<float4 *>(a.skin);
+  if (x.act) {
+    const int cid = __ldg(a.item_chars + wi.start + x.c);
+    x.out = reinterpret_cast<float4 *>(a.skin) + a.row_off[cid] * 3;
+    const float tm = __ldg(a.time + cid);
+    if (isfinite(tm)) {
+      const float u = __fmul_rn(tm, T.rate);
+      x.al = u - floorf(u);
+    } else {
+      atomicOr(a.status, kStatusNonfiniteTime);
+    }
+    x.w = x.two ? __ldg(a.blend_w + cid) : 0.f;
+  }
+  const size_t clip_stride = (size_t)x.nk * x.S * 4 * x.P;
+  x.ra = T.wk_keys + (size_t)x.k0 * x.S * 4 * x.P;
+  x.rb = x.ra + clip_stride;
+  x.u = T.wk_u;
+  x.tab = T.wk_tab;
+  unsigned char *stage = wsm;
+  x.bslots = reinterpret_cast<float4 *>(wsm + kStages * kChunkBytes) + (size_t)x.c * a.nbs_max * 3;
+  uint32_t parity = 0, inflight = 0;
+  bool ok;
+  switch (T.wk_K) {
+    case 1: ok = walk_item<1>(x, stage, bars, parity, inflight); break;
+    case 2: ok = walk_item<2>(x, stage, bars, parity, inflight); break;
+    default: ok = walk_item<4>(x, stage, bars, parity, inflight); break;
+  }
+  if (!ok) {
+    // a staged chunk did not complete in time: report it, and before the CTA
+    // (and its shared memory) goes away wait once more, bounded, for the
+    // copies still in flight
+    if (lane == 0) atomicOr(a.status, kStatusTimeout);
+    for (int b = 0; b < kStages; ++b)
+      if (inflight & (1u << b)) mbar_wait(&bars[b], (parity >> b) & 1u);
   }
 }
 
 }  // namespace
 
 size_t walk_smem_bytes(int chars_per_item, int nbs) {
-  const size_t b = 48ull * (size_t)chars_per_item * (size_t)nbs;
-  return b > 16 ? b : 16;
+  return (size_t)kStages * kChunkBytes + 48ull * (size_t)chars_per_item * (size_t)nbs;
 }
 
 int walk_blocks_per_sm(size_t smem) {
+  static SmemLimit lim;
+  if (ensure_smem_limit((const void *)k_walk, lim, smem, 48 * 1024) != cudaSuccess) return 0;
   int nb = 0;
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                              cudaSuccess)
-    return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk, 32, smem) != cudaSuccess) return 0;
   return nb;
 }
 
-cudaError_t launch_walk(const WalkArgs &a, int ctas, size_t smem, cudaStream_t st) {
+cudaError_t launch_walk(const WalkArgs &a, size_t smem, cudaStream_t st) {
   static SmemLimit lim;
   cudaError_t e = ensure_smem_limit((const void *)k_walk, lim, smem, 48 * 1024);
   if (e != cudaSuccess) return e;
-  k_walk<<<ctas, 32, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_build_walk(const TypeDev &T, const float4 *keys, float4 *wk_keys, float4 *wk_bind,
-                              cudaStream_t st) {
-  if (T.wk_mode == 0) return cudaSuccess;
-  if (wk_bind && T.inv_bind) {
-    k_build_walk_bind<<<(T.wk_S * T.wk_P + 255) / 256, 256, 0, st>>>(T, wk_bind);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (wk_keys && keys && T.n_clips > 0) {
-    const long long total = (long long)T.n_clips * T.n_keys * T.wk_S * T.wk_P;
-    const long long nb = (total + 255) / 256;
-    const int blocks = (int)(nb < 4096 ? nb : 4096);
-    k_build_walk_keys<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(T, keys, wk_keys);
-    return cudaGetLastError();
-  }
-  return cudaSuccess;
+  // programmatic stream serialization: the CTAs become resident and set up
+  // while the work-queue kernel runs, and wait for it in griddepcontrol.wait
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)a.n_items);
+  lc.blockDim = dim3(32u);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, k_walk, a);
 }
 
 }  // namespace anim

@@ -784,3 +784,44 @@ def test_nonfinite_time_sets_status(torch):
     w2 = dict(w, time=np.array([0.2, 0.0, 0.0], np.float32))  # non-finite times sample key 0
     ref = oracle.frame(w2)
     _gpu.assert_skin_close(out.cpu().numpy(), ref, w2)
+
+
+@pytest.mark.parametrize("bind", ["rest", "rigid_matrices", "scaled_matrices"])
+def test_walk_kernel_bind_sources(torch, bind):
+    """The chain-walk frame kernel folds rigid inverse binds into its key
+    records (skin-space walk).  Inverse binds derived from the rest pose,
+    given as rigid 3x4 matrices, or given with a scale (not rigid: such a
+    type runs on the segmented kernel instead) all give the oracle's skin
+    matrices S = M B with the oracle's model poses M, under the walk kernel
+    on and off."""
+    rng = np.random.default_rng(31)
+    w = synth.subset(synth.config2(), list(range(0, 4096, 9)) + [4096])
+    types = w["types"]
+    Bs = [oracle.inverse_bind(t["parents"], t["rest_q"], t["rest_t"]).astype(np.float32) for t in types]
+    if bind == "scaled_matrices":
+        for B in Bs:
+            B[:, :, :3] *= 1.5
+    _, M = oracle.frame(w, want_model=True)
+    off = oracle.offsets(w["char_type"], types)
+    Bj = np.concatenate([Bs[t] for t in w["char_type"]]).astype(np.float64)
+    ref = oracle.bind(M, Bj)
+    assert Bj.shape[0] == off[-1]
+    import paper_2505_06703_gb300 as pk
+    for walk in (1, 0):
+        ctx = pk.Context(0)
+        if bind == "rest":
+            ids = ctx.create_skeletons([t["parents"] for t in types], rest_q=[t["rest_q"] for t in types],
+                                       rest_t=[t["rest_t"] for t in types])
+        else:
+            ids = ctx.create_skeletons([t["parents"] for t in types], inv_bind=Bs)
+        for i, t in zip(ids, types):
+            ctx.upload_clips(i, t["keys"], t["rate_hz"])
+        plan = ctx.plan(np.asarray(ids, np.int32)[w["char_type"]])
+        sched = ctx.get_schedule(plan)
+        ctx.set_schedule(plan, sched[:3] + [walk, sched[4]])
+        out = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"]))
+        scale = 1.5 if bind == "scaled_matrices" else 1.0
+        errs = _gpu.per_type_maxabs(out.cpu().numpy(), ref, w)
+        for ty, e in errs.items():
+            assert e <= scale * _gpu.tol_for_depth(types[ty]["depth"]), (walk, ty, e)
+        assert ctx.status() == 0
