@@ -553,98 +553,117 @@ struct TypeHost {
     dev.faces = d_faces;
   }
   bool walk_ready() const { return ws.mode != 0 && d_wkeys != nullptr; }
-  // The walk kernel's tables of a walkable type with rigid inverse binds and
-  // clips (synchronous; a type without them stays on the segmented kernel).
-  // Record of (clip c, key k, step s, slot p) for the joint j of entry
-  // [s][p], parent pj, keys a = key k and b = key k + 1 (mod n_keys) of joint
-  // j, normalized, b on a's hemisphere:
+  // Key-pair records with the inverse binds folded in (skin-space walk), for
+  // a walkable type with rigid inverse binds and clips (synchronous; without
+  // them the tables stay empty and the type runs on the segmented kernel).
+  // Record of (clip c, key k, joint j), parent pj, keys a = key k and b = key
+  // k + 1 (mod n_keys) of joint j, normalized, b on a's hemisphere:
   //   theta = 2 atan2(|a - b|, |a + b|),  q_perp = (b - (a.b) a) / |...| (0 if
   //   b == a),  and with the parent's inverse bind (q_Bp, t_Bp) (identity at
   //   a root) and the joint's q_Bj folded in:
   //   q0' = conj(q_Bp) a q_Bj,  q_perp' = conj(q_Bp) q_perp q_Bj,
-  //   t0' = R(conj(q_Bp)) (t_a - t_Bp),  dt' = R(conj(q_Bp)) (t_b - t_a).
-  // u of the entry's joint: R(conj(q_Bj)) t_Bj.  Computed in double, stored
-  // as float.
+  //   t0' = R(conj(q_Bp)) (t_a - t_Bp),  dt' = R(conj(q_Bp)) (t_b - t_a),
+  // stored as 4 float4 (q0', q_perp', (t0', theta), (dt', 0)); u of joint j is
+  // R(conj(q_Bj)) t_Bj.  Built per joint, then laid out in the walk
+  // schedule's order [clip][key][S][4][P] (d_wkeys) and [S][P] (d_wu).
+  // Computed in double, stored as float.
   cudaError_t build_walk_data() {
-    if (d_wkeys) cudaFree(d_wkeys);
-    if (d_wu) cudaFree(d_wu);
-    d_wkeys = nullptr;
-    d_wu = nullptr;
+    for (float4 **p : {&d_wkeys, &d_wu}) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
     if (ws.mode == 0 || !bind_rigid || n_clips == 0 || keys_h.empty()) {
       sync_dev();
       return cudaSuccess;
     }
-    const int P = ws.P, S = ws.S, nc = std::min(n_clips, 2), nk = n_keys;
-    std::vector<float4> rec((size_t)nc * nk * S * 4 * P, make_float4(0.f, 0.f, 0.f, 0.f));
-    std::vector<float4> u((size_t)S * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    const int nc = std::min(n_clips, 2), nk = n_keys;
     const double ident[4] = {0.0, 0.0, 0.0, 1.0}, zero[3] = {0.0, 0.0, 0.0};
-    for (int st = 0; st < S; ++st)
-      for (int p = 0; p < P; ++p) {
-        const uint32_t e = ws.tab[(size_t)st * P + p];
-        if (e == kWInvalid) continue;
-        const int j = (int)(e & kWJoint), pj = parent[j];
-        const double *qBj = &bind_q[4 * j], *tBj = &bind_t[3 * j];
-        const double *qBp = pj >= 0 ? &bind_q[4 * pj] : ident, *tBp = pj >= 0 ? &bind_t[3 * pj] : zero;
-        double cBp[4], cBj[4], uj[3];
-        dq_conj(qBp, cBp);
-        dq_conj(qBj, cBj);
-        dq_rot(cBj, tBj, uj);
-        u[(size_t)st * P + p] = make_float4((float)uj[0], (float)uj[1], (float)uj[2], 0.f);
-        for (int c = 0; c < nc; ++c)
-          for (int k = 0; k < nk; ++k) {
-            const int k1 = k + 1 == nk ? 0 : k + 1;
-            const float *ka = &keys_h[(((size_t)c * nk + k) * n + j) * 8];
-            const float *kb = &keys_h[(((size_t)c * nk + k1) * n + j) * 8];
-            double a[4], b[4];
-            for (int m = 0; m < 4; ++m) {
-              a[m] = ka[m];
-              b[m] = kb[m];
-            }
-            dq_normalize(a);
-            dq_normalize(b);
-            double d = a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
-            if (d < 0.0) {
-              for (int m = 0; m < 4; ++m) b[m] = -b[m];
-              d = -d;
-            }
-            double dm = 0.0, dp = 0.0, v[4], nv = 0.0;
-            for (int m = 0; m < 4; ++m) {
-              dm += (a[m] - b[m]) * (a[m] - b[m]);
-              dp += (a[m] + b[m]) * (a[m] + b[m]);
-              v[m] = b[m] - d * a[m];
-              nv += v[m] * v[m];
-            }
-            const double theta = 2.0 * std::atan2(std::sqrt(dm), std::sqrt(dp));
-            nv = std::sqrt(nv);
-            for (int m = 0; m < 4; ++m) v[m] = nv > 0.0 ? v[m] / nv : 0.0;
-            double q0[4], qp[4], tmp[4], ta[3], dt[3], t0f[3], dtf[3];
-            dq_mul(cBp, a, tmp);
-            dq_mul(tmp, qBj, q0);
-            dq_mul(cBp, v, tmp);
-            dq_mul(tmp, qBj, qp);
-            for (int m = 0; m < 3; ++m) {
-              ta[m] = (double)ka[4 + m] - tBp[m];
-              dt[m] = (double)kb[4 + m] - (double)ka[4 + m];
-            }
-            dq_rot(cBp, ta, t0f);
-            dq_rot(cBp, dt, dtf);
-            float4 *r = &rec[((((size_t)c * nk + k) * S + st) * 4) * P + p];
-            r[0] = make_float4((float)q0[0], (float)q0[1], (float)q0[2], (float)q0[3]);
-            r[P] = make_float4((float)qp[0], (float)qp[1], (float)qp[2], (float)qp[3]);
-            r[2 * P] = make_float4((float)t0f[0], (float)t0f[1], (float)t0f[2], (float)theta);
-            r[3 * P] = make_float4((float)dtf[0], (float)dtf[1], (float)dtf[2], 0.f);
+    std::vector<float4> frec((size_t)nc * nk * n * 4), fu((size_t)n);
+    for (int j = 0; j < n; ++j) {
+      const int pj = parent[j];
+      const double *qBj = &bind_q[4 * j], *tBj = &bind_t[3 * j];
+      const double *qBp = pj >= 0 ? &bind_q[4 * pj] : ident, *tBp = pj >= 0 ? &bind_t[3 * pj] : zero;
+      double cBp[4], cBj[4], uj[3];
+      dq_conj(qBp, cBp);
+      dq_conj(qBj, cBj);
+      dq_rot(cBj, tBj, uj);
+      fu[j] = make_float4((float)uj[0], (float)uj[1], (float)uj[2], 0.f);
+      for (int c = 0; c < nc; ++c)
+        for (int k = 0; k < nk; ++k) {
+          const int k1 = k + 1 == nk ? 0 : k + 1;
+          const float *ka = &keys_h[(((size_t)c * nk + k) * n + j) * 8];
+          const float *kb = &keys_h[(((size_t)c * nk + k1) * n + j) * 8];
+          double a[4], b[4];
+          for (int m = 0; m < 4; ++m) {
+            a[m] = ka[m];
+            b[m] = kb[m];
           }
-      }
-    cudaError_t e = cudaMalloc(&d_wkeys, rec.size() * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&d_wu, u.size() * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMemcpy(d_wkeys, rec.data(), rec.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_wu, u.data(), u.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      if (d_wkeys) cudaFree(d_wkeys);
-      if (d_wu) cudaFree(d_wu);
-      d_wkeys = nullptr;
-      d_wu = nullptr;
+          dq_normalize(a);
+          dq_normalize(b);
+          double d = a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
+          if (d < 0.0) {
+            for (int m = 0; m < 4; ++m) b[m] = -b[m];
+            d = -d;
+          }
+          double dm = 0.0, dp = 0.0, v[4], nv = 0.0;
+          for (int m = 0; m < 4; ++m) {
+            dm += (a[m] - b[m]) * (a[m] - b[m]);
+            dp += (a[m] + b[m]) * (a[m] + b[m]);
+            v[m] = b[m] - d * a[m];
+            nv += v[m] * v[m];
+          }
+          const double theta = 2.0 * std::atan2(std::sqrt(dm), std::sqrt(dp));
+          nv = std::sqrt(nv);
+          for (int m = 0; m < 4; ++m) v[m] = nv > 0.0 ? v[m] / nv : 0.0;
+          double q0[4], qp[4], tmp[4], ta[3], dt[3], t0f[3], dtf[3];
+          dq_mul(cBp, a, tmp);
+          dq_mul(tmp, qBj, q0);
+          dq_mul(cBp, v, tmp);
+          dq_mul(tmp, qBj, qp);
+          for (int m = 0; m < 3; ++m) {
+            ta[m] = (double)ka[4 + m] - tBp[m];
+            dt[m] = (double)kb[4 + m] - (double)ka[4 + m];
+          }
+          dq_rot(cBp, ta, t0f);
+          dq_rot(cBp, dt, dtf);
+          float4 *r = &frec[(((size_t)c * nk + k) * n + j) * 4];
+          r[0] = make_float4((float)q0[0], (float)q0[1], (float)q0[2], (float)q0[3]);
+          r[1] = make_float4((float)qp[0], (float)qp[1], (float)qp[2], (float)qp[3]);
+          r[2] = make_float4((float)t0f[0], (float)t0f[1], (float)t0f[2], (float)theta);
+          r[3] = make_float4((float)dtf[0], (float)dtf[1], (float)dtf[2], 0.f);
+        }
     }
+    std::vector<std::pair<float4 **, const std::vector<float4> *>> up;
+    std::vector<float4> wrec, wu;
+    {  // the records in the walk schedule's order
+      const int P = ws.P, S = ws.S;
+      wrec.assign((size_t)nc * nk * S * 4 * P, make_float4(0.f, 0.f, 0.f, 0.f));
+      wu.assign((size_t)S * P, make_float4(0.f, 0.f, 0.f, 0.f));
+      for (int st = 0; st < S; ++st)
+        for (int p = 0; p < P; ++p) {
+          const uint32_t e = ws.tab[(size_t)st * P + p];
+          if (e == kWInvalid) continue;
+          const int j = (int)(e & kWJoint);
+          wu[(size_t)st * P + p] = fu[j];
+          for (int c = 0; c < nc; ++c)
+            for (int k = 0; k < nk; ++k)
+              for (int f = 0; f < 4; ++f)
+                wrec[((((size_t)c * nk + k) * S + st) * 4 + f) * P + p] = frec[(((size_t)c * nk + k) * n + j) * 4 + f];
+        }
+      up.push_back({&d_wkeys, &wrec});
+      up.push_back({&d_wu, &wu});
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto &u : up) {
+      if (e == cudaSuccess) e = cudaMalloc(u.first, u.second->size() * sizeof(float4));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(*u.first, u.second->data(), u.second->size() * sizeof(float4), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess)
+      for (float4 **p : {&d_wkeys, &d_wu}) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+      }
     sync_dev();
     return e;
   }

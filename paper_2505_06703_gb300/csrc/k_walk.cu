@@ -103,45 +103,6 @@ __device__ __forceinline__ void rec_sample(const float4 *r, int P, float al, flo
   t = make_float3(fmaf(al, dt.x, t0.x), fmaf(al, dt.y, t0.y), fmaf(al, dt.z, t0.z));
 }
 
-// atan2(y, x) for y, x >= 0 (the first quadrant), branch-free: with
-// t = min / max in [0, 1], atan(t) = t P(t^2) for a degree-7 polynomial P
-// fitted here to minimize the maximum error on [0, 1] (Lawson's iteratively
-// reweighted least squares on Chebyshev points; approximation error 4e-8,
-// about 1.3e-7 rad with float evaluation), then pi/2 - atan(t) when y > x.
-// Straight-line code, so the compiler can interleave several samples.
-__device__ __forceinline__ float atan2_q1(const float y, const float x) {
-  const float lo = fminf(x, y), hi = fmaxf(fmaxf(x, y), 1e-30f);
-  const float t = __fdividef(lo, hi), u = t * t;
-  float p = -0.004054560791701078f;
-  p = fmaf(p, u, 0.0218629352748394f);
-  p = fmaf(p, u, -0.05591229721903801f);
-  p = fmaf(p, u, 0.09642194956541061f);
-  p = fmaf(p, u, -0.1390862911939621f);
-  p = fmaf(p, u, 0.19946566224098206f);
-  p = fmaf(p, u, -0.33329859375953674f);
-  p = fmaf(p, u, 0.9999993443489075f);
-  const float a = t * p;
-  return y > x ? 1.5707963267948966f - a : a;
-}
-
-// Slerp on the shorter arc between unit quaternions a and b at weight w:
-// with d = a.b, v = sign(d) b - |d| a (orthogonal to a, |v| = sin(theta)),
-// theta = atan2(|v|, |d|), the result is cos(w theta) a + sin(w theta) v/|v|.
-// For v = 0 (equal rotations) theta = 0 and the result is a.
-__device__ __forceinline__ float4 blend_unit(const float4 a, const float4 b, const float w) {
-  const float d = dot4(a, b);
-  const float sg = d < 0.f ? -1.f : 1.f, x = fabsf(d);
-  const float4 v = make_float4(fmaf(sg, b.x, -x * a.x), fmaf(sg, b.y, -x * a.y), fmaf(sg, b.z, -x * a.z),
-                               fmaf(sg, b.w, -x * a.w));
-  const float vv = fmaxf(dot4(v, v), 1e-36f);
-  const float rs = rsqrtf(vv);
-  const float th = atan2_q1(vv * rs, x);
-  float s, c;
-  __sincosf(w * th, &s, &c);
-  const float k = s * rs;
-  return make_float4(fmaf(c, a.x, k * v.x), fmaf(c, a.y, k * v.y), fmaf(c, a.z, k * v.z), fmaf(c, a.w, k * v.w));
-}
-
 // L' = [R(q) | t + R(q) u] for a unit quaternion q.
 __device__ __forceinline__ Aff local_skin(const float4 q, const float3 t, const float4 u) {
   Aff L = aff_from_qt(q, 0.f, 0.f, 0.f);
