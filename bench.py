@@ -656,6 +656,7 @@ def run_ik(device, dev, world, peak, schedule=None) -> dict:
     ms = aggregate_max(time_events(lambda s: graph.replay(), reps, 1), world)
     ms_step = ms / (reps * n_steps)
     e_mean, e_max = eff_err()
+    q_final = q.cpu().numpy()  # the final pose of the timed run, for the FP64 comparison
     q.copy_(q0)
     e0_mean, _ = eff_err()
     alg = active * 108 + plan.n_chars * eff.shape[1] * 12
@@ -668,6 +669,7 @@ def run_ik(device, dev, world, peak, schedule=None) -> dict:
             "adam_state": "the IK object's own (active joints only, contiguous)",
             "effector_error": {"start_mean": e0_mean, "final_mean": e_mean, "final_max": e_max,
                                "note": "distance to targets (skeletons of unit extent)"},
+            "_q_final": q_final,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes_per_step": alg,
                          "note": "108 B per active joint (q, t, m, v in; q, m, v out) + targets"}}
@@ -873,6 +875,41 @@ def oracle_all_cores(reps: int, warm: int = 1, workers: int | None = None) -> tu
     return dt, n
 
 
+def ik_vs_oracle(q_gpu) -> dict:
+    """The FP64 oracle's run of the same IK schedule (config 5: 8,192
+    characters, 200 Adam steps, every host core) and the agreement of the
+    GPU run's final effector positions with it (each side with its own
+    targets); also the oracle's rate on this workload."""
+    import oracle
+    w = synth.config5()
+    types, ct, eff = w["types"], w["char_type"], w["effectors"]
+    tg = oracle.ik_targets(w)
+    t0 = time.perf_counter()
+    q_ref, _, procs = oracle.ik_all_cores(types, ct, w["t"], w["q0"], eff, tg, int(w["n_steps"]), lr=w["lr"],
+                                          betas=w["betas"], eps=w["eps"])
+    dt = time.perf_counter() - t0
+    off = oracle.offsets(ct, types)
+    rows = (off[:-1, None] + eff[ct]).ravel()
+    pe = []
+    for q in (np.asarray(q_gpu, np.float64), q_ref):
+        _, M = oracle.forward_qt(types, ct, q, w["t"], with_skin=False)
+        pe.append(M[rows, :, 3].reshape(len(ct), -1, 3))
+    err_g = np.linalg.norm(pe[0] - tg, axis=-1)
+    err_r = np.linalg.norm(pe[1] - tg, axis=-1)
+    d = np.linalg.norm(pe[0] - pe[1], axis=-1)
+    joints = int(off[-1])
+    return {"final_mean_gpu": float(err_g.mean()), "final_max_gpu": float(err_g.max()),
+            "final_mean_oracle": float(err_r.mean()), "final_max_oracle": float(err_r.max()),
+            "max_abs_effector_diff": float(np.abs(pe[0] - pe[1]).max()),
+            "frac_effectors_within_1pct": float((d <= 1e-2).mean()), "effectors": int(d.size),
+            "bar": "mean and max remaining error within 25% of the FP64 run's, >= 99.5% of effectors within 1e-2 "
+                   "(1% of the unit extent) of their FP64 positions",
+            "oracle": {"seconds": dt, "cores": procs, "steps_per_s": int(w["n_steps"]) / dt,
+                       "joint_steps_per_s": joints * int(w["n_steps"]) / dt, "kind": "oracle", "cpu": cpu_model(),
+                       "sample": f"the whole run: {len(ct):,} characters x {int(w['n_steps'])} Adam steps, FP64, "
+                                 f"characters split over {procs} processes (full trees each step)"}}
+
+
 def cpu_baseline(min_seconds: float = 6.0) -> dict:
     """The FP64 oracle as it stands on the full frame: on every host core (one
     process per core, each on its share of the characters) and on one host
@@ -952,6 +989,7 @@ def run_only(args) -> dict:
     else:
         fn = {"mixed": run_mixed_frame, "ik": run_ik, "skinned": run_skinned_frame, "layers": run_layered_frame}
         res = fn[args.only](local, dev, world, peak, schedule=sched)
+        res.pop("_q_final", None)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -977,6 +1015,7 @@ def summary(r: dict) -> dict:
     if isinstance(ik, dict) and isinstance(ik.get("vs_oracle"), dict):
         v = ik["vs_oracle"]
         out["ik_max_dev_from_oracle"] = v.get("max_abs_effector_diff")
+        out["ik_frac_within_1pct"] = v.get("frac_effectors_within_1pct")
         out["ik_final_err_gpu"] = v.get("final_mean_gpu")
         out["ik_final_err_oracle"] = v.get("final_mean_oracle")
     return {k: (round(v, 6) if isinstance(v, float) else v) for k, v in out.items()}
@@ -1019,9 +1058,12 @@ def main():
         return
     world, rank, _ = dist_env()
     r = run_ours(args)
+    q_ik = r.get("ik", {}).pop("_q_final", None) if isinstance(r.get("ik"), dict) else None
     if rank == 0:
         if world == 1 and not args.no_cpu:
             r["cpu_baseline"] = cpu_baseline()
+            if q_ik is not None:  # the oracle's IK run, part of the CPU-baseline leg
+                r["ik"]["vs_oracle"] = ik_vs_oracle(q_ik)
         add_nominal_fractions(r)
         r["summary"] = summary(r)  # last, so that the end of the line carries it
         print(json.dumps(r))

@@ -28,7 +28,8 @@ Functions and the passages they follow (paper section, equation):
     gradient of a position loss, pinned against central finite
     differences and a single-joint closed form.
   * adam / ik             -- Adam as PyTorch defines it (pinned against
-    torch.optim.Adam in fp64) and batched IK.
+    torch.optim.Adam in fp64) and batched IK; ik_all_cores runs ik on
+    shares of the characters in parallel processes (same arithmetic).
 """
 from __future__ import annotations
 
@@ -273,6 +274,40 @@ def ik(types, char_type, t, q0, effectors, targets, n_steps, lr=1e-2, betas=(0.9
                          float(lr), float(betas[0]), float(betas[1]), float(eps), _p(q, c_double),
                          _p(hist, c_double)), "ik")
     return q, hist
+
+
+def _ik_share(task):
+    """One process of ik_all_cores: oracle.ik on a contiguous share of the
+    characters (the characters are independent problems)."""
+    types, ct, t, q0, eff, tg, n_steps, lr, betas, eps = task
+    return ik(types, ct, t, q0, eff, tg, n_steps, lr, betas, eps)
+
+
+def ik_all_cores(types, char_type, t, q0, effectors, targets, n_steps, lr=1e-2, betas=(0.9, 0.999), eps=1e-8,
+                 workers: int | None = None):
+    """oracle.ik with the characters split into contiguous shares, one per
+    process (started with spawn, so none forks after CUDA has started).
+    Returns (q_final [sum][4] fp64, loss history [n_steps] summed over the
+    shares, processes used)."""
+    import multiprocessing as mp
+    ct = _i32(char_type)
+    if workers is None:
+        try:
+            workers = len(os.sched_getaffinity(0))
+        except (AttributeError, OSError):
+            workers = os.cpu_count() or 1
+    workers = max(1, min(workers, len(ct)))
+    off = offsets(ct, types)
+    t, q0, tg = _f64(t), _f64(q0), _f64(targets).reshape(len(ct), -1, 3)
+    tasks = []
+    for idx in np.array_split(np.arange(len(ct)), workers):
+        if len(idx) == 0:
+            continue
+        r0, r1 = int(off[idx[0]]), int(off[idx[-1] + 1])
+        tasks.append((types, ct[idx], t[r0:r1], q0[r0:r1], effectors, tg[idx], n_steps, lr, betas, eps))
+    with mp.get_context("spawn").Pool(len(tasks)) as pool:
+        res = pool.map(_ik_share, tasks)
+    return np.concatenate([r[0] for r in res]), np.sum([r[1] for r in res], axis=0), len(tasks)
 
 
 def ik_targets(w: dict) -> np.ndarray:
