@@ -48,10 +48,9 @@ struct TypeDev {
   // Chain-walk frame kernel (k_walk): a static lane schedule of wk_S steps
   // for wk_P lanes per character, staged in chunks of wk_K steps (the table
   // is padded with idle entries to whole chunks); entry [s][slot] names the
-  // joint lane `slot` composes at step s (kWInvalid: idle).  wk_mode 1: natural chains walked parent-first,
-  // branch-point matrices passed through shared memory; wk_mode 2: a pure
-  // chain cut into wk_P pieces joined by a warp-shuffle scan; 0: the type
-  // runs on the segmented CTA kernels only.
+  // joint lane `slot` composes at step s (kWInvalid: idle).  wk_mode 1:
+  // natural chains walked parent-first, branch-point matrices passed through
+  // shared memory; 0: the type runs on the segmented CTA kernels only.
   int wk_mode, wk_P, wk_logP, wk_S;
   int wk_nbs;                // branch-point slots per character (mode 1)
   int wk_K;

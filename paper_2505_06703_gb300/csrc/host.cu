@@ -132,7 +132,9 @@ int default_seg_len(int) { return 16; }
 // longest path to a leaf; a chain is ready one step after its link joint
 // was composed.  Joints that chains hang from keep their model pose in a
 // branch slot from their step to the last start that reads it (slots reused
-// by interval colouring).  mode 2: a pure chain cut into P pieces.
+// by interval colouring).  A pure chain longer than kWalkMaxSteps is not
+// walked (its one dependent path would take that many steps); the segmented
+// kernel's pointer jumping serves it.
 struct WalkSched {
   int mode = 0, P = 0, logP = 0, S = 0, nbs = 0;
   int K = 1;                  // steps per staged chunk
@@ -155,21 +157,6 @@ static int ilog2(int p) {
   int l = 0;
   while ((1 << l) < p) ++l;
   return l;
-}
-
-WalkSched walk_chain(int n, int P) {
-  WalkSched W;
-  W.mode = 2;
-  W.P = P;
-  W.logP = ilog2(P);
-  const int L = (n + P - 1) / P;
-  W.S = L;
-  W.tab.assign((size_t)L * P, kWInvalid);
-  for (int l = 0; l < P; ++l) {
-    const int a0 = l * L, a1 = std::min(n, a0 + L);
-    for (int j = a0; j < a1; ++j) W.tab[(size_t)(j - a0) * P + l] = (uint32_t)j;
-  }
-  return W;
 }
 
 WalkSched walk_tree(const std::vector<int32_t> &par, int P) {
@@ -266,7 +253,6 @@ bool walk_check(const WalkSched &W, const std::vector<int32_t> &par) {
   const int n = (int)par.size();
   if (W.mode == 0 || W.P < 1 || W.P > 32 || (W.P & (W.P - 1)) || W.S < 1) return false;
   std::vector<int> seen(n, 0), done_step(n, -1), lane_at(n, -1), owner(std::max(W.nbs, 1), -1);
-  const int L = W.S;  // mode 2: piece length
   for (int s = 0; s < W.S; ++s) {
     std::vector<int> read_slot, write_slot;
     for (int l = 0; l < W.P; ++l) {
@@ -276,10 +262,6 @@ bool walk_check(const WalkSched &W, const std::vector<int32_t> &par) {
       if (j >= n || seen[j]++) return false;
       done_step[j] = s;
       lane_at[j] = l;
-      if (W.mode == 2) {
-        if (j != l * L + s) return false;  // piece l = joints [l L, l L + L) in lane order
-        continue;
-      }
       if (e & kWStart) {
         const uint32_t ls = (e >> kWLoadShift) & 0xFFu;
         if (par[j] < 0) {
@@ -304,29 +286,16 @@ bool walk_check(const WalkSched &W, const std::vector<int32_t> &par) {
   }
   for (int j = 0; j < n; ++j)
     if (seen[j] != 1) return false;
-  if (W.mode == 2)
-    for (int j = 1; j < n; ++j)
-      if (par[j] != j - 1) return false;
   return true;
 }
 
-// Pick the type's walk schedule: a pure chain takes mode 2 beyond
-// kWalkMaxSteps joints; otherwise mode 1 on the lane count whose schedule
+// Pick the type's walk schedule: mode 1 on the lane count whose schedule
 // keeps lanes busiest, preferring fewer steps among counts within 15 % of
 // the best lane utilization.  A type whose best utilization is below 60 %,
-// or whose schedule is longer than kWalkMaxSteps, stays off the walk kernel.
+// or whose schedule is longer than kWalkMaxSteps (a pure chain longer than
+// that among them), stays off the walk kernel.
 WalkSched choose_walk(const std::vector<int32_t> &par) {
   const int n = (int)par.size();
-  bool chain = par[0] < 0;
-  for (int j = 1; j < n && chain; ++j) chain = par[j] == j - 1;
-  if (chain && n > kWalkMaxSteps) {
-    int P = 1;
-    while (P < 32 && n / (2 * P) >= 16) P *= 2;
-    WalkSched W = walk_chain(n, P);
-    if (!walk_check(W, par)) return WalkSched{};
-    walk_pad(W);
-    return W;
-  }
   std::vector<WalkSched> cand;
   double best = 0.0;
   for (int P = 1; P <= 32; P *= 2) {
@@ -2094,27 +2063,64 @@ int anim_tune(anim_ctx *ctx, anim_plan *plan, int which) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  auto run_once = [&]() -> int {
-    if (which == 0) return anim_evaluate_frame(ctx, plan, d_time, d_w, d_out, nullptr);
-    if (which == 1) return anim_forward_local(ctx, plan, d_q, d_t, d_out, nullptr, nullptr);
-    if (which == 3) return anim_evaluate_frame_skinned(ctx, plan, d_time, d_w, nullptr, d_verts, nullptr);
-    if (which == 4) return anim_evaluate_frame_layers(ctx, plan, d_time, d_w, d_w, d_out, nullptr);
-    return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, nullptr);
+  // Candidates are timed the way frames usually run: one call captured in a
+  // CUDA graph on a private stream and the graph launched five times back to
+  // back (a frame whose two kernels fork onto the side stream pays for that
+  // in every graph launch); direct launches if the capture fails.
+  cudaStream_t ts = nullptr;
+  if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    return fail(ctx, ANIM_ECUDA, "tuning stream");
+  }
+  auto run_once = [&](cudaStream_t s) -> int {
+    if (which == 0) return anim_evaluate_frame(ctx, plan, d_time, d_w, d_out, s);
+    if (which == 1) return anim_forward_local(ctx, plan, d_q, d_t, d_out, nullptr, s);
+    if (which == 3) return anim_evaluate_frame_skinned(ctx, plan, d_time, d_w, nullptr, d_verts, s);
+    if (which == 4) return anim_evaluate_frame_layers(ctx, plan, d_time, d_w, d_w, d_out, s);
+    return anim_loss_backward(ctx, plan, d_q, d_t, d_tg, d_gq, d_gt, nullptr, s);
+  };
+  auto time_graph = [&](float *ms) -> bool {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    bool ok = run_once(ts) == ANIM_OK;
+    const cudaError_t ce = cudaStreamEndCapture(ts, &g);
+    ok = ok && ce == cudaSuccess && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    for (int r = 0; r < 2 && ok; ++r) ok = cudaGraphLaunch(ge, ts) == cudaSuccess;
+    cudaEventRecord(e0, ts);
+    for (int r = 0; r < 5 && ok; ++r) ok = cudaGraphLaunch(ge, ts) == cudaSuccess;
+    cudaEventRecord(e1, ts);
+    ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+    if (ok) {
+      cudaEventElapsedTime(ms, e0, e1);
+      *ms /= 5.f;
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();  // a failed capture leaves its error here: do not report it later
+    return ok;
   };
   anim_ctx::TuneChoice best{0, 0, 0, 0, 0, 1e30f};
   for_each_candidate(ctx, which, [&](int seg, int cps, int jpi, int walk, int adj_c) {
     if (apply_choice(ctx, plan, seg, cps, jpi, walk, adj_c) != ANIM_OK) return;  // e.g. does not fit
     bool ok = true;
-    for (int w = 0; w < 2 && ok; ++w) ok = run_once() == ANIM_OK;
-    cudaEventRecord(e0, nullptr);
-    for (int r = 0; r < 5 && ok; ++r) ok = run_once() == ANIM_OK;
-    cudaEventRecord(e1, nullptr);
-    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) return;
+    for (int w = 0; w < 2 && ok; ++w) ok = run_once(ts) == ANIM_OK;  // outside capture: attributes, side stream
+    if (!ok || cudaStreamSynchronize(ts) != cudaSuccess) return;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ms /= 5.f;
+    if (!time_graph(&ms)) {
+      cudaEventRecord(e0, ts);
+      for (int r = 0; r < 5 && ok; ++r) ok = run_once(ts) == ANIM_OK;
+      cudaEventRecord(e1, ts);
+      if (!ok || cudaEventSynchronize(e1) != cudaSuccess) return;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= 5.f;
+    }
     if (ms < best.ms) best = {seg, cps, jpi, walk, adj_c, ms};
   });
+  cudaStreamSynchronize(ts);
+  cudaStreamDestroy(ts);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   release();

@@ -1,7 +1,7 @@
 // Chain-walk frame kernel: Simulation -> Hierarchy-Scan -> Bind MeshPose
 // (Sec. 1 steps 1-3, Eq. 1) walked directly in skin space, for skeleton
 // types whose natural chains can be list-scheduled on a few lanes with few
-// idle steps, and for pure chains.
+// idle steps (long pure chains stay on the segmented kernel).
 //
 // Skin-space walk.  With rigid inverse binds B, the skin matrix of joint j
 // satisfies S_j = M_j B_j = S_p (B_p^-1 L_j B_j) = S_p L'_j (p the parent; a
@@ -21,9 +21,7 @@
 // type's static schedule (host-built) names the joint each slot composes at
 // each step.  A lane keeps S in registers along its natural chain; branch
 // points leave S in a shared-memory slot for the lane that starts a child
-// chain at a later step.  Pure chains (mode 2) are cut into P pieces: pass A
-// forms each piece's product, a warp-shuffle Hillis-Steele scan over the
-// pieces gives each piece's parent transform, pass B walks again from it.
+// chain at a later step.
 //
 // Staging.  The steps are processed in chunks of K = 32 / P (at most 4)
 // steps.  A chunk's key records (both clips), u vectors and schedule entries
@@ -112,20 +110,9 @@ __device__ __forceinline__ Aff local_skin(const float4 q, const float3 t, const 
   return L;
 }
 
-__device__ __forceinline__ Aff shfl_up_aff(const Aff &a, int d, int width) {
-  Aff r;
-  r.r0 = make_float4(__shfl_up_sync(kFull, a.r0.x, d, width), __shfl_up_sync(kFull, a.r0.y, d, width),
-                     __shfl_up_sync(kFull, a.r0.z, d, width), __shfl_up_sync(kFull, a.r0.w, d, width));
-  r.r1 = make_float4(__shfl_up_sync(kFull, a.r1.x, d, width), __shfl_up_sync(kFull, a.r1.y, d, width),
-                     __shfl_up_sync(kFull, a.r1.z, d, width), __shfl_up_sync(kFull, a.r1.w, d, width));
-  r.r2 = make_float4(__shfl_up_sync(kFull, a.r2.x, d, width), __shfl_up_sync(kFull, a.r2.y, d, width),
-                     __shfl_up_sync(kFull, a.r2.z, d, width), __shfl_up_sync(kFull, a.r2.w, d, width));
-  return r;
-}
-
 struct ItemCtx {
   int P, logP, S, nk, k0, slot, c, count;
-  bool act, two, tree;
+  bool act, two;
   float al, w;
   float4 *out;     // the lane's character's skin rows
   float4 *bslots;  // the lane's character's branch slots [nbs][3]
@@ -152,14 +139,12 @@ __device__ __forceinline__ void issue_chunk(const ItemCtx &x, int ch, unsigned c
   bulk_g2s(stage + kTabOff, x.tab + ustep, tb, bar);
 }
 
-// One staged chunk.  KIND 0: tree walk (branch slots, stores); KIND 1: the
-// product of a chain piece only; KIND 2: a chain piece walked from its parent
-// transform, with stores.  S carries the lane's running skin matrix.
+// One staged chunk of the walk.  S carries the lane's running skin matrix.
 // The local transforms of all K steps are formed first, without branches
 // (steps past the end of a short last chunk compute unused values from
 // whatever the buffer holds), so their latencies overlap; the walk itself is
 // then one 3x4 product per step.
-template <int K, int KIND>
+template <int K>
 __device__ __forceinline__ void walk_chunk(const ItemCtx &x, const unsigned char *stage, Aff &S) {
   const float4 *ra = reinterpret_cast<const float4 *>(stage) + x.slot;
   const float4 *rb = reinterpret_cast<const float4 *>(stage + kRecBytes) + x.slot;
@@ -186,30 +171,29 @@ __device__ __forceinline__ void walk_chunk(const ItemCtx &x, const unsigned char
     const uint32_t e = ts[k * P];  // idle entries past the schedule's end
     const bool valid = x.act && e != kWInvalid;
     Aff Sp = S;
-    if (KIND == 0 && valid && (e & kWStart)) {
+    if (valid && (e & kWStart)) {
       const uint32_t ls = (e >> kWLoadShift) & 0xFFu;
       Sp = ls == kWRootSlot ? aff_identity() : lds_aff(x.bslots + 3 * ls);
     }
     const Aff Sn = aff_mul(Sp, L[k]);
     if (valid) {
       S = Sn;
-      if (KIND == 0 && (e & kWStore)) sts_aff(x.bslots + 3 * ((e >> kWStoreShift) & 0xFFu), Sn);
-      if (KIND != 1) stg_aff(x.out + 3 * (e & kWJoint), Sn);
+      if (e & kWStore) sts_aff(x.bslots + 3 * ((e >> kWStoreShift) & 0xFFu), Sn);
+      stg_aff(x.out + 3 * (e & kWJoint), Sn);
     }
-    if (KIND == 0) __syncwarp();  // branch slots written at this step are read at later steps
+    __syncwarp();  // branch slots written at this step are read at later steps
   }
 }
 
-// The whole item: the chunk sequence (once for a tree, twice for a chain
-// split), up to kStages chunks staged ahead of the compute.  Returns false if
-// a chunk never arrived (its wait ran out).
+// The whole item: the chunk sequence, up to kStages chunks staged ahead of
+// the compute.  Returns false if a chunk never arrived (its wait ran out).
 template <int K>
 __device__ bool walk_item(const ItemCtx &x, unsigned char *stage, uint64_t *bars, uint32_t &parity,
                           uint32_t &inflight) {
   const int lane = threadIdx.x;
-  const int nch = (x.S + K - 1) / K, nq = x.tree ? nch : 2 * nch;
+  const int nch = (x.S + K - 1) / K, nq = nch;
   for (int b = 0; b < kStages && b < nq; ++b) {
-    if (lane == 0) issue_chunk<K>(x, b % nch, stage + b * kChunkBytes, &bars[b]);
+    if (lane == 0) issue_chunk<K>(x, b, stage + b * kChunkBytes, &bars[b]);
     inflight |= 1u << b;  // buffers with a copy issued and not yet waited for
   }
   Aff S = aff_identity();
@@ -219,27 +203,10 @@ __device__ bool walk_item(const ItemCtx &x, unsigned char *stage, uint64_t *bars
     parity ^= 1u << buf;
     inflight &= ~(1u << buf);
     const unsigned char *st = stage + buf * kChunkBytes;
-    if (x.tree) {
-      walk_chunk<K, 0>(x, st, S);
-    } else if (q < nch) {
-      walk_chunk<K, 1>(x, st, S);
-    } else {
-      if (q == nch) {
-        // S holds this piece's product: inclusive scan over the character's
-        // P pieces, shifted by one, gives the transform the piece hangs from
-        const int slot = x.slot;
-        for (int d = 1; d < x.P; d <<= 1) {
-          const Aff X = shfl_up_aff(S, d, x.P);
-          if (slot >= d) S = aff_mul(X, S);
-        }
-        const Aff M0 = shfl_up_aff(S, 1, x.P);
-        S = slot == 0 ? aff_identity() : M0;
-      }
-      walk_chunk<K, 2>(x, st, S);
-    }
+    walk_chunk<K>(x, st, S);
     __syncwarp();
     if (q + kStages < nq) {
-      if (lane == 0) issue_chunk<K>(x, (q + kStages) % nch, stage + buf * kChunkBytes, &bars[buf]);
+      if (lane == 0) issue_chunk<K>(x, q + kStages, stage + buf * kChunkBytes, &bars[buf]);
       inflight |= 1u << buf;
     }
   }
@@ -269,7 +236,6 @@ __global__ void __launch_bounds__(32, 12) k_walk(const WalkArgs a) {
   x.nk = T.n_keys;
   x.k0 = wi.k0;
   x.two = T.n_clips >= 2;
-  x.tree = T.wk_mode == 1;
   x.c = lane >> x.logP;
   x.slot = lane & (x.P - 1);
   x.count = wi.count;
