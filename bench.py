@@ -54,7 +54,7 @@ L2_BYTES = 129 * 1024 * 1024
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources it was taken on (comments and whitespace aside); reported
 # as null once the code changes.
-NCU_TRAFFIC = {"4165125c1ebdc126": 1353984 + 40237056}
+NCU_TRAFFIC = {"0684181190987b7f": 1361152 + 38773248}
 
 
 # ------------------------------------------------------------------ helpers
@@ -431,12 +431,12 @@ def run_ours(args) -> dict:
     return result
 
 
-def run_mixed_frame(device, dev, world, peak, schedule=None) -> dict:
+def run_mixed_frame(device, dev, world, peak, schedule=None, workload=None) -> dict:
     """Batched heterogeneous frame (10,000 characters of 5 types, 32 to 2,048
     joints, depths 8 to 2,048): the autotuned schedule, frames replayed from
     one CUDA graph with outputs rotated over buffers larger than L2."""
     import torch
-    w = synth.config3()
+    w = workload if workload is not None else synth.config3()
     ctx, plan = setup_ctx(w, device)
     set_or_tune(ctx, plan, schedule, 0)
     joints = plan.total
@@ -459,13 +459,38 @@ def run_mixed_frame(device, dev, world, peak, schedule=None) -> dict:
     ms_step = ms / (reps * n_out)
     alg = frame_algorithmic_bytes(w)
     achieved = alg / (ms_step / 1e3) / 1e9
-    return {"value": world * joints / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step,
+    return {"value": world * joints / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step, "joints": joints,
             "workload": "frame: 10,000 chars of 32/128/512/1,024/2,048-joint types (depths 8/16/70/256/2,048) "
                         "at 40/30/15/10/5 %, shuffled",
             "schedule": ctx.get_schedule(plan),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes": alg,
                          "note": "whole frame (work queue + kernels), frames back to back in one CUDA graph"}}
+
+
+def run_mixed_split(device, dev, world, peak, schedule=None) -> dict:
+    """The heterogeneous frame (config 3) type by type: the frame restricted
+    to each type's characters, under the schedule the autotuner picks for the
+    whole mix (or the given one), timed like run_mixed_frame; beside the whole
+    mix.  Shows where the mixed frame's time goes."""
+    import torch
+    w = synth.config3()
+    ctx, plan = setup_ctx(w, device)
+    set_or_tune(ctx, plan, schedule, 0)
+    sched = ctx.get_schedule(plan)
+    out = {"schedule": sched, "types": []}
+    for ty in list(range(len(w["types"]))) + [None]:
+        chars = np.nonzero(w["char_type"] == ty)[0] if ty is not None else np.arange(len(w["char_type"]))
+        ws = synth.subset(w, chars)
+        r = run_mixed_frame(device, dev, world, peak, schedule=sched, workload=ws)
+        ent = {"ms_per_step": r["ms_per_step"], "joints": int(r["joints"]), "frac": r["roofline"]["frac"]}
+        if ty is None:
+            out["whole_mix"] = ent
+        else:
+            ty_d = w["types"][ty]
+            ent.update({"type_joints": len(ty_d["parents"]), "depth": int(ty_d["depth"]), "characters": len(chars)})
+            out["types"].append(ent)
+    return out
 
 
 def run_skinned_frame(device, dev, world, peak, schedule=None) -> dict:
@@ -987,7 +1012,8 @@ def run_only(args) -> dict:
     if args.only == "forward":
         res = time_forward_methods(rank_workload(rank), local, dev, world, algs=(), schedule=sched)
     else:
-        fn = {"mixed": run_mixed_frame, "ik": run_ik, "skinned": run_skinned_frame, "layers": run_layered_frame}
+        fn = {"mixed": run_mixed_frame, "mixed_split": run_mixed_split, "ik": run_ik, "skinned": run_skinned_frame,
+              "layers": run_layered_frame}
         res = fn[args.only](local, dev, world, peak, schedule=sched)
         res.pop("_q_final", None)
     if world > 1:
@@ -1032,7 +1058,7 @@ def main():
     ap.add_argument("--schedule", default="", help="seg_len,ctas_per_sm,joints_per_item,walk[,adj_ctas] for the frame "
                                                    "instead of running the autotuner")
     ap.add_argument("--schedule-bwd", default="", help="the same for the forward+adjoint measurement")
-    ap.add_argument("--only", choices=["mixed", "ik", "skinned", "layers", "forward"], default="",
+    ap.add_argument("--only", choices=["mixed", "mixed_split", "ik", "skinned", "layers", "forward"], default="",
                     help="run one of the extra workloads alone (under --schedule if given, else autotuned) and "
                          "print its result object; a short command for profiling its kernel")
     ap.add_argument("--paper-sweep", action="store_true",

@@ -27,9 +27,9 @@
 // steps.  A chunk's key records (both clips), u vectors and schedule entries
 // are contiguous in schedule order in global memory; lane 0 copies them into
 // a ring of shared-memory buffers with cp.async.bulk (TMA, 1-D), each
-// completing on its own mbarrier, several chunks ahead of the compute.  Within a chunk each lane
-// first samples its K local poses (independent work, so the latency of the
-// trigonometry overlaps), then walks the K steps.
+// completing on its own mbarrier, several chunks ahead of the compute.
+// Within a chunk each lane first forms its K local transforms (independent
+// work, so the latency of the trigonometry overlaps), then walks the K steps.
 #include <cuda_runtime.h>
 
 #include "anim_internal.h"
@@ -40,7 +40,6 @@ namespace anim {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before a chunk counts as lost
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
