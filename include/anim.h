@@ -175,10 +175,15 @@ ANIM_API int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const flo
  * are copied back into h_skin (host [total][12] float), all in order on
  * `stream`; the output is complete once `stream` has synchronized.
  * Page-locked buffers (cudaMallocHost, cudaHostRegister) make the copies
- * asynchronous; pageable ones work through the driver's staging.  The device
- * staging buffers (n_chars x 8 B + total x 48 B) belong to the plan and are
- * allocated by the first call, which is therefore not capturable in a CUDA
- * graph; later calls are. */
+ * asynchronous; pageable ones work through the driver's staging.  A plan of
+ * at least 1,024 characters is evaluated in up to 4 contiguous ranges of
+ * nearly equal joint counts, each range's skin matrices copied back on a
+ * second stream of the plan while the next range's frame runs (the call's
+ * `stream` waits for those copies, so the rule above holds).  The device
+ * staging buffers (n_chars x 8 B + total x 48 B), the ranges' own plans, the
+ * copy stream and its events belong to the plan and are created by the
+ * first call, which is therefore not capturable in a CUDA graph; later calls
+ * with page-locked buffers are. */
 ANIM_API int anim_evaluate_frame_host(anim_ctx *ctx, anim_plan *plan, const float *h_time, const float *h_blend_w,
                              float *h_skin, void *stream);
 

@@ -804,7 +804,19 @@ struct anim_plan {
   std::vector<int64_t> vert_off;  // [n_chars + 1]
   int64_t *d_vert_off = nullptr;
   float *d_host_in = nullptr, *d_host_skin = nullptr;  // staging of the host-buffer frame
+  // host-buffer frame: the characters in contiguous ranges, each a plan of its
+  // own (registered with the context, destroyed with this plan), so that a
+  // range's copy-out on copy_stream overlaps the next range's frame
+  std::vector<anim_plan *> host_parts;
+  std::vector<int64_t> part_char0;  // first character of each range, then n_chars
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> part_ev;  // range i's frame done (on the call's stream)
+  cudaEvent_t copy_ev = nullptr;     // every copy-out issued so far done (on copy_stream)
   ~anim_plan() {
+    for (cudaEvent_t e : part_ev)
+      if (e) cudaEventDestroy(e);
+    if (copy_ev) cudaEventDestroy(copy_ev);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
     for (void *p : {(void *)d_char_type, (void *)d_row_off, (void *)d_type_chars, (void *)d_items_scan,
                     (void *)d_items_adj, (void *)d_sorted, (void *)d_items_frame, (void *)d_ranges,
                     (void *)d_queue, (void *)d_used,
@@ -1419,6 +1431,8 @@ int anim_plan_create(anim_ctx *ctx, int64_t n_chars, const int32_t *char_type, a
 
 int anim_plan_destroy(anim_ctx *ctx, anim_plan *plan) {
   if (!ctx || !plan || !ctx->plans.count(plan)) return ctx ? fail(ctx, ANIM_EINVAL, "unknown plan") : ANIM_EINVAL;
+  for (anim_plan *part : plan->host_parts) anim_plan_destroy(ctx, part);
+  plan->host_parts.clear();
   for (auto it = ctx->iks.begin(); it != ctx->iks.end();) {
     if ((*it)->plan == plan) {
       delete *it;
@@ -1556,6 +1570,40 @@ int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_tim
   return anim_frame_run_queue(ctx, plan, d_time, d_blend_w, d_skin, stream);
 }
 
+// Ranges of the host-buffer frame: up to kHostParts of nearly equal joint
+// counts, for plans of at least kHostPartMinChars characters.
+constexpr int kHostParts = 4;
+constexpr int64_t kHostPartMinChars = 1024;
+
+static int make_host_parts(anim_ctx *ctx, anim_plan *plan) {
+  const int64_t N = plan->n_chars, total = plan->total;
+  std::vector<int64_t> cut = {0};
+  for (int k = 1; k < kHostParts; ++k) {
+    const int64_t target = total * k / kHostParts;
+    int64_t c = cut.back();
+    while (c < N && plan->row_off[c] < target) ++c;
+    if (c > cut.back() && c < N) cut.push_back(c);
+  }
+  cut.push_back(N);
+  std::vector<anim_plan *> parts;
+  for (size_t i = 0; i + 1 < cut.size(); ++i) {
+    anim_plan *p = nullptr;
+    const int rc = anim_plan_create(ctx, cut[i + 1] - cut[i], plan->char_type.data() + cut[i], &p);
+    if (rc != ANIM_OK) {
+      for (anim_plan *q : parts) anim_plan_destroy(ctx, q);
+      return rc;
+    }
+    parts.push_back(p);
+  }
+  CK(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&plan->copy_ev, cudaEventDisableTiming));
+  plan->part_ev.assign(parts.size(), nullptr);
+  for (auto &e : plan->part_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  plan->host_parts = std::move(parts);
+  plan->part_char0 = std::move(cut);
+  return ANIM_OK;
+}
+
 int anim_evaluate_frame_host(anim_ctx *ctx, anim_plan *plan, const float *h_time, const float *h_blend_w,
                              float *h_skin, void *stream) {
   int rc = check_plan(ctx, plan);
@@ -1572,14 +1620,37 @@ int anim_evaluate_frame_host(anim_ctx *ctx, anim_plan *plan, const float *h_time
       plan->d_host_skin = nullptr;
       return fail(ctx, ANIM_ECUDA, "%s", cudaGetErrorString(e));
     }
+    if (plan->n_chars >= kHostPartMinChars) {
+      rc = make_host_parts(ctx, plan);
+      if (rc) return rc;
+    }
   }
   cudaStream_t st = (cudaStream_t)stream;
   float *d_time = plan->d_host_in, *d_blend = plan->d_host_in + n_pad;
   CK(cudaMemcpyAsync(d_time, h_time, n * sizeof(float), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_blend, h_blend_w, n * sizeof(float), cudaMemcpyHostToDevice, st));
-  rc = anim_evaluate_frame(ctx, plan, d_time, d_blend, plan->d_host_skin, stream);
-  if (rc) return rc;
-  CK(cudaMemcpyAsync(h_skin, plan->d_host_skin, (size_t)plan->total * 48, cudaMemcpyDeviceToHost, st));
+  if (plan->host_parts.empty()) {
+    rc = anim_evaluate_frame(ctx, plan, d_time, d_blend, plan->d_host_skin, stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h_skin, plan->d_host_skin, (size_t)plan->total * 48, cudaMemcpyDeviceToHost, st));
+    return ANIM_OK;
+  }
+  // range by range: range i's frame on `stream`, then its copy-out on the
+  // copy stream while range i + 1's frame runs; `stream` finally waits for
+  // the copies, so the output is complete when `stream` is
+  for (size_t i = 0; i < plan->host_parts.size(); ++i) {
+    const int64_t c0 = plan->part_char0[i], c1 = plan->part_char0[i + 1];
+    const int64_t r0 = plan->row_off[c0], r1 = plan->row_off[c1];
+    rc = anim_evaluate_frame(ctx, plan->host_parts[i], d_time + c0, d_blend + c0, plan->d_host_skin + r0 * 12,
+                             stream);
+    if (rc) return rc;
+    CK(cudaEventRecord(plan->part_ev[i], st));
+    CK(cudaStreamWaitEvent(plan->copy_stream, plan->part_ev[i], 0));
+    CK(cudaMemcpyAsync(h_skin + r0 * 12, plan->d_host_skin + r0 * 12, (size_t)(r1 - r0) * 48,
+                       cudaMemcpyDeviceToHost, plan->copy_stream));
+  }
+  CK(cudaEventRecord(plan->copy_ev, plan->copy_stream));
+  CK(cudaStreamWaitEvent(st, plan->copy_ev, 0));
   return ANIM_OK;
 }
 
