@@ -35,6 +35,9 @@ struct TypeDev {
   // IK views: the active subtree of a type; view joint j reads row gather[j]
   // of the full type (nullptr = identity).
   const int32_t *gather;
+  // A view that renumbers every joint of its type: the view slot of each of
+  // the type's joints (the inverse of gather), else nullptr.
+  const int32_t *inv_gather;
   // The paper's 64-node blocks (comparator kernels): nearest ancestor of
   // each joint outside its block of 64 consecutive indices, -1 at the top.
   const int32_t *blk_out;

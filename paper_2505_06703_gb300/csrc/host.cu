@@ -423,7 +423,8 @@ struct TypeHost {
   float4 *d_keys = nullptr;
   int n_clips = 0, n_keys = 0;
   float rate = 0.f;
-  std::vector<int32_t> gather;  // IK views only
+  std::vector<int32_t> gather;  // views only
+  std::vector<int32_t> inv_gather;  // views of every joint: type joint -> view joint
   WalkSched ws;                 // chain-walk schedule (mode 0: not walkable)
   bool ws_done = false;
   float4 *d_add = nullptr;      // additive layer keys [n_keys][n][2]
@@ -467,6 +468,7 @@ struct TypeHost {
     const size_t o_sl = B.add(seg.link.data(), seg.link.size() * 4);
     const size_t o_se = B.add(dfsord.sub_end.data(), dfsord.sub_end.size() * 4);
     const size_t o_g = B.add(gather.data(), gather.size() * 4);
+    const size_t o_ig = B.add(inv_gather.data(), inv_gather.size() * 4);
     const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
     const size_t o_wt = B.add(ws.tab.data(), ws.tab.size() * 4);
     std::vector<int32_t> blk_out(n);
@@ -494,6 +496,7 @@ struct TypeHost {
     dev.seg_link = (const int32_t *)(base + o_sl);
     dev.sub_end = (const int32_t *)(base + o_se);
     dev.gather = gather.empty() ? nullptr : (const int32_t *)(base + o_g);
+    dev.inv_gather = inv_gather.empty() ? nullptr : (const int32_t *)(base + o_ig);
     dev.jinfo = (const uint32_t *)(base + o_ji);
     dev.wk_mode = ws.mode;
     dev.wk_P = ws.P;
@@ -732,6 +735,7 @@ std::unique_ptr<TypeHost> make_view(const TypeHost &T, const std::vector<char> &
     for (auto it = k.rbegin(); it != k.rend(); ++it) st.push_back(*it);
   }
   V->n = (int)V->gather.size();
+  if (V->n == n) V->inv_gather.assign(vid.begin(), vid.end());
   for (int j : V->gather) V->parent.push_back(T.parent[j] < 0 ? -1 : vid[T.parent[j]]);
   V->depth = depths_of(V->parent);
   V->max_depth = *std::max_element(V->depth.begin(), V->depth.end());

@@ -135,12 +135,17 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
   // ---- pass 1a: local poses (q normalized, t); the joint's loss input
   // (dLoss/dp or target) is fetched alongside into its depth-first slot
   stage_tables<NT>(b, Lt, tid);
+  // A view of every joint (the loss and backward passes) reads the rows in
+  // the caller's order -- coalesced, and independent of the view table --
+  // and scatters them to their view slots; the IK's partial views gather.
+  const int32_t *inv = MODE < 2 ? b.T.inv_gather : nullptr;
   {
     const float4 *q4 = reinterpret_cast<const float4 *>(a.q);
 #pragma unroll 2
     for (int idx = tid; idx < CN; idx += NT) {
-      const int c = (int)b.divN.div(idx), j = idx - c * n;
-      const long long row = b.off[c] + (gath ? __ldg(gat + j) : j);
+      const int c = (int)b.divN.div(idx), k = idx - c * n;
+      const int j = inv ? __ldg(inv + k) : k;
+      const long long row = b.off[c] + (inv ? k : gath ? __ldg(gat + k) : k);
       const float4 q = normalize4(__ldg(q4 + row));
       const float *tp = a.t + 3 * row;
       sts_qt(P + c * cs2, j, n, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
@@ -220,7 +225,8 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     step_size = a.lr / (1.f - powf(a.beta1, (float)step));
   }
   for (int idx = tid; idx < CN; idx += NT) {
-    const int c = (int)b.divN.div(idx), j = idx - c * n;
+    const int c = (int)b.divN.div(idx), k = idx - c * n;
+    const int j = inv ? __ldg(inv + k) : k;  // in the caller's row order for full views
     const int i = j, e = sub16[j];
     const float4 f0 = PF[c * (n + 1) + i], f1 = PF[c * (n + 1) + e];
     const float4 t0 = PT[c * (n + 1) + i], t1 = PT[c * (n + 1) + e];
@@ -238,7 +244,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       tau = qrot(qc, tw);
       dt = qrot(qc, F);
     }
-    const long long row = b.off[c] + gat16[j];
+    const long long row = b.off[c] + (inv ? k : gat16[j]);
     const float4 q = __ldg(reinterpret_cast<const float4 *>(a.q) + row);
     const float inv = rsqrtf(dot4(q, q));
     const float4 u = make_float4(q.x * inv, q.y * inv, q.z * inv, q.w * inv);
