@@ -324,8 +324,8 @@ ANIM_API int anim_ik_step(anim_ctx *ctx, anim_ik *ik, float *d_q, float *d_m, fl
  * pointer-jumping scan, 1, 2 or 3 resident CTAs per SM of the persistent
  * kernels, work items of about 1,024/2,048/4,096 joints, and for the
  * frame whether walkable types (chain schedules of at most 160 steps with
- * most lanes busy, and pure chains) run on the one-warp chain-walk kernel
- * beside the segmented kernel -- of
+ * most lanes busy) run on one of the two chain-walk kernels beside the
+ * segmented kernel -- of
  * `which` (0 = fused frame, 1 = forward_local, 2 = loss_backward, 3 = frame
  * with skinning, 4 = frame with layered blending) with CUDA events on scratch
  * inputs it allocates, and keeps the fastest.  The result
@@ -349,7 +349,9 @@ ANIM_API int anim_tune_ik(anim_ctx *ctx, anim_plan *plan, int n_eff, const int32
 
 /* The schedule the autotuner picked, as 5 integers: segment length, resident
  * CTAs per SM, work-item size in joints, chain-walk kernel for the frame
- * (0/1), adjoint kernel (0: persistent, k = 1..8: one work item per CTA,
+ * (0: none, 1: one warp per item, 2: three warps per item, two of them
+ * sampling the local transforms and writing the skin rows out, one walking
+ * the chains), adjoint kernel (0: persistent, k = 1..8: one work item per CTA,
  * items sized so k CTAs share an SM) -- read with anim_get_schedule (segment
  * length of the plan's first type) and re-applied without timing by
  * anim_set_schedule (for example in another process); CTAs per SM is 1, 2

@@ -153,7 +153,7 @@ cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s)
 // work items of at most cap[type] characters sharing (type, k0) into its
 // region, then empty items (count 0) into the rest of the region.
 constexpr int kRangeChars = 256;
-constexpr int kRangeCharsMax = 1024;
+constexpr int kRangeCharsMax = 4096;
 constexpr int kMaxRanges = 4096;  // so at most ~900,000 characters per plan
 struct RangeDev {
   int32_t type;
@@ -236,6 +236,16 @@ struct WalkArgs {
   float *skin;
 };
 size_t walk_smem_bytes(int chars_per_item, int nbs);
+// The warp-specialized variant (three warps per item: two sample and write
+// out, one walks), same arguments and tables.
+size_t walk2_smem_bytes(int chars_per_item, int nbs);
+cudaError_t launch_walk2(const WalkArgs &a, size_t smem, cudaStream_t s);
+int walk2_blocks_per_sm(size_t smem);
+// Shared memory per CTA of the warp-specialized walk, padded up from `smem`
+// so that at most ceil(n_items / sm_count) CTAs are resident per SM: the
+// block scheduler then spreads the items evenly instead of stacking one
+// more on some SMs (the frame ends with its most loaded SM).
+size_t walk2_spread_smem(size_t smem, int n_items, int sm_count);
 cudaError_t launch_walk(const WalkArgs &a, size_t smem, cudaStream_t s);
 int walk_blocks_per_sm(size_t smem);  // resident one-warp CTAs per SM at this shared-memory size
 

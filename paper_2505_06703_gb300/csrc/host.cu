@@ -865,7 +865,8 @@ struct anim_ctx {
   int *d_status = nullptr;
   int version = 0;  // bumps when types/schedules change
   int ctas_per_sm = 2;            // resident persistent CTAs per SM the schedule is sized for
-  int use_walk = 1;               // frame: walkable types run on the chain-walk kernel
+  int use_walk = 1;               // frame: walkable types run on the chain-walk kernel (2: its
+                                  // warp-specialized variant)
   int adj_ctas = 0;               // adjoint: 0 = persistent kernel, k = one-item kernel sized for k CTAs per SM
   cudaStream_t side = nullptr;    // frame: the CTA kernel's stream when both kernels have work
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1067,9 +1068,14 @@ int plan_schedule(anim_ctx *ctx, anim_plan *P) {
     }
     if (pass == 0) P->n_slots_walk = slots;
   }
-  P->walk_smem = P->n_slots_walk > 0 ? walk_smem_bytes(wcmax, P->walk_nbs) : 0;
-  if (P->n_slots_walk > 0 && walk_blocks_per_sm(P->walk_smem) < 1)
-    return fail(ctx, ANIM_ECUDA, "chain-walk kernel: no resident CTA at %zu bytes of shared memory", P->walk_smem);
+  const bool walk2 = ctx->use_walk == 2;
+  P->walk_smem = P->n_slots_walk == 0 ? 0 : walk2 ? walk2_smem_bytes(wcmax, P->walk_nbs)
+                                                   : walk_smem_bytes(wcmax, P->walk_nbs);
+  if (walk2 && P->n_slots_walk > 0) P->walk_smem = walk2_spread_smem(P->walk_smem, P->n_slots_walk, ctx->sm_count);
+  if (P->n_slots_walk > 0 &&
+      (walk2 ? walk2_blocks_per_sm(P->walk_smem) : walk_blocks_per_sm(P->walk_smem)) < 1)
+    return fail(ctx, ANIM_EUNSUPPORTED, "chain-walk kernel: no resident CTA at %zu bytes of shared memory",
+                P->walk_smem);
   P->n_ranges = (int)ranges.size();
   P->n_slots = slots;
   CK(upload_vec(&P->d_ranges, ranges));
@@ -1553,7 +1559,10 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
     w.time = d_time;
     w.blend_w = d_blend_w;
     w.skin = d_skin;
-    CK(launch_walk(w, plan->walk_smem, st));
+    if (ctx->use_walk == 2)
+      CK(launch_walk2(w, plan->walk_smem, st));
+    else
+      CK(launch_walk(w, plan->walk_smem, st));
   }
   if (has_walk && has_cta) {
     CK(cudaEventRecord(ctx->ev_join, ctx->side));
@@ -2039,7 +2048,7 @@ static int apply_choice(anim_ctx *ctx, const anim_plan *P, int seg_len, int cps,
                         int adj_ctas) {
   ctx->ctas_per_sm = cps;
   ctx->joints_per_item = jpi;
-  ctx->use_walk = walk != 0;
+  ctx->use_walk = walk;
   ctx->adj_ctas = adj_ctas;
   for (int t : P->used) {
     TypeHost &T = *ctx->types[t];
@@ -2066,7 +2075,7 @@ template <class F>
 static void for_each_candidate(const anim_ctx *ctx, int which, F &&f) {
   const int segs[] = {4, 8, 16, 32}, cpss[] = {1, 2, 3}, jpis[] = {256, 512, 1024, 2048, 4096};
   const int adjs[] = {0, 4, 6, 7, 8};
-  const int walk_lo = which == 0 ? 0 : ctx->use_walk, walk_hi = which == 0 ? 1 : ctx->use_walk;
+  const int walk_lo = which == 0 ? 0 : ctx->use_walk, walk_hi = which == 0 ? 2 : ctx->use_walk;
   const int adj_keep = ctx->adj_ctas;
   for (int walk = walk_lo; walk <= walk_hi; ++walk)
     for (int adj : adjs)
@@ -2295,7 +2304,7 @@ int anim_set_schedule(anim_ctx *ctx, anim_plan *plan, const int32_t *in5) {
   int rc = check_plan(ctx, plan);
   if (rc) return rc;
   if (!in5 || in5[0] < 1 || in5[0] > ANIM_MAX_JOINTS || in5[1] < 1 || in5[1] > 3 || in5[2] < 1 ||
-      (in5[3] != 0 && in5[3] != 1) || in5[4] < 0 || in5[4] > 8)
+      in5[3] < 0 || in5[3] > 2 || in5[4] < 0 || in5[4] > 8)
     return fail(ctx, ANIM_EINVAL, "schedule out of range");
   CK(cudaSetDevice(ctx->device));
   int32_t prev[5];

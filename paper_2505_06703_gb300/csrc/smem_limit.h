@@ -40,6 +40,7 @@ inline cudaError_t ensure_smem_limit(const void *fn, SmemLimit &lim, size_t smem
   if (cached && smem <= lim.set[dev].load(std::memory_order_relaxed)) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess && cached) lim.set[dev].store(smem, std::memory_order_release);
+  if (e != cudaSuccess) cudaGetLastError();  // returned here: do not leave it for a later launch check
   return e;
 }
 

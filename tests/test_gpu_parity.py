@@ -113,7 +113,7 @@ def test_frame_from_host_buffers(torch):
     _gpu.assert_skin_close(out.numpy(), oracle.frame(w), w)
 
 
-@pytest.mark.parametrize("walk", [0, 1])
+@pytest.mark.parametrize("walk", [0, 1, 2])
 def test_back_to_back_frames(torch, walk):
     """Frames enqueued back to back (each work-queue kernel and frame kernel
     launched with programmatic stream serialization after the previous one),
@@ -156,6 +156,23 @@ def test_back_to_back_frames(torch, walk):
     torch.cuda.synchronize()
     for o, r in zip(outs, refs):
         assert torch.equal(o, r)
+
+
+@pytest.mark.parametrize("walk", [1, 2])
+def test_walk_frame_several_ranges(torch, walk):
+    """8,192 characters of config 2's 512-joint type plus the dragon chain: the
+    walk types' work queue cuts them into two ranges of 4,096 characters, each
+    with its own item region.  Sampled characters (both ends of each range
+    among them) equal the oracle's frame."""
+    w = synth.config2(n_chars=8192)
+    ctx, plan = _gpu.setup(w)
+    ctx.set_schedule(plan, [16, 3, 4096, walk, 0])
+    skin = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])).cpu().numpy()
+    assert ctx.status() == 0
+    sel = list(range(0, 8192, 37)) + [4095, 4096, 8191, 8192]
+    ws = synth.subset(w, sel)
+    off = oracle.offsets(w["char_type"], w["types"])
+    _gpu.assert_skin_close(skin[_rows(off, sel)], oracle.frame(ws), ws)
 
 
 @pytest.mark.parametrize("sched", [[16, 3, 2048, 0, 7], [16, 2, 2048, 0, 0]])
@@ -222,7 +239,7 @@ def test_autotuned_frame_parity(torch):
 
 
 @pytest.mark.parametrize("sched", [[2, 1, 1024, 0, 0], [8, 2, 2048, 0, 6], [32, 3, 4096, 0, 4], [16, 2, 2048, 1, 8],
-                                   [16, 3, 1024, 1, 0], [16, 2, 256, 1, 6]])
+                                   [16, 3, 1024, 1, 0], [16, 2, 256, 1, 6], [16, 3, 2048, 2, 0]])
 def test_every_schedule_variant_parity(torch, sched):
     """Each schedule the autotuner may pick (segment length, CTAs per SM --
     3 selects the other compiled kernel variant --, item size, chain-walk
@@ -860,7 +877,7 @@ def test_walk_kernel_bind_sources(torch, bind):
     ref = oracle.bind(M, Bj)
     assert Bj.shape[0] == off[-1]
     import paper_2505_06703_gb300 as pk
-    for walk in (1, 0):
+    for walk in (2, 1, 0):
         ctx = pk.Context(0)
         if bind == "rest":
             ids = ctx.create_skeletons([t["parents"] for t in types], rest_q=[t["rest_q"] for t in types],
