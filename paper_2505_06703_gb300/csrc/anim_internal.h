@@ -153,7 +153,7 @@ cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t s)
 // work items of at most cap[type] characters sharing (type, k0) into its
 // region, then empty items (count 0) into the rest of the region.
 constexpr int kRangeChars = 256;
-constexpr int kRangeCharsMax = 4096;
+constexpr int kRangeCharsMax = 1024;
 constexpr int kMaxRanges = 4096;  // so at most ~900,000 characters per plan
 struct RangeDev {
   int32_t type;

@@ -199,7 +199,7 @@ cudaError_t launch_scan(const ScanArgs &a, const LaunchCfg &cfg, cudaStream_t st
 }
 
 // ------------------------------------------------------------ work queue
-constexpr int kBucketThreads = 1024;
+constexpr int kBucketThreads = 256;
 constexpr int kBucketPer = kRangeCharsMax / kBucketThreads;  // characters per thread
 static_assert(kBucketPer * kBucketThreads == kRangeCharsMax, "range size");
 

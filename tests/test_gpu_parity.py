@@ -161,15 +161,15 @@ def test_back_to_back_frames(torch, walk):
 @pytest.mark.parametrize("walk", [1, 2])
 def test_walk_frame_several_ranges(torch, walk):
     """8,192 characters of config 2's 512-joint type plus the dragon chain: the
-    walk types' work queue cuts them into two ranges of 4,096 characters, each
-    with its own item region.  Sampled characters (both ends of each range
+    walk types' work queue cuts them into eight ranges of 1,024 characters,
+    each with its own item region.  Sampled characters (the ends of ranges
     among them) equal the oracle's frame."""
     w = synth.config2(n_chars=8192)
     ctx, plan = _gpu.setup(w)
     ctx.set_schedule(plan, [16, 3, 4096, walk, 0])
     skin = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"])).cpu().numpy()
     assert ctx.status() == 0
-    sel = list(range(0, 8192, 37)) + [4095, 4096, 8191, 8192]
+    sel = list(range(0, 8192, 37)) + [1023, 1024, 4095, 4096, 8191, 8192]
     ws = synth.subset(w, sel)
     off = oracle.offsets(w["char_type"], w["types"])
     _gpu.assert_skin_close(skin[_rows(off, sel)], oracle.frame(ws), ws)
