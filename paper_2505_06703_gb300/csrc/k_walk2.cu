@@ -4,19 +4,20 @@
 // sampling runs on more warps per SM than the walk's lanes alone provide and
 // the skin matrices leave as lane-contiguous stores:
 //   warps 1 and 2 (samplers)  wait for a chunk of key records staged by
-//       cp.async.bulk, sample the local transforms L' = (q', t' + R(q') u) of
+//       cp.async.bulk, sample the local rotation q' and translation t' of
 //       half of its steps each into the chunk's row buffer, and write the
 //       previous chunk's skin matrices out: 16-byte parts of the chunk's rows
 //       enumerated lane by lane, so consecutive lanes store consecutive parts
 //       of one joint run (a run is a lane's chain over the chunk's steps);
-//   warp 0 (walker)  takes the chunk's local transforms, composes
-//       S = S_parent L' along its chains (branch points through shared
-//       memory) and overwrites each transform in place with its rows.
-// Hand-offs are mbarriers: records full (bulk-copy bytes) / empty, row
-// buffer sampled / composed / written out.  Every wait is bounded; a wait
-// that runs out sets status bit 4 and the warp stops (the others then run
-// out too), after waiting once more, bounded, for its own bulk copies in
-// flight.
+//   warp 0 (walker)  takes the chunk's local transforms
+//       L' = (R(q'), t' + R(q') u), composes S = S_parent L' along its chains
+//       (branch points through shared memory), overwrites each transform in
+//       place with its rows, and refills the record stages.
+// Hand-offs are mbarriers: records staged (bulk-copy bytes), row buffer
+// sampled / composed / written out.  Every wait is bounded; a wait that runs
+// out sets status bit 4 and the warp stops (the others then run out too);
+// the walker, which issues the bulk copies, first waits once more, bounded,
+// for those in flight.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -81,14 +82,6 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
 __device__ __forceinline__ void rec_sample_w2(const float4 *r, int P, float al, float4 &q, float3 &t) {
   rec_eval(r[0], r[P], r[2 * P], r[3 * P], al, q, t);
 }
-// R(q) v for a unit quaternion q: v + 2 w (u x v) + 2 u x (u x v), u = q.xyz.
-__device__ __forceinline__ float3 qrot_w2(const float4 q, const float3 v) {
-  const float cx = 2.f * (q.y * v.z - q.z * v.y), cy = 2.f * (q.z * v.x - q.x * v.z),
-              cz = 2.f * (q.x * v.y - q.y * v.x);
-  return make_float3(fmaf(q.w, cx, v.x) + (q.y * cz - q.z * cy), fmaf(q.w, cy, v.y) + (q.z * cx - q.x * cz),
-                     fmaf(q.w, cz, v.z) + (q.x * cy - q.y * cx));
-}
-
 // Shared memory of one CTA (dynamic, 128-byte aligned parts):
 //   rec[2]   staged key records, u and schedule entries of a chunk, the
 //            layout of k_walk's chunk buffer (clip 0 records [K][4][P],
@@ -112,11 +105,11 @@ template <int K>
 constexpr int kXStride = K == 1 ? 5 : 3 * K + 1;  // 5, 7, 13
 static_assert(32 * kXStride<4> * 16 <= (int)kXBuf, "row buffer");
 
-// Arrival counts: rec_full 1 (+ the copies' bytes), rec_empty 64 (sampler
-// lanes), x_full 64, x_rows 32 (walker lanes), x_empty 64 (sampler lanes,
-// after their part of the write-out).
+// Arrival counts: rec_full 1 (+ the copies' bytes), x_full 64 (sampler
+// lanes), x_rows 32 (walker lanes), x_empty 64 (sampler lanes, after their
+// part of the write-out).
 struct Bars {
-  uint64_t rec_full[2], rec_empty[2];
+  uint64_t rec_full[2];
   uint64_t x_full[2], x_rows[2], x_empty[2];
 };
 
@@ -177,35 +170,27 @@ __device__ __forceinline__ void w2_write_out(const float4 *xb, const uint32_t (&
 }
 
 // Sampler warp sw (0 or 1): steps k = sw, sw + 2 of every chunk into the row
-// buffer, and its part of the write-out of the chunk before.  Sampler 0's lane 0 also
-// keeps the record stages filled two chunks ahead.  al, w: the lane's
-// character's key fraction and blend weight.
+// buffer, and its part of the write-out of the chunk before.  al, w: the
+// lane's character's key fraction and blend weight.
 template <int K>
 __device__ bool w2_sampler(const W2Item &it, unsigned char *sm, Bars &B, float4 *const *outs, int sw, float al,
-                           float w, uint32_t &inflight) {
+                           float w) {
   constexpr int X = kXStride<K>;
   const int lane = threadIdx.x & 31, P = it.P, slot = lane & (P - 1);
   const bool act = (lane >> it.logP) < it.count;
-  uint32_t rpar = 0, repar = 0, xe = 3u, xr = 0;
+  uint32_t rpar = 0, xe = 3u, xr = 0;
   uint32_t part[kParts<K>];
   w2_parts<K>(sw, part);
-  auto fail = [&]() {  // drain this lane's own copies in flight, bounded
-    for (int s = 0; s < 2; ++s)
-      if (inflight & (1u << s)) mb_wait(&B.rec_full[s], (rpar >> s) & 1u);
-    return false;
-  };
   for (int q = 0; q <= it.nch; ++q) {
     if (q < it.nch) {
       const int s = q & 1;
-      if (!mb_wait(&B.rec_full[s], (rpar >> s) & 1u)) return fail();
+      if (!mb_wait(&B.rec_full[s], (rpar >> s) & 1u)) return false;
       rpar ^= 1u << s;
-      inflight &= ~(1u << s);
-      if (!mb_wait(&B.x_empty[s], (xe >> s) & 1u)) return fail();
+      if (!mb_wait(&B.x_empty[s], (xe >> s) & 1u)) return false;
       xe ^= 1u << s;
       const unsigned char *rec = sm + s * kRecBuf;
       const float4 *ra = reinterpret_cast<const float4 *>(rec) + slot;
       const float4 *rb = reinterpret_cast<const float4 *>(rec + kRecBytes) + slot;
-      const float4 *us = reinterpret_cast<const float4 *>(rec + kUOff) + slot;
       const uint32_t *ts = reinterpret_cast<const uint32_t *>(rec + kTabOff) + slot;
       float4 *xb = reinterpret_cast<float4 *>(sm + kXOff + s * kXBuf) + lane * X;
 #pragma unroll
@@ -222,24 +207,15 @@ __device__ bool w2_sampler(const W2Item &it, unsigned char *sm, Bars &B, float4 
           q4 = blend_unit(q4, qb, w);
           t = make_float3(fmaf(w, tb.x - t.x, t.x), fmaf(w, tb.y - t.y, t.y), fmaf(w, tb.z - t.z, t.z));
         }
-        const float4 u = us[k * P];
-        const float3 r = qrot_w2(q4, make_float3(u.x, u.y, u.z));
         const uint32_t e = act ? ts[k * P] : kWInvalid;
         xb[3 * k] = q4;
-        xb[3 * k + 1] = make_float4(t.x + r.x, t.y + r.y, t.z + r.z, __uint_as_float(e));
+        xb[3 * k + 1] = make_float4(t.x, t.y, t.z, __uint_as_float(e));
       }
-      mb_arrive(&B.x_full[s]);
-      mb_arrive(&B.rec_empty[s]);
-      if (sw == 0 && lane == 0 && q + 2 < it.nch) {
-        if (!mb_wait(&B.rec_empty[s], (repar >> s) & 1u)) return fail();  // both samplers done with it
-        repar ^= 1u << s;
-        w2_issue<K>(it, q + 2, sm + s * kRecBuf, &B.rec_full[s]);
-        inflight |= 1u << s;
-      }
+      mb_arrive(&B.x_full[s]);  // also: done with the record stage
     }
     if (q >= 1) {  // write-out of chunk q - 1
       const int o = (q - 1) & 1;
-      if (!mb_wait(&B.x_rows[o], (xr >> o) & 1u)) return fail();
+      if (!mb_wait(&B.x_rows[o], (xr >> o) & 1u)) return false;
       xr ^= 1u << o;
       w2_write_out<K>(reinterpret_cast<const float4 *>(sm + kXOff + o * kXBuf), part, outs, it.logP);
       mb_arrive(&B.x_empty[o]);
@@ -248,18 +224,38 @@ __device__ bool w2_sampler(const W2Item &it, unsigned char *sm, Bars &B, float4 
   return true;
 }
 
-// The walker warp: compose each chunk's transforms along the chains and
-// leave the rows in place for the samplers' write-out.
+// The walker warp: compose each chunk's transforms along the chains (the
+// local translation completed to t + R(q') u with the record stage's u) and
+// leave the rows in place for the samplers' write-out.  Its lane 0 keeps the
+// record stages filled two chunks ahead: a stage is refilled once the
+// samplers have sampled it and the walker has read its u.
 template <int K>
 __device__ bool w2_walker(const W2Item &it, unsigned char *sm, Bars &B, float4 *bslots) {
   constexpr int X = kXStride<K>;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, slot = lane & (it.P - 1);
   Aff S = aff_identity();
-  uint32_t xf = 0;
+  uint32_t xf = 0, rpar = 0;
   for (int q = 0; q < it.nch; ++q) {
     const int s = q & 1;
-    if (!mb_wait(&B.x_full[s], (xf >> s) & 1u)) return false;
+    bool ok = mb_wait(&B.x_full[s], (xf >> s) & 1u) && mb_wait(&B.rec_full[s], (rpar >> s) & 1u);
+    if (!ok) {  // drain the copies in flight (chunks q and q + 1), bounded
+      for (int c = q; c < q + 2 && c < it.nch; ++c) mb_wait(&B.rec_full[c & 1], (c >> 1) & 1u);
+      return false;
+    }
     xf ^= 1u << s;
+    rpar ^= 1u << s;
+    const float4 *us = reinterpret_cast<const float4 *>(sm + s * kRecBuf + kUOff) + slot;
+    float3 u[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float4 v = us[k * it.P];
+      u[k] = make_float3(v.x, v.y, v.z);
+    }
+    __syncwarp();  // every lane's reads of the stage before its refill
+    if (lane == 0 && q + 2 < it.nch) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      w2_issue<K>(it, q + 2, sm + s * kRecBuf, &B.rec_full[s]);
+    }
     float4 *xb = reinterpret_cast<float4 *>(sm + kXOff + s * kXBuf) + lane * X;
     uint32_t jk[4] = {kWInvalid, kWInvalid, kWInvalid, kWInvalid};
 #pragma unroll
@@ -267,7 +263,10 @@ __device__ bool w2_walker(const W2Item &it, unsigned char *sm, Bars &B, float4 *
       const float4 q4 = xb[3 * k], tt = xb[3 * k + 1];
       const uint32_t e = __float_as_uint(tt.w);
       const bool valid = e != kWInvalid;
-      const Aff L = aff_from_qt(q4, tt.x, tt.y, tt.z);
+      Aff L = aff_from_qt(q4, tt.x, tt.y, tt.z);
+      L.r0.w = fmaf(L.r0.x, u[k].x, fmaf(L.r0.y, u[k].y, fmaf(L.r0.z, u[k].z, L.r0.w)));
+      L.r1.w = fmaf(L.r1.x, u[k].x, fmaf(L.r1.y, u[k].y, fmaf(L.r1.z, u[k].z, L.r1.w)));
+      L.r2.w = fmaf(L.r2.x, u[k].x, fmaf(L.r2.y, u[k].y, fmaf(L.r2.z, u[k].z, L.r2.w)));
       Aff Sp = S;
       if (valid && (e & kWStart)) {
         const uint32_t ls = (e >> kWLoadShift) & 0xFFu;
@@ -287,7 +286,6 @@ __device__ bool w2_walker(const W2Item &it, unsigned char *sm, Bars &B, float4 *
     xb[3 * K] = make_float4(__uint_as_float(jk[0]), __uint_as_float(jk[1]), __uint_as_float(jk[2]),
                             __uint_as_float(jk[3]));
     mb_arrive(&B.x_rows[s]);
-
   }
   return true;
 }
@@ -303,7 +301,6 @@ __global__ void __launch_bounds__(kW2Threads, 8) k_walk2(const WalkArgs a) {
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
       mb_init(&B.rec_full[i], 1);
-      mb_init(&B.rec_empty[i], 64);
       mb_init(&B.x_full[i], 64);
       mb_init(&B.x_rows[i], 32);
       mb_init(&B.x_empty[i], 64);
@@ -341,14 +338,12 @@ __global__ void __launch_bounds__(kW2Threads, 8) k_walk2(const WalkArgs a) {
   }
   if (tid < wi.count) outs[tid] = reinterpret_cast<float4 *>(a.skin) + a.row_off[__ldg(a.item_chars + wi.start + tid)] * 3;
   __syncthreads();  // barriers initialized, outs[] filled
-  uint32_t inflight = 0;
-  if (warp == 1 && lane == 0) {
+  if (warp == 0 && lane == 0) {
     const int K = it.K;
     for (int q = 0; q < 2 && q < it.nch; ++q) {
       if (K == 1) w2_issue<1>(it, q, sm + q * kRecBuf, &B.rec_full[q]);
       else if (K == 2) w2_issue<2>(it, q, sm + q * kRecBuf, &B.rec_full[q]);
       else w2_issue<4>(it, q, sm + q * kRecBuf, &B.rec_full[q]);
-      inflight |= 1u << q;
     }
   }
   float4 *bslots = reinterpret_cast<float4 *>(sm + kSlotOff) + (size_t)c * a.nbs_max * 3;
@@ -359,9 +354,9 @@ __global__ void __launch_bounds__(kW2Threads, 8) k_walk2(const WalkArgs a) {
                      : w2_walker<4>(it, sm, B, bslots);
   } else {
     const int sw = warp - 1;
-    ok = it.K == 1   ? w2_sampler<1>(it, sm, B, outs, sw, al, w, inflight)
-         : it.K == 2 ? w2_sampler<2>(it, sm, B, outs, sw, al, w, inflight)
-                     : w2_sampler<4>(it, sm, B, outs, sw, al, w, inflight);
+    ok = it.K == 1   ? w2_sampler<1>(it, sm, B, outs, sw, al, w)
+         : it.K == 2 ? w2_sampler<2>(it, sm, B, outs, sw, al, w)
+                     : w2_sampler<4>(it, sm, B, outs, sw, al, w);
   }
   if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
 }
