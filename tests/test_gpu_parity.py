@@ -608,6 +608,7 @@ def _edge_types(rng):
             synth.make_type(synth.relabel_random_topological(synth.random_tree(33, 9, rng, spine=9), rng)[0],
                             rng, with_clips=True),                                         # non depth-first
             synth.make_type(synth.random_tree(1000, 40, rng, spine=40), rng, with_clips=True),
+            synth.make_type(np.array([-1] + [0] * 599, np.int32), rng, with_clips=True),     # star: 32 walk lanes
             synth.make_type(synth.chain(2048), rng, with_clips=True)]                      # maximum size
 
 
@@ -618,8 +619,15 @@ def test_edge_types_frame_and_local(torch):
     rng.shuffle(ct)
     w = {"types": types, "char_type": ct, "time": rng.uniform(-3, 5, len(ct)).astype(np.float32),
          "weight": rng.uniform(0, 1, len(ct)).astype(np.float32)}
-    _gpu.assert_skin_close(run_frame(w), oracle.frame(w), w)
-    _gpu.assert_skin_close(run_frame(w, levelsync=True), oracle.frame(w), w)
+    ref_frame = oracle.frame(w)
+    _gpu.assert_skin_close(run_frame(w), ref_frame, w)
+    _gpu.assert_skin_close(run_frame(w, levelsync=True), ref_frame, w)
+    for walk in (1, 2):  # both chain-walk kernels (4-, 2- and 1-step chunks among these types)
+        ctx, plan = _gpu.setup(w)
+        ctx.set_schedule(plan, [16, 3, 2048, walk, 0])
+        out = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"]))
+        assert ctx.status() == 0
+        _gpu.assert_skin_close(out.cpu().numpy(), ref_frame, w)
     off = oracle.offsets(ct, types)
     q, t = synth.local_poses(rng, int(off[-1]), t_half=0.0005)
     ref, mref = oracle.forward_qt(types, ct, q, t)
