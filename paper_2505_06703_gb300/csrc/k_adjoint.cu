@@ -110,7 +110,28 @@ __device__ void prefix_pairs(float4 *F, float4 *T, int n, float4 *wsF, float4 *w
 // MODE 2 IK step (effector loss, adjoint, Adam update of q, m, v), MODE 3
 // the same with the moments in the IK object's own state.  NT
 // threads run the passes (tid < NT); `step` is the 1-based Adam step.
-template <int MODE, int NT>
+// The view's tables in the item's shared memory: subtree ends, parents and
+// gather map (int16), and the segment tables of the forward scan.  Plan
+// data only, so the one-item kernel stages them before waiting for the
+// preceding grid.
+template <int NT>
+__device__ __forceinline__ void adjoint_tables(const ItemBuf &b, float4 *sm, int tid) {
+  const int C = b.C, n = b.T.n;
+  const ItemLayout Lt = item_layout_qt(sm, C, n, b.T.nseg);
+  int16_t *sub16 = reinterpret_cast<int16_t *>(Lt.end + 2 * (C * (n + 1) + 1));
+  int16_t *par16 = sub16 + n, *gat16 = par16 + n;
+  const int32_t *gat = b.T.gather;
+  for (int j = tid; j < n; j += NT) {
+    sub16[j] = (int16_t)__ldg(b.T.sub_end + j);
+    par16[j] = (int16_t)__ldg(b.T.parent + j);
+    gat16[j] = (int16_t)(gat ? __ldg(gat + j) : j);
+  }
+  stage_tables<NT>(b, Lt, tid);
+}
+
+// STAGED: adjoint_tables already ran for this item (all NT threads, before
+// a barrier that precedes the item).
+template <int MODE, int NT, bool STAGED = false>
 __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf &b, float4 *sm, float4 *wsF,
                                              float4 *wsT, int tid, int step) {
   const int C = b.C, n = b.T.n, nseg = b.T.nseg;
@@ -121,20 +142,15 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
   float4 *PT = PF + C * (n + 1) + 1;  // [C][n+1] (+1: the scan's total)
   // The adjoint runs on views numbered in depth-first pre-order, so a
   // joint's slot is its index and its subtree is [j, sub_end[j]).
-  int16_t *sub16 = reinterpret_cast<int16_t *>(PT + C * (n + 1) + 1);
-  int16_t *par16 = sub16 + n, *gat16 = par16 + n;
+  const int16_t *sub16 = reinterpret_cast<const int16_t *>(PT + C * (n + 1) + 1);
+  const int16_t *par16 = sub16 + n, *gat16 = par16 + n;
   const int32_t *gat = b.T.gather;
   const bool gath = gat != nullptr;
   const int CN = C * n;
-  for (int j = tid; j < n; j += NT) {
-    sub16[j] = (int16_t)__ldg(b.T.sub_end + j);
-    par16[j] = (int16_t)__ldg(b.T.parent + j);
-    gat16[j] = (int16_t)(gath ? __ldg(gat + j) : j);
-  }
+  if (!STAGED) adjoint_tables<NT>(b, sm, tid);
 
   // ---- pass 1a: local poses (q normalized, t); the joint's loss input
   // (dLoss/dp or target) is fetched alongside into its depth-first slot
-  stage_tables<NT>(b, Lt, tid);
   // A view of every joint (the loss and backward passes) reads the rows in
   // the caller's order -- coalesced, and independent of the view table --
   // and scatters them to their view slots; the IK's partial views gather.
@@ -351,6 +367,7 @@ __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const Adj
                   MODE == 3 ? a.state_off : nullptr);
   }
   __syncthreads();
+  adjoint_tables<kAdjSmallThreads>(b, sm, tid);  // read after the item's first barrier
   if (MODE < 2) {
     // warm L2 with the item's rows of poses and loss inputs while the
     // preceding grid finishes: a prefetch loads nothing into the kernel, and
@@ -373,7 +390,7 @@ __global__ void __launch_bounds__(kAdjSmallThreads, 7) k_adjoint_small(const Adj
   // preceding kernel in the stream: wait for it to complete
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int step = (MODE >= 2) ? *a.step + 1 : 0;
-  adjoint_item<MODE, kAdjSmallThreads>(a, b, sm, wsF, wsT, tid, step);
+  adjoint_item<MODE, kAdjSmallThreads, true>(a, b, sm, wsF, wsT, tid, step);
   if (MODE >= 2 && tid == 0) {  // the last CTA advances the IK step
     __threadfence();
     if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
