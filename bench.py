@@ -50,6 +50,7 @@ METRIC = "joint transforms/s fwd and fwd+bwd on 1 GB300, % of HBM roofline, vs p
 WORKLOAD = "frame: 4,096 x 512-joint biped (depth 70) + 1 x 1,024-joint dragon chain, 2 clips x 30 keys"
 UNIT = "joints/s"
 L2_BYTES = 129 * 1024 * 1024
+FRAMES_PER_GRAPH = 4  # frames per captured CUDA graph in the timed frame loop
 # DRAM bytes per launch of the frame's dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources it was taken on (comments and whitespace aside); reported
@@ -292,31 +293,40 @@ def run_ours(args) -> dict:
     times = [torch.as_tensor(np.mod(w["time"] + k / 60.0, 1.0).astype(np.float32), device=dev) for k in range(n_in)]
     blend = torch.as_tensor(w["weight"], device=dev)
 
-    # one graph per (output buffer): work queue + persistent kernel
-    n_graph = n_out * n_in // math.gcd(n_out, n_in)
+    # frames captured FRAMES_PER_GRAPH at a time (each frame its own work
+    # queue + frame kernels, on its own times and output buffer), as a render
+    # loop would submit them; single-frame graphs for the remainder, so that
+    # exactly `steps` frames are timed
+    n_frames = n_out * n_in // math.gcd(n_out, n_in)
+    n_frames = FRAMES_PER_GRAPH * math.ceil(n_frames / FRAMES_PER_GRAPH)
     stream = torch.cuda.Stream()
-    graphs = []
     with torch.cuda.stream(stream):
-        for i in range(n_graph):  # warm once outside capture (sets kernel attributes)
+        for i in range(n_frames):  # warm once outside capture (sets kernel attributes)
             ctx.evaluate_frame(plan, times[i % n_in], blend, out=outs[i % n_out])
     stream.synchronize()
-    for i in range(n_graph):
+
+    def capture(first, count):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            ctx.evaluate_frame(plan, times[i % n_in], blend, out=outs[i % n_out])
-        graphs.append(g)
+            for i in range(first, first + count):
+                ctx.evaluate_frame(plan, times[i % n_in], blend, out=outs[i % n_out])
+        return g
+
+    graphs = [capture(i, FRAMES_PER_GRAPH) for i in range(0, n_frames, FRAMES_PER_GRAPH)]
+    singles = [capture(i, 1) for i in range(n_frames)]
+    n_graph = len(graphs)
     torch.cuda.synchronize()
 
     steps, warmup = args.steps, args.warmup
     for s in range(warmup):
-        graphs[s % n_graph].replay()
+        singles[s % n_frames].replay()
     torch.cuda.synchronize()
     barrier(world)
     def load_for(seconds):
         t0 = time.perf_counter()
         k = 0
         while time.perf_counter() - t0 < seconds:
-            for _ in range(64):
+            for _ in range(16):
                 graphs[k % n_graph].replay()
                 k += 1
             torch.cuda.synchronize()
@@ -328,8 +338,10 @@ def run_ours(args) -> dict:
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for s in range(steps):
-            graphs[(warmup + s) % n_graph].replay()
+        for s in range(steps // FRAMES_PER_GRAPH):
+            graphs[s % n_graph].replay()
+        for s in range(steps % FRAMES_PER_GRAPH):
+            singles[s % n_frames].replay()
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
@@ -375,12 +387,15 @@ def run_ours(args) -> dict:
                          "steps_of_the_frame": "slerp keys, slerp 2-clip blend, hierarchy scan, bind",
                          "joints_per_step_per_gpu": joints, "characters_per_gpu": n_chars,
                          "l2": f"output rotated over {n_out} buffers ({n_out * out_bytes / 1e6:.0f} MB > 129 MB L2)",
-                         "timing": "one CUDA graph per frame (work queue + frame kernels), graphs replayed back to back, "
-                                   "CUDA events; the roofline's kernel time from one graph of frame-kernel launches back to back",
+                         "timing": f"CUDA graphs of {FRAMES_PER_GRAPH} consecutive frames (each frame: work queue + frame "
+                                   "kernels, its own times and output buffer) replayed back to back, CUDA events; the "
+                                   "roofline's kernel time from one graph of frame-kernel launches back to back",
                          "schedule": {"seg_len,ctas_per_sm,joints_per_item,walk,adj_ctas": schedule,
                                       "source": "--schedule" if args.schedule else "anim_tune"},
                          "parallelism": f"replicas x{world} (independent character batches)"},
-              "roofline": roofline, "gpu_launches": 2 * steps, "clocks": clock}
+              # per frame: the work queue, the frame kernel, and with a chain-walk
+              # schedule the segmented kernel beside it (the dragon chain is never walked)
+              "roofline": roofline, "gpu_launches": (3 if schedule[3] else 2) * steps, "clocks": clock}
 
     # end to end through the C-ABI call with host buffers
     # (anim_evaluate_frame_host): page-locked inputs copied in and the whole
@@ -1013,6 +1028,9 @@ def run_only(args) -> dict:
     sched = [int(x) for x in args.schedule.split(",")] if args.schedule else None
     if args.only == "forward":
         res = time_forward_methods(rank_workload(rank), local, dev, world, algs=(), schedule=sched)
+    elif args.only == "fwd_bwd":
+        res = run_fwd_bwd(ctx_factory=setup_ctx, device=local, dev=dev, steps=args.steps, warmup=args.warmup,
+                          world=world, peak=peak, schedule=args.schedule_bwd or None)
     else:
         fn = {"mixed": run_mixed_frame, "mixed_split": run_mixed_split, "ik": run_ik, "skinned": run_skinned_frame,
               "layers": run_layered_frame}
@@ -1060,7 +1078,8 @@ def main():
     ap.add_argument("--schedule", default="", help="seg_len,ctas_per_sm,joints_per_item,walk[,adj_ctas] for the frame "
                                                    "instead of running the autotuner")
     ap.add_argument("--schedule-bwd", default="", help="the same for the forward+adjoint measurement")
-    ap.add_argument("--only", choices=["mixed", "mixed_split", "ik", "skinned", "layers", "forward"], default="",
+    ap.add_argument("--only", choices=["mixed", "mixed_split", "ik", "skinned", "layers", "forward", "fwd_bwd"],
+                    default="",
                     help="run one of the extra workloads alone (under --schedule if given, else autotuned) and "
                          "print its result object; a short command for profiling its kernel")
     ap.add_argument("--paper-sweep", action="store_true",
