@@ -234,6 +234,13 @@ struct WalkArgs {
   int *status;
   const float *time, *blend_w;
   float *skin;
+  // 0: wait for the preceding grid (the work-queue kernel) before reading
+  // the item.  1 (k_walk2 only): the preceding grid is the segmented frame
+  // kernel, which lets this launch start only after its own wait for the
+  // work queue; the item and the inputs are read from L2 at once, and each
+  // CTA waits for that grid at its end, so that the next launch in the
+  // stream (the next frame's work queue) still follows both.
+  int pred_waited;
 };
 size_t walk_smem_bytes(int chars_per_item, int nbs);
 // The warp-specialized variant (three warps per item: two sample and write

@@ -1509,6 +1509,10 @@ int anim_frame_build_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_
   return ANIM_OK;
 }
 
+// Item slots of the segmented kernel up to which a frame runs it on the
+// same stream before the warp-specialized walk kernel (anim_frame_run_queue).
+constexpr int kChainSlots = 16;
+
 int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
                          float *d_skin, void *stream) {
   int rc = frame_checks(ctx, plan, d_time);
@@ -1518,7 +1522,15 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
     return fail(ctx, ANIM_EINVAL, "d_skin must be 16-byte aligned, d_blend_w 4-byte aligned");
   cudaStream_t st = (cudaStream_t)stream, cta_st = st;
   const bool has_walk = plan->n_slots_walk > 0, has_cta = plan->n_slots > plan->n_slots_walk;
-  if (has_walk && has_cta) {
+  // A segmented part of a few items beside the warp-specialized walk (a
+  // dragon chain among bipeds) runs first on the same stream: the two
+  // kernels overlap through programmatic dependent launch (the walk kernel
+  // starts once the segmented kernel has seen the work queue, and finishes
+  // after it), and the next launch in the stream keeps a single kernel
+  // predecessor -- a fork onto the side stream and back ends that chain and
+  // costs the next frame its early start.
+  const bool chain = has_walk && has_cta && ctx->use_walk == 2 && plan->n_slots - plan->n_slots_walk <= kChainSlots;
+  if (has_walk && has_cta && !chain) {
     // the two kernels run side by side: fork onto the context's side stream
     if (!ctx->side) {
       CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
@@ -1563,12 +1575,13 @@ int anim_frame_run_queue(anim_ctx *ctx, const anim_plan *plan, const float *d_ti
     w.time = d_time;
     w.blend_w = d_blend_w;
     w.skin = d_skin;
+    w.pred_waited = chain ? 1 : 0;
     if (ctx->use_walk == 2)
       CK(launch_walk2(w, plan->walk_smem, st));
     else
       CK(launch_walk(w, plan->walk_smem, st));
   }
-  if (has_walk && has_cta) {
+  if (has_walk && has_cta && !chain) {
     CK(cudaEventRecord(ctx->ev_join, ctx->side));
     CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   }

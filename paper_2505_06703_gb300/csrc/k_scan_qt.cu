@@ -32,16 +32,20 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
   const int tid = threadIdx.x;
   // launched with programmatic stream serialization (after the work-queue
   // kernel, for the frame): wait for the preceding grid to complete before
-  // reading anything it may have written.  The next frame's work-queue
-  // kernel may start now (it reads only plan tables before its own wait).
+  // reading anything it may have written.  The next launch may start now
+  // (the next frame's work-queue kernel reads only plan tables before its
+  // own wait) -- in the plain frame only once this grid's wait is over, as
+  // the chain-walk kernel launched after it may then read the work queue
+  // without a wait of its own (WalkArgs::pred_waited).
   // The forward from local poses (fixed work items) prefetches its first
   // wave's rows of q and t into L2 before the wait, and each next item's
   // while the current one runs.
-  asm volatile("griddepcontrol.launch_dependents;");
+  if (MODE != 0) asm volatile("griddepcontrol.launch_dependents;");
   const RowPrefetch pf = MODE == 1 ? RowPrefetch{{a.q, a.t, nullptr, nullptr}, {4, 3, 0, 0}, 0} : RowPrefetch{};
   if (MODE == 1 && tid >= kComputeThreads)
     prefetch_first_wave(bufs[1], a.n_items, a.items, a.types, a.item_chars, a.row_off, pf);
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (MODE == 0) asm volatile("griddepcontrol.launch_dependents;");
   const int n_items = a.n_items;
 
   if (tid >= kComputeThreads) {

@@ -296,7 +296,10 @@ __global__ void __launch_bounds__(kW2Threads, 8) k_walk2(const WalkArgs a) {
   __shared__ float4 *outs[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // launched with programmatic stream serialization after the work-queue
-  // kernel: set up, then wait for it before reading the item
+  // kernel: set up, then wait for it before reading the item (or, after
+  // the segmented frame kernel, read at once and wait at the end:
+  // WalkArgs::pred_waited).  Queue entries and inputs are loaded from L2
+  // (.cg), never from a line an earlier frame left in L1.
   asm volatile("griddepcontrol.launch_dependents;");
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -307,9 +310,19 @@ __global__ void __launch_bounds__(kW2Threads, 8) k_walk2(const WalkArgs a) {
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const WorkItem wi = a.items[blockIdx.x];
-  if (wi.count <= 0) return;
+  if (!a.pred_waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+  WorkItem wi;
+  {
+    const int4 v = __ldcg(reinterpret_cast<const int4 *>(a.items) + blockIdx.x);
+    wi.start = v.x;
+    wi.count = v.y;
+    wi.type = v.z;
+    wi.k0 = v.w;
+  }
+  if (wi.count <= 0) {
+    if (a.pred_waited && tid == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
+    return;
+  }
   const TypeDev &T = a.types[wi.type];
   W2Item it;
   it.P = T.wk_P;
@@ -326,17 +339,17 @@ __global__ void __launch_bounds__(kW2Threads, 8) k_walk2(const WalkArgs a) {
   const int c = lane >> it.logP;
   float al = 0.f, w = 0.f;
   if (c < wi.count) {
-    const int cid = __ldg(a.item_chars + wi.start + c);
-    const float tm = __ldg(a.time + cid);
+    const int cid = __ldcg(a.item_chars + wi.start + c);
+    const float tm = __ldcg(a.time + cid);
     if (isfinite(tm)) {
       const float uu = __fmul_rn(tm, T.rate);
       al = uu - floorf(uu);
     } else if (warp == 1) {
       atomicOr(a.status, kStatusNonfiniteTime);
     }
-    w = it.two ? __ldg(a.blend_w + cid) : 0.f;
+    w = it.two ? __ldcg(a.blend_w + cid) : 0.f;
   }
-  if (tid < wi.count) outs[tid] = reinterpret_cast<float4 *>(a.skin) + a.row_off[__ldg(a.item_chars + wi.start + tid)] * 3;
+  if (tid < wi.count) outs[tid] = reinterpret_cast<float4 *>(a.skin) + a.row_off[__ldcg(a.item_chars + wi.start + tid)] * 3;
   __syncthreads();  // barriers initialized, outs[] filled
   if (warp == 0 && lane == 0) {
     const int K = it.K;
@@ -359,6 +372,7 @@ __global__ void __launch_bounds__(kW2Threads, 8) k_walk2(const WalkArgs a) {
                      : w2_sampler<4>(it, sm, B, outs, sw, al, w);
   }
   if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+  if (a.pred_waited && tid == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 }  // namespace
