@@ -164,8 +164,12 @@ ANIM_API int anim_plan_vertex_offsets(anim_ctx *ctx, const anim_plan *plan, int6
  * type's clips at d_time[c] seconds, blend clip 0 -> clip 1 with
  * d_blend_w[c], compose down the hierarchy (Eq. 1) and multiply by the inverse
  * bind.  d_time, d_blend_w: device [n_chars] float; d_skin: device
- * [total][12] float (written).  One persistent launch plus a small
- * work-queue launch on `stream`. */
+ * [total][12] float (written).  A small work-queue launch, then the frame
+ * kernels: the segmented persistent kernel for the types without a
+ * chain-walk schedule and, under a schedule that enables it, the chain-walk
+ * kernel for the others -- one after the other on `stream` when the
+ * segmented part holds at most 16 work items, otherwise side by side on a
+ * second stream of the context that `stream` forks to and joins back. */
 ANIM_API int anim_evaluate_frame(anim_ctx *ctx, const anim_plan *plan, const float *d_time, const float *d_blend_w,
                         float *d_skin, void *stream);
 
