@@ -25,8 +25,6 @@ struct TypeDev {
   const int32_t *seg_start;  // [nseg + 1]
   const int32_t *seg_link;   // [nseg]  parent joint of the segment's first joint, -1 for roots
   const uint32_t *jinfo;     // [n] segment of the joint (bits 0-15) | kJStart | kJLink
-  const int32_t *seg_order;  // [nseg] segments longest first: the lane order of the segment walks
-                             // (a warp walks as long as its longest segment); nullptr: index order
   const float4 *inv_bind;    // [n][3] rows of B_i
   const float4 *keys;        // [n_clips][n_keys][n][2]: (qx qy qz qw), (tx ty tz theta); theta's sign
                              // bit: the next key lies on the other hemisphere

@@ -34,7 +34,6 @@ struct Segments {
   std::vector<int32_t> start, link;
   std::vector<uint16_t> seg_of;
   std::vector<uint32_t> jinfo;     // per joint: segment | kJStart | kJLink
-  std::vector<int32_t> order;      // segments by length, longest first (stable)
 };
 
 // Segments: maximal runs of consecutive joints where each joint's parent is
@@ -79,11 +78,6 @@ Segments analyze_segments(const std::vector<int32_t> &par, int seg_len) {
     const int g = S.seg_of[j];
     S.jinfo[j] = (uint32_t)g | (j == S.start[g] ? kJStart : 0u) | (S.link[g] >= 0 ? kJLink : 0u);
   }
-  S.order.resize(S.nseg);
-  for (int g = 0; g < S.nseg; ++g) S.order[g] = g;
-  std::stable_sort(S.order.begin(), S.order.end(), [&](int x, int y) {
-    return S.start[x + 1] - S.start[x] > S.start[y + 1] - S.start[y];
-  });
   return S;
 }
 
@@ -476,7 +470,6 @@ struct TypeHost {
     const size_t o_g = B.add(gather.data(), gather.size() * 4);
     const size_t o_ig = B.add(inv_gather.data(), inv_gather.size() * 4);
     const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
-    const size_t o_so = B.add(seg.order.data(), seg.order.size() * 4);
     const size_t o_wt = B.add(ws.tab.data(), ws.tab.size() * 4);
     std::vector<int32_t> blk_out(n);
     for (int j = 0; j < n; ++j) {  // parent of the block-local root of j
@@ -505,7 +498,6 @@ struct TypeHost {
     dev.gather = gather.empty() ? nullptr : (const int32_t *)(base + o_g);
     dev.inv_gather = inv_gather.empty() ? nullptr : (const int32_t *)(base + o_ig);
     dev.jinfo = (const uint32_t *)(base + o_ji);
-    dev.seg_order = (const int32_t *)(base + o_so);
     dev.wk_mode = ws.mode;
     dev.wk_P = ws.P;
     dev.wk_logP = ws.logP;

@@ -315,16 +315,12 @@ __device__ __forceinline__ void pass1a_qt(const ItemBuf &b, float4 *P, int cs4, 
   }
 }
 
-// Pass 1b: running products along each segment, in place.  Segments are
-// taken longest first (TypeDev::seg_order), so a warp's lanes walk segments
-// of similar lengths.
+// Pass 1b: running products along each segment, in place.
 template <int NT = kComputeThreads>
 __device__ __forceinline__ void pass1b(const ItemBuf &b, const ItemLayout &Lt, float4 *P, int cs4, int tid) {
   const int C = b.C, NS = b.T.nseg * C;
-  const int32_t *ord = b.T.seg_order;
   for (int idx = tid; idx < NS; idx += NT) {
-    const int gi = (int)b.divC.div(idx), c = idx - gi * C;
-    const int g = ord ? __ldg(ord + gi) : gi;
+    const int g = (int)b.divC.div(idx), c = idx - g * C;
     const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1];
     float4 *Pc = P + c * cs4;
     Aff acc = lds_aff(Pc + 3 * a0);
@@ -504,14 +500,12 @@ __host__ __device__ inline size_t qt_item_bytes(int n, int nseg, int C) {
 }
 
 // Pass 1b on (q, t) pairs: running products along each segment, in place
-// (P's character stride cs2 in float4), segments longest first.
+// (P's character stride cs2 in float4).
 template <int NT = kComputeThreads>
 __device__ __forceinline__ void pass1b_qt(const ItemBuf &b, const ItemLayout &Lt, float4 *P, int cs2, int tid) {
   const int C = b.C, NS = b.T.nseg * C;
-  const int32_t *ord = b.T.seg_order;
   for (int idx = tid; idx < NS; idx += NT) {
-    const int gi = (int)b.divC.div(idx), c = idx - gi * C;
-    const int g = ord ? __ldg(ord + gi) : gi;
+    const int g = (int)b.divC.div(idx), c = idx - g * C;
     const int a0 = Lt.seg_start[g], a1 = Lt.seg_start[g + 1], n = b.T.n;
     float4 *Pc = P + c * cs2;
     QT acc = lds_qt(Pc, a0, n);
