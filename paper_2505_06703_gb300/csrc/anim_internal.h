@@ -25,6 +25,12 @@ struct TypeDev {
   const int32_t *seg_start;  // [nseg + 1]
   const int32_t *seg_link;   // [nseg]  parent joint of the segment's first joint, -1 for roots
   const uint32_t *jinfo;     // [n] segment of the joint (bits 0-15) | kJStart | kJLink
+  // The same tables in the 16-bit form the kernels keep in shared memory,
+  // staged there by cp.async: jinfo16 [n rounded up to even] = segment |
+  // kJ16Start | kJ16Link; sub16, par16, gat16 [n] = sub_end, parent and
+  // gather (identity for a type) as int16.
+  const uint16_t *jinfo16;
+  const int16_t *sub16, *par16, *gat16;
   const float4 *inv_bind;    // [n][3] rows of B_i
   const float4 *keys;        // [n_clips][n_keys][n][2]: (qx qy qz qw), (tx ty tz theta); theta's sign
                              // bit: the next key lies on the other hemisphere
@@ -87,6 +93,8 @@ constexpr int kStatusTimeout = 4;
 
 constexpr uint32_t kJStart = 1u << 16;  // joint opens its segment
 constexpr uint32_t kJLink = 1u << 17;   // the joint's segment hangs from a parent joint
+// 16-bit joint info (shared memory): segment (14 bits) | start | link.
+constexpr uint16_t kJ16Seg = 0x3FFFu, kJ16Start = 0x4000u, kJ16Link = 0x8000u;
 
 // One unit of work: `count` characters of one type.  For the frame the
 // characters share the key index k0 (so they read the same key records).

@@ -470,6 +470,20 @@ struct TypeHost {
     const size_t o_g = B.add(gather.data(), gather.size() * 4);
     const size_t o_ig = B.add(inv_gather.data(), inv_gather.size() * 4);
     const size_t o_ji = B.add(seg.jinfo.data(), seg.jinfo.size() * 4);
+    // 16-bit forms staged by cp.async (jinfo16 padded to an even count)
+    std::vector<uint16_t> j16((size_t)(n + (n & 1)), 0);
+    std::vector<int16_t> s16(n), p16(n), g16(n);
+    for (int j = 0; j < n; ++j) {
+      const uint32_t i = seg.jinfo[j];
+      j16[j] = (uint16_t)((i & kJ16Seg) | ((i & kJStart) ? kJ16Start : 0u) | ((i & kJLink) ? kJ16Link : 0u));
+      s16[j] = (int16_t)dfsord.sub_end[j];
+      p16[j] = (int16_t)parent[j];
+      g16[j] = (int16_t)(gather.empty() ? j : gather[j]);
+    }
+    const size_t o_j16 = B.add(j16.data(), j16.size() * 2);
+    const size_t o_s16 = B.add(s16.data(), s16.size() * 2);
+    const size_t o_p16 = B.add(p16.data(), p16.size() * 2);
+    const size_t o_g16 = B.add(g16.data(), g16.size() * 2);
     const size_t o_wt = B.add(ws.tab.data(), ws.tab.size() * 4);
     std::vector<int32_t> blk_out(n);
     for (int j = 0; j < n; ++j) {  // parent of the block-local root of j
@@ -498,6 +512,10 @@ struct TypeHost {
     dev.gather = gather.empty() ? nullptr : (const int32_t *)(base + o_g);
     dev.inv_gather = inv_gather.empty() ? nullptr : (const int32_t *)(base + o_ig);
     dev.jinfo = (const uint32_t *)(base + o_ji);
+    dev.jinfo16 = (const uint16_t *)(base + o_j16);
+    dev.sub16 = (const int16_t *)(base + o_s16);
+    dev.par16 = (const int16_t *)(base + o_p16);
+    dev.gat16 = (const int16_t *)(base + o_g16);
     dev.wk_mode = ws.mode;
     dev.wk_P = ws.P;
     dev.wk_logP = ws.logP;

@@ -114,19 +114,35 @@ __device__ void prefix_pairs(float4 *F, float4 *T, int n, float4 *wsF, float4 *w
 // gather map (int16), and the segment tables of the forward scan.  Plan
 // data only, so the one-item kernel stages them before waiting for the
 // preceding grid.
+// Staged by cp.async in 4-byte words from the view's 16-bit tables when n is
+// even (the three arrays then start on 4-byte boundaries), else converted
+// here; every thread waits for its copies (cp_async_wait_all) before the
+// barrier that follows pass 1a.
 template <int NT>
 __device__ __forceinline__ void adjoint_tables(const ItemBuf &b, float4 *sm, int tid) {
   const int C = b.C, n = b.T.n;
   const ItemLayout Lt = item_layout_qt(sm, C, n, b.T.nseg);
   int16_t *sub16 = reinterpret_cast<int16_t *>(Lt.end + 2 * (C * (n + 1) + 1));
   int16_t *par16 = sub16 + n, *gat16 = par16 + n;
-  const int32_t *gat = b.T.gather;
-  for (int j = tid; j < n; j += NT) {
-    sub16[j] = (int16_t)__ldg(b.T.sub_end + j);
-    par16[j] = (int16_t)__ldg(b.T.parent + j);
-    gat16[j] = (int16_t)(gat ? __ldg(gat + j) : j);
+  if ((n & 1) == 0 && b.T.sub16) {
+    const int w = n / 2;
+    const uint32_t *ss = reinterpret_cast<const uint32_t *>(b.T.sub16);
+    const uint32_t *sp = reinterpret_cast<const uint32_t *>(b.T.par16);
+    const uint32_t *sg = reinterpret_cast<const uint32_t *>(b.T.gat16);
+    for (int k = tid; k < w; k += NT) {
+      cp_async4(reinterpret_cast<uint32_t *>(sub16) + k, ss + k);
+      cp_async4(reinterpret_cast<uint32_t *>(par16) + k, sp + k);
+      cp_async4(reinterpret_cast<uint32_t *>(gat16) + k, sg + k);
+    }
+  } else {
+    const int32_t *gat = b.T.gather;
+    for (int j = tid; j < n; j += NT) {
+      sub16[j] = (int16_t)__ldg(b.T.sub_end + j);
+      par16[j] = (int16_t)__ldg(b.T.parent + j);
+      gat16[j] = (int16_t)(gat ? __ldg(gat + j) : j);
+    }
   }
-  stage_tables<NT>(b, Lt, tid);
+  stage_tables<NT>(b, Lt, tid);  // commits this thread's copies
 }
 
 // STAGED: adjoint_tables already ran for this item (all NT threads, before
@@ -171,6 +187,7 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       }
     }
   }
+  cp_async_wait_all();  // this thread's table copies (adjoint_tables)
   pass_sync<NT>();
   pass1b_qt<NT>(b, Lt, P, cs2, tid);
   pass_sync<NT>();

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
       pending = false;
     }
     compute_sync();
-    stage_tables(b, Lt, tid);
+    stage_tables<kComputeThreads, false>(b, Lt, tid);
     pass1a_qt(b, P, cs4, q, t, tid);
     compute_sync();
     pass1b(b, Lt, P, cs4, tid);

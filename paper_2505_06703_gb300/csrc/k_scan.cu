@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan(const ScanArgs a) {
         sts_aff(P + c * cs4 + 3 * j, sample_local(r, b.alpha[c], b.blend[c], two));
       }
     }
+    cp_async_wait_all();  // this thread's table copies (stage_tables)
     compute_sync();
 
     // ---- pass 1b: running products along segments

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
         }
       }
     }
+    cp_async_wait_all();  // this thread's table copies (stage_tables)
     compute_sync();
 
     // ---- pass 1b: running products along segments

@@ -258,7 +258,6 @@ __device__ __forceinline__ void prefetch_first_wave(ItemBuf &b, int n_items, con
 //   seg_start int32 [nseg+1], seg_link int32 [nseg], jinfo uint16 [n]
 //            the type's tables, staged once per item so the serial passes
 //            read shared memory instead of waiting on global loads.
-constexpr uint16_t kJ16Seg = 0x3FFFu, kJ16Start = 0x4000u, kJ16Link = 0x8000u;
 struct ItemLayout {
   float4 *P, *Y0, *Y1;
   int16_t *ptr0, *ptr1;
@@ -283,17 +282,50 @@ __device__ __forceinline__ ItemLayout item_layout(float4 *sm, int C, int n, int 
   L.end = reinterpret_cast<float4 *>(t + item_table_bytes(n, nseg));
   return L;
 }
-// Copy the type's segment tables into the item's shared memory (all compute
-// threads; issued at the start of pass 1a so the loads overlap its work).
-template <int NT = kComputeThreads>
+// cp.async global -> shared copy of 4 bytes (both addresses 4-byte aligned);
+// the issuing thread waits for its copies with cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage the type's segment tables (the parent structure of the scan) into
+// the item's shared memory by cp.async: seg_start, seg_link and the 16-bit
+// joint info in 4-byte words (an odd last entry by a plain load, so nothing
+// is written past the table).  Issued at the start of pass 1a; every thread
+// calls cp_async_wait_all before the barrier that precedes the tables' first
+// use, so the copies overlap pass 1a's work.  ASYNC false: plain loads,
+// the joint info converted here (the allocation-free entry's type record,
+// which has no 16-bit tables).
+template <int NT = kComputeThreads, bool ASYNC = true>
 __device__ __forceinline__ void stage_tables(const ItemBuf &b, const ItemLayout &L, int tid) {
   const int n = b.T.n, nseg = b.T.nseg;
-  for (int k = tid; k <= nseg; k += NT) L.seg_start[k] = __ldg(b.T.seg_start + k);
-  for (int k = tid; k < nseg; k += NT) L.seg_link[k] = __ldg(b.T.seg_link + k);
-  for (int j = tid; j < n; j += NT) {
-    const uint32_t i = __ldg(b.T.jinfo + j);
-    L.jinfo[j] = (uint16_t)((i & kJ16Seg) | ((i & kJStart) ? kJ16Start : 0u) | ((i & kJLink) ? kJ16Link : 0u));
+  if (!ASYNC) {
+    for (int k = tid; k <= nseg; k += NT) L.seg_start[k] = __ldg(b.T.seg_start + k);
+    for (int k = tid; k < nseg; k += NT) L.seg_link[k] = __ldg(b.T.seg_link + k);
+    for (int j = tid; j < n; j += NT) {
+      const uint32_t i = __ldg(b.T.jinfo + j);
+      L.jinfo[j] = (uint16_t)((i & kJ16Seg) | ((i & kJStart) ? kJ16Start : 0u) | ((i & kJLink) ? kJ16Link : 0u));
+    }
+    return;
   }
+  for (int k = tid; k <= nseg; k += NT) cp_async4(L.seg_start + k, b.T.seg_start + k);
+  for (int k = tid; k < nseg; k += NT) cp_async4(L.seg_link + k, b.T.seg_link + k);
+  if (b.T.jinfo16) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(b.T.jinfo16);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(L.jinfo);
+    for (int k = tid; k < n / 2; k += NT) cp_async4(dst + k, src + k);
+    if ((n & 1) && tid == 0) L.jinfo[n - 1] = __ldg(b.T.jinfo16 + n - 1);
+  } else {
+    for (int j = tid; j < n; j += NT) {
+      const uint32_t i = __ldg(b.T.jinfo + j);
+      L.jinfo[j] = (uint16_t)((i & kJ16Seg) | ((i & kJStart) ? kJ16Start : 0u) | ((i & kJLink) ? kJ16Link : 0u));
+    }
+  }
+  cp_async_commit();
 }
 
 // Pass 1a from given local poses (q normalized here, t), optionally through a
