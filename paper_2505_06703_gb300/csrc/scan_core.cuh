@@ -50,6 +50,16 @@ __device__ __forceinline__ void pass_sync() {
     __syncthreads();
 }
 
+// cp.async global -> shared copy of 4 bytes (both addresses 4-byte aligned);
+// the issuing thread waits for its copies with cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Everything one work item needs besides the big buffers (double-buffered).
 struct ItemBuf {
   TypeDev T;
@@ -109,9 +119,11 @@ __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &w
                                            const float *blend_w, int *status, const int64_t *vert_off,
                                            LayerIn layers) {
   const int lane = threadIdx.x & 31;
+  // the type record by cp.async, overlapping the character loads below
   const int *src = reinterpret_cast<const int *>(types + wi.type);
   int *dst = reinterpret_cast<int *>(&b.T);
-  for (int k = lane; k < (int)(sizeof(TypeDev) / 4); k += 32) dst[k] = src[k];
+  for (int k = lane; k < (int)(sizeof(TypeDev) / 4); k += 32) cp_async4(dst + k, src + k);
+  cp_async_commit();
   const float rate = types[wi.type].rate;
   for (int c = lane; c < wi.count; c += 32) {
     const int cid = __ldg(item_chars + wi.start + c);
@@ -150,6 +162,7 @@ __device__ __forceinline__ void stage_item(ItemBuf &b, int it, const WorkItem &w
     b.cpt = (wi.count + g - 1) / g;
     b.cgroups = (wi.count + b.cpt - 1) / b.cpt;
   }
+  cp_async_wait_all();  // the type record's copies
   __syncwarp();
 }
 
@@ -282,16 +295,6 @@ __device__ __forceinline__ ItemLayout item_layout(float4 *sm, int C, int n, int 
   L.end = reinterpret_cast<float4 *>(t + item_table_bytes(n, nseg));
   return L;
 }
-// cp.async global -> shared copy of 4 bytes (both addresses 4-byte aligned);
-// the issuing thread waits for its copies with cp_async_wait_all.
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Stage the type's segment tables (the parent structure of the scan) into
 // the item's shared memory by cp.async: seg_start, seg_link and the 16-bit
 // joint info in 4-byte words (an odd last entry by a plain load, so nothing
