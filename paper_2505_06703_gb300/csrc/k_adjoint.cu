@@ -171,14 +171,23 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
   // the caller's order -- coalesced, and independent of the view table --
   // and scatters them to their view slots; the IK's partial views gather.
   const int32_t *inv = MODE < 2 ? b.T.inv_gather : nullptr;
+  // backward passes: a thread's first two rows of q stay in registers for
+  // the gradient pass, which visits the same (character, joint) pairs in the
+  // same order (the IK step, whose kernels are larger, reads them again)
+  constexpr bool kKeep = MODE < 2;
+  float4 qkeep[2] = {make_float4(0.f, 0.f, 0.f, 1.f), make_float4(0.f, 0.f, 0.f, 1.f)};
   {
     const float4 *q4 = reinterpret_cast<const float4 *>(a.q);
+    int it = 0;
 #pragma unroll 2
-    for (int idx = tid; idx < CN; idx += NT) {
+    for (int idx = tid; idx < CN; idx += NT, ++it) {
       const int c = (int)b.divN.div(idx), k = idx - c * n;
       const int j = inv ? __ldg(inv + k) : k;
       const long long row = b.off[c] + (inv ? k : gath ? __ldg(gat + k) : k);
-      const float4 q = normalize4(__ldg(q4 + row));
+      const float4 qr = __ldg(q4 + row);
+      if (kKeep && it == 0) qkeep[0] = qr;
+      if (kKeep && it == 1) qkeep[1] = qr;
+      const float4 q = normalize4(qr);
       const float *tp = a.t + 3 * row;
       sts_qt(P + c * cs2, j, n, QT{q, make_float4(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), 0.f)});
       if (MODE < 2) {
@@ -257,7 +266,8 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
     bc2s = sqrtf(1.f - powf(a.beta2, (float)step));
     step_size = a.lr / (1.f - powf(a.beta1, (float)step));
   }
-  for (int idx = tid; idx < CN; idx += NT) {
+  int git = 0;
+  for (int idx = tid; idx < CN; idx += NT, ++git) {
     const int c = (int)b.divN.div(idx), k = idx - c * n;
     const int j = inv ? __ldg(inv + k) : k;  // in the caller's row order for full views
     const int i = j, e = sub16[j];
@@ -278,7 +288,9 @@ __device__ __forceinline__ void adjoint_item(const AdjointArgs &a, const ItemBuf
       dt = qrot(qc, F);
     }
     const long long row = b.off[c] + (inv ? k : gat16[j]);
-    const float4 q = __ldg(reinterpret_cast<const float4 *>(a.q) + row);
+    const float4 q = kKeep && git == 0   ? qkeep[0]
+                     : kKeep && git == 1 ? qkeep[1]
+                                         : __ldg(reinterpret_cast<const float4 *>(a.q) + row);
     const float inv = rsqrtf(dot4(q, q));
     const float4 u = make_float4(q.x * inv, q.y * inv, q.z * inv, q.w * inv);
     const float4 r = qmul(make_float4(tau.x, tau.y, tau.z, 0.f), u);
