@@ -284,21 +284,41 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket(const BucketArgs a) {
       pos[m] = atomicAdd(&s_hist[k[m]], 1);  // rank inside the bin
     }
   __syncthreads();
-  // exclusive scans over the bins: character starts and item starts
+  // exclusive scans over the bins: character starts and item starts (one
+  // warp's shuffles when the bins fit in a warp, else block-wide)
   const int per = (nk + nth - 1) / nth;
   const int b0 = min(nk, tid * per), b1 = min(nk, b0 + per);
-  int run = 0, irun = 0;
-  for (int b = b0; b < b1; ++b) {
-    run += s_hist[b];
-    irun += (s_hist[b] + cap - 1) / cap;
-  }
-  int pre = block_excl_scan(run, s_warp, &s_total);
-  int ipre = block_excl_scan(irun, s_warp, &s_itotal);
-  for (int b = b0; b < b1; ++b) {
-    s_start[b] = pre;
-    s_istart[b] = ipre;
-    pre += s_hist[b];
-    ipre += (s_hist[b] + cap - 1) / cap;
+  if (nk <= 32) {
+    if (tid < 32) {
+      const int h = tid < nk ? s_hist[tid] : 0, ih = (h + cap - 1) / cap;
+      int x = h, ix = ih;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o), iy = __shfl_up_sync(0xffffffffu, ix, o);
+        if (tid >= o) {
+          x += y;
+          ix += iy;
+        }
+      }
+      if (tid < nk) {
+        s_start[tid] = x - h;
+        s_istart[tid] = ix - ih;
+      }
+      if (tid == 31) s_itotal = ix;
+    }
+  } else {
+    int run = 0, irun = 0;
+    for (int b = b0; b < b1; ++b) {
+      run += s_hist[b];
+      irun += (s_hist[b] + cap - 1) / cap;
+    }
+    int pre = block_excl_scan(run, s_warp, &s_total);
+    int ipre = block_excl_scan(irun, s_warp, &s_itotal);
+    for (int b = b0; b < b1; ++b) {
+      s_start[b] = pre;
+      s_istart[b] = ipre;
+      pre += s_hist[b];
+      ipre += (s_hist[b] + cap - 1) / cap;
+    }
   }
   __syncthreads();
 #pragma unroll
