@@ -643,6 +643,33 @@ def test_edge_types_frame_and_local(torch):
     assert (np.abs(gt.cpu().numpy() - dt_ref).max(axis=1) <= tol).all()
 
 
+@pytest.mark.parametrize("walk", [0, 2])
+def test_frame_key_counts(torch, walk):
+    """Clips of 3 and of 40 keys: the work-queue kernel sorts characters by
+    key index with one warp's scan for at most 32 keys and with block-wide
+    scans beyond; both frames match the oracle, with times over several
+    clip loops and ranges of several hundred characters per type."""
+    rng = np.random.default_rng(91)
+    types = []
+    for parents, nk in ((synth.random_tree(48, 9, rng, spine=9), 3), (synth.random_tree(96, 20, rng, spine=20), 40),
+                        (synth.chain(64), 40)):
+        t = synth.make_type(parents, rng, with_clips=True)
+        keys = t["keys"]
+        reps = -(-nk // keys.shape[1])
+        t["keys"] = np.ascontiguousarray(np.concatenate([keys] * reps, axis=1)[:, :nk])
+        types.append(t)
+    ct = np.array([0] * 300 + [1] * 300 + [2] * 40, np.int32)
+    rng.shuffle(ct)
+    w = {"types": types, "char_type": ct, "time": rng.uniform(0.0, 3.0, len(ct)).astype(np.float32),
+         "weight": rng.uniform(0, 1, len(ct)).astype(np.float32)}
+    ref = oracle.frame(w)
+    ctx, plan = _gpu.setup(w)
+    ctx.set_schedule(plan, [16, 3, 2048, walk, 0])
+    out = ctx.evaluate_frame(plan, _gpu.cuda(w["time"]), _gpu.cuda(w["weight"]))
+    assert ctx.status() == 0
+    _gpu.assert_skin_close(out.cpu().numpy(), ref, w)
+
+
 @pytest.mark.parametrize("algorithm", [1, 2, 3, 4, 5])
 def test_paper_algorithms_parity(torch, algorithm):
     """The paper's Algorithms 1-4 and the leaf walk it describes (5) as GPU
