@@ -19,7 +19,7 @@ struct TypeDev {
   int n_clips;     // 0 if no clips uploaded
   int n_keys;
   float rate;
-  int pad0;
+  int chain;       // 1: the joints form one natural chain (parent[i] = i - 1 for i > 0)
   const int32_t *parent;     // [n]
   const int32_t *depth;      // [n]
   const int32_t *seg_start;  // [nseg + 1]

@@ -504,6 +504,7 @@ struct TypeHost {
     dev.nseg = seg.nseg;
     dev.rounds = seg.rounds;
     dev.max_depth = max_depth;
+    dev.chain = n >= 2 && max_depth == n ? 1 : 0;  // depth n with parent[i] < i: parent[i] = i - 1
     dev.parent = (const int32_t *)(base + o_par);
     dev.depth = (const int32_t *)(base + o_dep);
     dev.seg_start = (const int32_t *)(base + o_ss);

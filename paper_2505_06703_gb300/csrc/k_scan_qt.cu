@@ -25,10 +25,62 @@ namespace anim {
 
 namespace {
 
+__device__ __forceinline__ QT shfl_up_qt(const QT &a, int o) {
+  QT r;
+  r.q.x = __shfl_up_sync(0xffffffffu, a.q.x, o);
+  r.q.y = __shfl_up_sync(0xffffffffu, a.q.y, o);
+  r.q.z = __shfl_up_sync(0xffffffffu, a.q.z, o);
+  r.q.w = __shfl_up_sync(0xffffffffu, a.q.w, o);
+  r.t.x = __shfl_up_sync(0xffffffffu, a.t.x, o);
+  r.t.y = __shfl_up_sync(0xffffffffu, a.t.y, o);
+  r.t.z = __shfl_up_sync(0xffffffffu, a.t.z, o);
+  r.t.w = 0.f;
+  return r;
+}
+
+// A pure chain, one character per item: joint j's model pose is the product
+// L_0 ... L_j (Eq. 1 along the one path).  Each compute thread composes its
+// run of J consecutive joints in place (J = ceil(n / 256) rounded up to odd);
+// a warp-shuffle scan
+// over the runs' products and a scan of the 8 warp totals give each run the
+// product of everything before it, which the run then applies in place.
+// Two barriers instead of the segment walks and pointer-jumping rounds, so a
+// 2,048-deep chain is never walked more than J levels by one thread.
+__device__ __forceinline__ void chain_scan_qt(int n, float4 *P, QT *wtot, int tid) {
+  const int lane = tid & 31, warp = tid >> 5;
+  // an odd run length: the lanes' slots (J float4 apart) fall in distinct banks
+  const int J = ((n + kComputeThreads - 1) / kComputeThreads) | 1;
+  const int j0 = min(n, tid * J), j1 = min(n, j0 + J);
+  QT acc = qt_identity();
+  for (int j = j0; j < j1; ++j) {
+    const QT L = lds_qt(P, j, n);
+    acc = j == j0 ? L : qt_mul(acc, L);
+    if (j > j0) sts_qt(P, j, n, acc);
+  }
+  QT x = acc;  // inclusive scan of the run products over the warp's lanes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const QT y = shfl_up_qt(x, o);
+    if (lane >= o) x = qt_mul(y, x);
+  }
+  QT ex = shfl_up_qt(x, 1);
+  if (lane == 0) ex = qt_identity();
+  if (lane == 31) wtot[warp] = x;
+  compute_sync();
+  QT wp = qt_identity();
+  for (int w = 0; w < warp; ++w) wp = w == 0 ? wtot[0] : qt_mul(wp, wtot[w]);
+  if (tid > 0) {
+    const QT E = warp == 0 ? ex : lane == 0 ? wp : qt_mul(wp, ex);
+    for (int j = j0; j < j1; ++j) sts_qt(P, j, n, qt_mul(E, lds_qt(P, j, n)));
+  }
+  compute_sync();
+}
+
 template <int MODE, int MINB>
 __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ ItemBuf bufs[2];
+  __shared__ QT wtot[kComputeWarps];  // chain scan: the warps' run products
   const int tid = threadIdx.x;
   // launched with programmatic stream serialization (after the work-queue
   // kernel, for the frame): wait for the preceding grid to complete before
@@ -130,11 +182,20 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
     cp_async_wait_all();  // this thread's table copies (stage_tables)
     compute_sync();
 
-    // ---- pass 1b: running products along segments
-    pass1b_qt(b, Lt, P, cs2, tid);
-    compute_sync();
-    // ---- pass 2: pointer jumping over segments
-    const float4 *Y = pass2_qt(b, Lt, P, cs2, tid);
+    // ---- pass 1b: running products along segments; pass 2: pointer jumping
+    // over segments -- or, for one character of a pure chain of more than
+    // 1,024 joints, the chain scan (same-box A/B: config 3's 2,048-joint
+    // chains 54.2 -> 43.8 us per frame; the forward on config 2, whose
+    // 1,024-joint dragon it would also take, 50.6 -> 51.3 us)
+    const bool chain = b.T.chain && C == 1 && n > 1024;
+    const float4 *Y = nullptr;
+    if (chain) {
+      chain_scan_qt(n, P, wtot, tid);
+    } else {
+      pass1b_qt(b, Lt, P, cs2, tid);
+      compute_sync();
+      Y = pass2_qt(b, Lt, P, cs2, tid);
+    }
 
     // ---- pass 3: model pose, normalize, matrix, (bind,) store
     {
@@ -151,7 +212,7 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_scan_qt(const ScanArgs a)
         const int c1 = min(C, (grp + 1) * cpt);
         for (int c = grp * cpt; c < c1; ++c) {
           QT m = lds_qt(P + c * cs2, j, n);
-          if (info & kJ16Link) m = qt_mul(lds_qt(Y, c * nseg + g, C * nseg), m);
+          if (!chain && (info & kJ16Link)) m = qt_mul(lds_qt(Y, c * nseg + g, C * nseg), m);
           const Aff M = aff_from_qt(normalize4(m.q), m.t.x, m.t.y, m.t.z);
           if (model) stg_aff(model4 + (b.off[c] + j) * 3, M);
           if (skin) stg_aff(skin4 + (b.off[c] + j) * 3, aff_mul(M, B));
