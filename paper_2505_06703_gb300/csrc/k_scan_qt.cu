@@ -8,7 +8,10 @@
 //   MODE 2  the frame with layered blending (up to 4 clips by per-character
 //           weights and an additive layer, sample_layers_at).
 // The smaller item footprint lets more characters be in flight per SM, which
-// is what bounds the latency-limited scan passes.  The bind pass normalizes
+// is what bounds the latency-limited scan passes.  The segment tables are
+// staged by cp.async during pass 1a; one character of a pure chain longer
+// than 1,024 joints takes a two-level chain scan (chain_scan_qt) instead of
+// the segment walks and pointer jumping.  The bind pass normalizes
 // the composed quaternion once (removing the norm drift of long products),
 // forms M = [R(q) | t] and writes M and / or S = M B straight to global
 // memory.  Same item pipeline as k_scan (producer warp, 8 compute warps,
@@ -40,12 +43,12 @@ __device__ __forceinline__ QT shfl_up_qt(const QT &a, int o) {
 
 // A pure chain, one character per item: joint j's model pose is the product
 // L_0 ... L_j (Eq. 1 along the one path).  Each compute thread composes its
-// run of J consecutive joints in place (J = ceil(n / 256) rounded up to odd);
-// a warp-shuffle scan
-// over the runs' products and a scan of the 8 warp totals give each run the
-// product of everything before it, which the run then applies in place.
-// Two barriers instead of the segment walks and pointer-jumping rounds, so a
-// 2,048-deep chain is never walked more than J levels by one thread.
+// run of J consecutive joints in place (J = ceil(n / 256) rounded up to
+// odd); a warp-shuffle scan over the runs' products and a scan of the 8 warp
+// totals give each run the product of everything before it, which the run
+// then applies in place.  Two barriers instead of the segment walks and
+// pointer-jumping rounds, so a 2,048-deep chain is never walked more than J
+// levels by one thread.
 __device__ __forceinline__ void chain_scan_qt(int n, float4 *P, QT *wtot, int tid) {
   const int lane = tid & 31, warp = tid >> 5;
   // an odd run length: the lanes' slots (J float4 apart) fall in distinct banks
