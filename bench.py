@@ -4,19 +4,20 @@
 One step = one full frame of the 4,096 x 512-joint + 1,024-joint-dragon
 workload (2,098,176 joints): per-character key sampling, slerp/lerp between
 keys and between two clips, the Hierarchy-Scan and the bind product, as the
-library's two launches (work queue + persistent kernel) replayed from CUDA
-graphs.  The output rotates over enough buffers that consecutive steps
-touch more memory than the 129 MB L2 (inputs larger than L2).
+library's launches (the work queue, then the frame kernels) replayed from CUDA
+graphs of four consecutive frames.  The output rotates over enough buffers
+that consecutive steps touch more memory than the 129 MB L2 (inputs larger
+than L2).
 
 Printed (rank 0, one JSON line): joints/s of the whole job, the roofline of
-the persistent frame kernel (algorithmic bytes / CUDA-event duration against
-the measured HBM copy bandwidth), the end-to-end rate through the public API
+the frame kernels (algorithmic bytes / CUDA-event duration against the
+measured HBM copy bandwidth), the end-to-end rate through the public API
 with host buffers, the plain level-synchronous kernel on the same frame, the
 fused forward+adjoint (loss_backward) on the 1,024 x 256-joint workload, the
 FP64 oracle on the host cores, and SM clocks sampled during the timed loop.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on
-a bounded sample of the same workload.
+--impl reference times the FP64 CPU oracle on the host cores, one full frame
+of the same workload per step.
 
 Multi-GPU: characters are independent, so each rank runs its own batch of
 the same size (weak scaling, no data-path collective); the timing is the
